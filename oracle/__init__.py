@@ -1,0 +1,127 @@
+"""FP64 CPU oracle for global Shepard IDW (Sec. 2.1, Eq. 1).
+
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only ``tests/``,
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
+this package.  It shares no code with the CUDA library
+(``paper_1402_4986_gb300``) and never imports it.
+
+The arithmetic lives in ``idw_oracle.c`` (plain C, FP64, Neumaier sums,
+pthreads over queries); this module only compiles it with gcc and marshals
+numpy arrays.  Inputs given as float32 are promoted to float64 exactly, so the
+oracle sees the same bit patterns as the GPU path.
+
+Parity: pinned by ``tests/test_oracle_pins.py`` (exact rationals, mpmath,
+closed forms, invariants, finite differences).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "idw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, f"liboracle_{platform.machine()}.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library with gcc (no contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        compile_source(_SRC, tmp)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def bind(lib):
+    """Declare the C signatures on a loaded oracle library and return it."""
+    d = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    lib.oracle_idw_forward.argtypes = [d, i64, d, i64, ctypes.c_double, d,
+                                       ctypes.POINTER(ctypes.c_int64), d, ctypes.c_int]
+    lib.oracle_idw_forward.restype = ctypes.c_int
+    lib.oracle_idw_grad.argtypes = [d, i64, d, i64, ctypes.c_double, d, d, d, d, d, d,
+                                    ctypes.c_int]
+    lib.oracle_idw_grad.restype = ctypes.c_int
+    return lib
+
+
+def compile_source(src_path: str, out_path: str) -> str:
+    """Compile an oracle C source to a shared library (gcc, plain IEEE FP64)."""
+    subprocess.check_call([
+        "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+        "-pthread", "-D_POSIX_C_SOURCE=200809L", src_path, "-o", out_path, "-lm",
+    ])
+    return out_path
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _f64(a, cols):
+    a = np.ascontiguousarray(np.asarray(a), dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != cols:
+        raise ValueError(f"expected an array of shape (k, {cols}), got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def idw(data_xyz, queries_xy, p: float, threads: int = 0, return_s0: bool = False):
+    """Eq. 1 in FP64 for every query.
+
+    data_xyz: (n, 3) array of (x, y, z); queries_xy: (m, 2) array of (x, y).
+    Returns (Z float64[m], hit int64[m]) where hit is the lowest index of a
+    coincident data point, or -1; with ``return_s0`` also the weight sum S0
+    scaled by d2_min^(p/2) (inf at an exact hit).
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    m = q.shape[0]
+    Z = np.empty(m, np.float64)
+    hit = np.empty(m, np.int64)
+    S0 = np.empty(m, np.float64) if return_s0 else None
+    rc = lib.oracle_idw_forward(_ptr(data), data.shape[0], _ptr(q), m, float(p), _ptr(Z),
+                                hit.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                _ptr(S0) if S0 is not None else None, int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_forward rejected its arguments")
+    return (Z, hit, S0) if return_s0 else (Z, hit)
+
+
+def idw_grad(data_xyz, queries_xy, p: float, g, threads: int = 0):
+    """Gradients of L = sum_j g_j Z(q_j) in FP64 (chain rule on Eq. 1).
+
+    Returns a dict with Z[m], grad_z[n], grad_xy[n,2], grad_q[m,2], grad_p.
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    n, m = data.shape[0], q.shape[0]
+    g = np.ascontiguousarray(np.asarray(g), dtype=np.float64).reshape(m)
+    Z = np.empty(m, np.float64)
+    gz = np.empty(n, np.float64)
+    gxy = np.empty((n, 2), np.float64)
+    gq = np.empty((m, 2), np.float64)
+    gp = np.empty(1, np.float64)
+    rc = lib.oracle_idw_grad(_ptr(data), n, _ptr(q), m, float(p), _ptr(g), _ptr(Z), _ptr(gz),
+                             _ptr(gxy), _ptr(gq), _ptr(gp), int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_grad rejected its arguments")
+    return {"Z": Z, "grad_z": gz, "grad_xy": gxy, "grad_q": gq, "grad_p": float(gp[0])}

@@ -1,0 +1,360 @@
+/*
+ * FP64 CPU oracle for global (standard) Shepard inverse-distance weighting.
+ *
+ * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg may load this library.
+ * It shares no code, header, table or helper with the CUDA library; the two
+ * meet only through the seeded input generators.
+ *
+ * What it computes (Sec. 2.1, Eq. 1 of Mei & Tian, "Performance Impact of
+ * Data Layout on the GPU-accelerated IDW Interpolation"):
+ *
+ *     Z(q) = sum_i w_i(q) z_i / sum_j w_j(q),    w_i(q) = d(q, x_i)^(-p)
+ *
+ * over ALL n data points (standard/global IDW, Sec. 1 and Sec. 2.1), with p
+ * an arbitrary positive real (Sec. 2.1).
+ *
+ * Readings taken where the paper is silent:
+ *   - d is the 2-D Euclidean distance in (x, y); the third coordinate of a
+ *     data record is the sampled value z_i.
+ *   - d^(-p) is evaluated as (d^2)^(-p/2); no square root is taken.
+ *   - A query that coincides with a data point (d = 0, i.e. both coordinates
+ *     numerically equal) returns z_i of the LOWEST such index i; Eq. 1 is
+ *     undefined there.
+ *   - Weights are scaled by the common factor (d2_min)^(p/2), where d2_min is
+ *     the smallest squared distance of the query.  Eq. 1 is a ratio of two
+ *     sums that are both homogeneous of degree one in the weights, so the
+ *     factor cancels exactly; it keeps every weight in (0, 1] so that large
+ *     p neither overflows nor underflows in FP64.
+ *   - Both sums use Neumaier's compensated summation so that the oracle's own
+ *     rounding error is far below the tolerances it is used to check.
+ *   - NaN anywhere in a query's inputs gives NaN unless an exact hit is found.
+ *
+ * Gradients (not in the paper; derived from Eq. 1 by the chain rule, with
+ * S0 = sum w_i, S1 = sum w_i z_i, Z = S1/S0, w_i = (d_i^2)^(-p/2)):
+ *   dZ/dz_i  = w_i / S0
+ *   dZ/dq    = -(p/S0) sum_i (z_i - Z) w_i (q - x_i) / d_i^2
+ *   dZ/dx_i  = +(p/S0)       (z_i - Z) w_i (q - x_i) / d_i^2
+ *   dZ/dp    = -(1/(2 S0)) sum_i (z_i - Z) w_i ln d_i^2
+ * At an exact hit Z = z_k, so dZ/dz_k = 1 and every other derivative is 0.
+ * All of these ratios are unchanged by the common weight scaling above.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no fast-math, no
+ * contraction, so every operation is the plain IEEE double it reads as).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <unistd.h>
+
+/* ------------------------------------------------------------------ sums */
+
+typedef struct {
+    double s; /* running sum */
+    double c; /* Neumaier correction */
+} nsum;
+
+static void nsum_add(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double nsum_value(const nsum *a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------ one query */
+
+static double sqdist(double qx, double qy, double x, double y)
+{
+    double dx = qx - x;
+    double dy = qy - y;
+    return dx * dx + dy * dy;
+}
+
+/* Scaled weight w_i / (d2_min)^(p/2) = (d2_min / d2)^(p/2). */
+static double scaled_weight(double d2min, double d2, double p)
+{
+    double r = d2min / d2;
+    if (p == 2.0)
+        return r;
+    return pow(r, 0.5 * p);
+}
+
+/*
+ * Scans the data for an exact hit and the smallest squared distance.
+ * Returns the lowest coincident index, or -1 if there is none.
+ */
+static int64_t scan_query(const double *data, int64_t n, double qx, double qy, double *d2min_out)
+{
+    double d2min = INFINITY;
+    for (int64_t i = 0; i < n; i++) {
+        double x = data[3 * i + 0];
+        double y = data[3 * i + 1];
+        if (x == qx && y == qy)
+            return i;
+        double d2 = sqdist(qx, qy, x, y);
+        if (d2 < d2min)
+            d2min = d2;
+    }
+    *d2min_out = d2min;
+    return -1;
+}
+
+/*
+ * Eq. 1 for one query.  Writes Z and the exact-hit index; optionally S0 and
+ * Z's sums in the scaled form (S0 is the scaled weight sum, so S0 >= 1 when
+ * there is no hit and the data are finite).
+ */
+static void one_query(const double *data, int64_t n, double qx, double qy, double p,
+                      double *Z, int64_t *hit, double *S0_scaled, double *d2min_out)
+{
+    double d2min = 0.0;
+    int64_t k = scan_query(data, n, qx, qy, &d2min);
+    if (d2min_out)
+        *d2min_out = d2min;
+    if (k >= 0) {
+        *Z = data[3 * k + 2];
+        *hit = k;
+        if (S0_scaled)
+            *S0_scaled = INFINITY;
+        return;
+    }
+    nsum s0 = {0.0, 0.0};
+    nsum s1 = {0.0, 0.0};
+    for (int64_t i = 0; i < n; i++) {
+        double d2 = sqdist(qx, qy, data[3 * i + 0], data[3 * i + 1]);
+        double w = scaled_weight(d2min, d2, p);
+        nsum_add(&s0, w);
+        nsum_add(&s1, w * data[3 * i + 2]);
+    }
+    double S0 = nsum_value(&s0);
+    *Z = nsum_value(&s1) / S0;
+    *hit = -1;
+    if (S0_scaled)
+        *S0_scaled = S0;
+}
+
+/* --------------------------------------------------------- thread pool */
+
+typedef struct {
+    void (*fn)(void *ctx, int64_t begin, int64_t end);
+    void *ctx;
+    int64_t begin, end;
+} work;
+
+static void *run_work(void *arg)
+{
+    work *w = (work *)arg;
+    w->fn(w->ctx, w->begin, w->end);
+    return NULL;
+}
+
+static int resolve_threads(int nthreads)
+{
+    if (nthreads > 0)
+        return nthreads;
+    long c = sysconf(_SC_NPROCESSORS_ONLN);
+    return c > 0 ? (int)c : 1;
+}
+
+/* Runs fn over [0, count) split into contiguous ranges, one per thread. */
+static int parallel_for(int64_t count, int nthreads,
+                        void (*fn)(void *, int64_t, int64_t), void *ctx)
+{
+    int t = resolve_threads(nthreads);
+    if ((int64_t)t > count)
+        t = count > 0 ? (int)count : 1;
+    pthread_t *tid = (pthread_t *)calloc((size_t)t, sizeof(pthread_t));
+    work *ws = (work *)calloc((size_t)t, sizeof(work));
+    if (!tid || !ws) {
+        free(tid);
+        free(ws);
+        return -1;
+    }
+    for (int i = 0; i < t; i++) {
+        ws[i].fn = fn;
+        ws[i].ctx = ctx;
+        ws[i].begin = count * i / t;
+        ws[i].end = count * (i + 1) / t;
+    }
+    int started = 0;
+    for (int i = 1; i < t; i++) {
+        if (pthread_create(&tid[i], NULL, run_work, &ws[i]) != 0)
+            break;
+        started = i;
+    }
+    /* Ranges whose thread failed to start run here, sequentially. */
+    run_work(&ws[0]);
+    for (int i = started + 1; i < t; i++)
+        run_work(&ws[i]);
+    for (int i = 1; i <= started; i++)
+        pthread_join(tid[i], NULL);
+    free(tid);
+    free(ws);
+    return t;
+}
+
+/* ------------------------------------------------------------- forward */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    double p;
+    double *Z;
+    int64_t *hit;
+    double *S0;
+} fwd_ctx;
+
+static void fwd_range(void *vctx, int64_t b, int64_t e)
+{
+    fwd_ctx *c = (fwd_ctx *)vctx;
+    for (int64_t j = b; j < e; j++)
+        one_query(c->data, c->n, c->q[2 * j], c->q[2 * j + 1], c->p, &c->Z[j], &c->hit[j],
+                  c->S0 ? &c->S0[j] : NULL, NULL);
+}
+
+/*
+ * Eq. 1 for m queries.
+ *   data : n x 3 row-major doubles (x, y, z), host memory, caller-owned.
+ *   q    : m x 2 row-major doubles (x, y).
+ *   Z    : m doubles out.   hit : m int64 out (-1 = no exact hit).
+ *   S0   : optional m doubles out, the scaled weight sum (inf at a hit).
+ * Returns the number of threads used, or -1 on bad arguments.
+ */
+int oracle_idw_forward(const double *data, int64_t n, const double *q, int64_t m, double p,
+                       double *Z, int64_t *hit, double *S0, int nthreads)
+{
+    if (!data || !q || !Z || !hit || n < 1 || m < 0 || !(p > 0.0) || !isfinite(p))
+        return -1;
+    fwd_ctx c = {data, n, q, p, Z, hit, S0};
+    if (m == 0)
+        return 0;
+    return parallel_for(m, nthreads, fwd_range, &c);
+}
+
+/* ------------------------------------------------------------ gradients */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    int64_t m;
+    double p;
+    const double *g;      /* upstream gradient, m */
+    double *Z;            /* m, from pass A */
+    int64_t *hit;         /* m, from pass A */
+    double *S0;           /* m, scaled, from pass A */
+    double *d2min;        /* m, from pass A */
+    double *grad_q;       /* m x 2 out */
+    double *grad_p_part;  /* m out: per-query share of dL/dp */
+    double *grad_z;       /* n out */
+    double *grad_xy;      /* n x 2 out */
+} grad_ctx;
+
+/* Pass A: per query, Z, S0, and the query-side sums of dZ/dq and dZ/dp. */
+static void grad_query_range(void *vctx, int64_t b, int64_t e)
+{
+    grad_ctx *c = (grad_ctx *)vctx;
+    for (int64_t j = b; j < e; j++) {
+        double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+        one_query(c->data, c->n, qx, qy, c->p, &c->Z[j], &c->hit[j], &c->S0[j], &c->d2min[j]);
+        if (c->hit[j] >= 0) {
+            c->grad_q[2 * j] = 0.0;
+            c->grad_q[2 * j + 1] = 0.0;
+            c->grad_p_part[j] = 0.0;
+            continue;
+        }
+        nsum gx = {0, 0}, gy = {0, 0}, gp = {0, 0};
+        for (int64_t i = 0; i < c->n; i++) {
+            double x = c->data[3 * i], y = c->data[3 * i + 1], z = c->data[3 * i + 2];
+            double dx = qx - x, dy = qy - y;
+            double d2 = dx * dx + dy * dy;
+            double w = scaled_weight(c->d2min[j], d2, c->p);
+            double a = (z - c->Z[j]) * w;
+            nsum_add(&gx, a * dx / d2);
+            nsum_add(&gy, a * dy / d2);
+            nsum_add(&gp, a * log(d2));
+        }
+        double gj = c->g[j];
+        double S0 = c->S0[j];
+        c->grad_q[2 * j] = -gj * (c->p / S0) * nsum_value(&gx);
+        c->grad_q[2 * j + 1] = -gj * (c->p / S0) * nsum_value(&gy);
+        c->grad_p_part[j] = -gj * nsum_value(&gp) / (2.0 * S0);
+    }
+}
+
+/* Pass B: per data point, the sums over queries of dZ/dz_i and dZ/dx_i. */
+static void grad_data_range(void *vctx, int64_t b, int64_t e)
+{
+    grad_ctx *c = (grad_ctx *)vctx;
+    for (int64_t i = b; i < e; i++) {
+        double x = c->data[3 * i], y = c->data[3 * i + 1], z = c->data[3 * i + 2];
+        nsum gz = {0, 0}, gx = {0, 0}, gy = {0, 0};
+        for (int64_t j = 0; j < c->m; j++) {
+            double gj = c->g[j];
+            if (c->hit[j] >= 0) {
+                if (c->hit[j] == i)
+                    nsum_add(&gz, gj);
+                continue;
+            }
+            double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+            double dx = qx - x, dy = qy - y;
+            double d2 = dx * dx + dy * dy;
+            double w = scaled_weight(c->d2min[j], d2, c->p);
+            double S0 = c->S0[j];
+            nsum_add(&gz, gj * w / S0);
+            double a = gj * (c->p / S0) * (z - c->Z[j]) * w / d2;
+            nsum_add(&gx, a * dx);
+            nsum_add(&gy, a * dy);
+        }
+        c->grad_z[i] = nsum_value(&gz);
+        c->grad_xy[2 * i] = nsum_value(&gx);
+        c->grad_xy[2 * i + 1] = nsum_value(&gy);
+    }
+}
+
+/*
+ * Gradient of L = sum_j g_j Z(q_j) with respect to every input of Eq. 1.
+ *   data, q, p : as in oracle_idw_forward.   g : m doubles (dL/dZ_j).
+ *   Outputs (all required, host memory): Z[m], grad_z[n], grad_xy[n x 2],
+ *   grad_q[m x 2], grad_p[1].
+ * Returns the number of threads used, or -1 on bad arguments / no memory.
+ */
+int oracle_idw_grad(const double *data, int64_t n, const double *q, int64_t m, double p,
+                    const double *g, double *Z, double *grad_z, double *grad_xy,
+                    double *grad_q, double *grad_p, int nthreads)
+{
+    if (!data || !q || !g || !Z || !grad_z || !grad_xy || !grad_q || !grad_p || n < 1 ||
+        m < 1 || !(p > 0.0) || !isfinite(p))
+        return -1;
+    int64_t *hit = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    double *S0 = (double *)malloc((size_t)m * sizeof(double));
+    double *d2min = (double *)malloc((size_t)m * sizeof(double));
+    double *gp = (double *)malloc((size_t)m * sizeof(double));
+    if (!hit || !S0 || !d2min || !gp) {
+        free(hit);
+        free(S0);
+        free(d2min);
+        free(gp);
+        return -1;
+    }
+    grad_ctx c = {data, n, q, m, p, g, Z, hit, S0, d2min, grad_q, gp, grad_z, grad_xy};
+    int t = parallel_for(m, nthreads, grad_query_range, &c);
+    if (t > 0)
+        t = parallel_for(n, nthreads, grad_data_range, &c);
+    nsum total = {0, 0};
+    for (int64_t j = 0; j < m; j++)
+        nsum_add(&total, gp[j]);
+    *grad_p = nsum_value(&total);
+    free(hit);
+    free(S0);
+    free(d2min);
+    free(gp);
+    return t;
+}

@@ -1,0 +1,80 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of the oracle's C source
+(on the CPU), compiles it, swaps it in, and checks that at least one pin of
+``test_oracle_pins`` fails.  The real oracle is untouched.
+"""
+import ctypes
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+MUTATIONS = [
+    ("transposed operand in d^2", "return dx * dx + dy * dy;", "return dx * dx + dx * dy;"),
+    ("sign of dy", "double dy = qy - y;\n    return", "double dy = qy + y;\n    return"),
+    ("power not halved", "return pow(r, 0.5 * p);", "return pow(r, p);"),
+    ("p = 2 path uses 1/d instead of 1/d^2", "        return r;\n    return pow",
+     "        return sqrt(r);\n    return pow"),
+    ("value index off by one", "nsum_add(&s1, w * data[3 * i + 2]);",
+     "nsum_add(&s1, w * data[3 * i + 1]);"),
+    ("dropped weight in S1", "nsum_add(&s1, w * data[3 * i + 2]);", "nsum_add(&s1, data[3 * i + 2]);"),
+    ("exact hit on x only", "if (x == qx && y == qy)\n            return i;",
+     "if (x == qx)\n            return i;"),
+    ("last hit instead of first", "if (x == qx && y == qy)\n            return i;",
+     "if (x == qx && y == qy && i + 1 < n && !(data[3*(i+1)] == qx && data[3*(i+1)+1] == qy))\n"
+     "            return i;"),
+    ("Neumaier correction sign", "a->c += (a->s - t) + x;", "a->c += (a->s - t) - x;"),
+    ("query-gradient sign", "c->grad_q[2 * j] = -gj * (c->p / S0) * nsum_value(&gx);",
+     "c->grad_q[2 * j] = gj * (c->p / S0) * nsum_value(&gx);"),
+    ("p-gradient factor 1/2 dropped", "c->grad_p_part[j] = -gj * nsum_value(&gp) / (2.0 * S0);",
+     "c->grad_p_part[j] = -gj * nsum_value(&gp) / S0;"),
+    ("data-gradient uses dy for x", "nsum_add(&gx, a * dx);\n            nsum_add(&gy, a * dy);",
+     "nsum_add(&gx, a * dy);\n            nsum_add(&gy, a * dy);"),
+    ("z-gradient not normalised", "nsum_add(&gz, gj * w / S0);", "nsum_add(&gz, gj * w);"),
+    ("exact-hit gradient dropped", "                if (c->hit[j] == i)\n                    nsum_add(&gz, gj);",
+     "                if (c->hit[j] == i)\n                    nsum_add(&gz, 0.0);"),
+]
+
+PINS = [
+    lambda: pins.test_exact_rational_even_p(2, 0),
+    lambda: pins.test_exact_rational_even_p(4, 1),
+    pins.test_exact_rational_with_hits_and_duplicates,
+    lambda: pins.test_mpmath_general_p(1.5),
+    lambda: pins.test_two_points_closed_form(3.0),
+    pins.test_square_centre_is_mean_and_bisector,
+    pins.test_constant_field_is_reproduced,
+    pins.test_permutation_invariance,
+    pins.test_exact_hit_rule_reproduces_data_values,
+    pins.test_shared_single_coordinate_is_not_a_hit,
+    lambda: pins.test_gradient_matches_central_differences(2.5),
+    pins.test_gradient_z_is_partition_of_unity,
+    pins.test_gradient_at_exact_hit,
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, old, new, tmp_path, monkeypatch):
+    src = open(oracle._SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not found uniquely: {name}"
+    mutated = tmp_path / "mutant.c"
+    mutated.write_text(src.replace(old, new))
+    lib = oracle.bind(ctypes.CDLL(oracle.compile_source(str(mutated), str(tmp_path / "mutant.so"))))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    caught = 0
+    for pin in PINS:
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, f"no pin caught: {name}"
+
+
+def test_unmutated_source_passes_every_pin(tmp_path, monkeypatch):
+    lib = oracle.bind(ctypes.CDLL(oracle.compile_source(oracle._SRC, str(tmp_path / "clean.so"))))
+    monkeypatch.setattr(oracle, "_lib", lib)
+    for pin in PINS:
+        pin()
+    assert os.path.exists(oracle._SRC)

@@ -1,0 +1,281 @@
+"""Pins for the FP64 oracle: each check is fixed by the mathematics of Eq. 1
+(Sec. 2.1), not by re-running the oracle's own formula.
+
+* exact rational arithmetic (fp32 inputs are dyadic rationals, and for even p
+  every weight is rational, so Eq. 1 has an exact value);
+* 50-digit mpmath evaluation for non-integer p;
+* closed forms (N = 1, two points, symmetric squares, bisector);
+* invariants (constant field, convex hull of z, permutation, dyadic
+  translation and scaling, nearest-neighbour limit as p grows, exact hits);
+* central finite differences of the forward pass for the analytic gradient.
+
+A dropped term, a wrong sign or index, or a transposed operand in the oracle
+fails at least one of these.
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+mpmath = pytest.importorskip("mpmath")
+
+
+def _tiny(seed, n, m, lo=0.0, hi=1.0):
+    rng = np.random.default_rng(seed)
+    data = np.empty((n, 3), np.float32)
+    data[:, :2] = rng.uniform(lo, hi, (n, 2)).astype(np.float32)
+    data[:, 2] = rng.standard_normal(n).astype(np.float32)
+    q = rng.uniform(lo, hi, (m, 2)).astype(np.float32)
+    return data, q
+
+
+def _exact_z(data, q, p_even):
+    """Exact rational Z of Eq. 1 for an even integer power."""
+    out = []
+    for qx, qy in q:
+        fx, fy = Fraction(float(qx)), Fraction(float(qy))
+        s0 = Fraction(0)
+        s1 = Fraction(0)
+        hit = None
+        for i, (x, y, z) in enumerate(data):
+            d2 = (fx - Fraction(float(x))) ** 2 + (fy - Fraction(float(y))) ** 2
+            if d2 == 0:
+                hit = i
+                break
+            w = 1 / d2 ** (p_even // 2)
+            s0 += w
+            s1 += w * Fraction(float(z))
+        out.append((float(data[hit, 2]), hit) if hit is not None else (float(s1 / s0), -1))
+    return out
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_exact_rational_even_p(p, seed):
+    data, q = _tiny(seed, 23, 17)
+    Z, hit = oracle.idw(data, q, float(p))
+    zmax = np.abs(data[:, 2]).max()
+    for j, (ze, he) in enumerate(_exact_z(data, q, p)):
+        assert hit[j] == he
+        assert abs(Z[j] - ze) <= 4e-16 * zmax, (j, Z[j], ze)
+
+
+def test_exact_rational_with_hits_and_duplicates():
+    data, q = _tiny(7, 19, 12)
+    data[11, :2] = data[4, :2]          # duplicate location, different z
+    q[3] = data[4, :2]                  # hit on the duplicated location
+    q[8] = data[18, :2]
+    Z, hit = oracle.idw(data, q, 2.0)
+    exact = _exact_z(data, q, 2)
+    assert hit[3] == 4 and Z[3] == np.float64(data[4, 2])
+    assert hit[8] == 18 and Z[8] == np.float64(data[18, 2])
+    for j, (ze, he) in enumerate(exact):
+        assert hit[j] == he
+        assert abs(Z[j] - ze) <= 4e-16 * np.abs(data[:, 2]).max()
+
+
+@pytest.mark.parametrize("p", [0.5, 1.5, 2.5, 3.5, 7.25])
+def test_mpmath_general_p(p):
+    data, q = _tiny(11, 21, 13)
+    Z, hit = oracle.idw(data, q, p)
+    mpmath.mp.dps = 50
+    for j, (qx, qy) in enumerate(q):
+        s0 = mpmath.mpf(0)
+        s1 = mpmath.mpf(0)
+        for x, y, z in data:
+            d2 = (mpmath.mpf(float(qx)) - float(x)) ** 2 + (mpmath.mpf(float(qy)) - float(y)) ** 2
+            w = d2 ** (-mpmath.mpf(p) / 2)
+            s0 += w
+            s1 += w * float(z)
+        ref = float(s1 / s0)
+        assert hit[j] == -1
+        assert abs(Z[j] - ref) <= 1e-15 * np.abs(data[:, 2]).max(), (p, j, Z[j], ref)
+
+
+def test_single_point_gives_its_value_everywhere():
+    data = np.array([[0.25, 0.75, -3.5]], np.float32)
+    q = np.random.default_rng(0).random((50, 2)).astype(np.float32)
+    for p in (0.3, 2.0, 5.0):
+        Z, hit = oracle.idw(data, q, p)
+        assert np.all(Z == -3.5)
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 3.0, 4.5])
+def test_two_points_closed_form(p):
+    # Points on the x axis, query between and beyond them.
+    data = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, -2.0]], np.float32)
+    qs = np.array([[0.25, 0.0], [0.5, 0.0], [0.75, 0.0], [2.0, 0.0], [0.5, 0.5]], np.float32)
+    Z, _ = oracle.idw(data, qs, p)
+    for j, (qx, qy) in enumerate(qs.astype(np.float64)):
+        a = np.hypot(qx - 0.0, qy)      # distance to point 1
+        b = np.hypot(qx - 1.0, qy)      # distance to point 2
+        ref = (1.0 * b ** p + (-2.0) * a ** p) / (a ** p + b ** p)
+        assert abs(Z[j] - ref) <= 1e-15, (p, j, Z[j], ref)
+
+
+def test_square_centre_is_mean_and_bisector():
+    # Four corners of a square around (0.5, 0.5): all equidistant from the centre.
+    data = np.array([[0.25, 0.25, 1.0], [0.75, 0.25, 2.0], [0.25, 0.75, 4.0],
+                     [0.75, 0.75, 8.0]], np.float32)
+    for p in (0.7, 2.0, 3.5):
+        Z, _ = oracle.idw(data, np.array([[0.5, 0.5]], np.float32), p)
+        assert Z[0] == pytest.approx(15.0 / 4.0, abs=1e-15)
+    # On the perpendicular bisector of two points the result is their mean.
+    two = np.array([[0.0, 0.0, 3.0], [1.0, 0.0, 5.0]], np.float32)
+    qs = np.array([[0.5, y] for y in (-2.0, 0.1, 0.5, 7.0)], np.float32)
+    Z, _ = oracle.idw(two, qs, 2.0)
+    assert np.all(np.abs(Z - 4.0) <= 1e-15)
+
+
+def test_constant_field_is_reproduced():
+    data, q = _tiny(3, 300, 200)
+    data[:, 2] = np.float32(0.3)
+    for p in (1.5, 2.0, 3.5):
+        Z, _ = oracle.idw(data, q, p)
+        assert np.all(np.abs(Z - np.float64(np.float32(0.3))) <= 2 * np.spacing(0.3))
+
+
+def test_result_inside_range_of_z():
+    prob = synthetic.uniform_problem(2000, 500, seed=5)
+    for p in (0.5, 2.0, 6.0):
+        Z, _ = oracle.idw(prob["data"], prob["queries"], p)
+        zmin, zmax = prob["data"][:, 2].min(), prob["data"][:, 2].max()
+        assert np.all(Z >= zmin - 1e-15) and np.all(Z <= zmax + 1e-15)
+
+
+def test_permutation_invariance():
+    prob = synthetic.uniform_problem(1500, 300, seed=6)
+    perm = np.random.default_rng(1).permutation(1500)
+    for p in (2.0, 3.5):
+        Za, _ = oracle.idw(prob["data"], prob["queries"], p)
+        Zb, _ = oracle.idw(prob["data"][perm], prob["queries"], p)
+        assert np.max(np.abs(Za - Zb)) <= 1e-15
+
+
+def test_dyadic_translation_and_scaling_are_exact():
+    prob = synthetic.uniform_problem(800, 200, seed=8)
+    d64 = prob["data"].astype(np.float64)
+    q64 = prob["queries"].astype(np.float64)
+    for p in (2.0, 3.5):
+        Z0, _ = oracle.idw(d64, q64, p)
+        # Translation by 0.5 and scaling by 2^5 are exact in FP64 on fp32
+        # inputs, and Eq. 1 depends only on distance ratios.
+        dt = d64.copy(); dt[:, :2] += 0.5
+        Zt, _ = oracle.idw(dt, q64 + 0.5, p)
+        ds = d64.copy(); ds[:, :2] *= 32.0
+        Zs, _ = oracle.idw(ds, q64 * 32.0, p)
+        assert np.array_equal(Z0, Zt)
+        assert np.array_equal(Z0, Zs)
+        # Non-dyadic scaling re-rounds the inputs: agreement to rounding level.
+        dn = d64.copy(); dn[:, :2] *= 3.7
+        Zn, _ = oracle.idw(dn, q64 * 3.7, p)
+        assert np.max(np.abs(Z0 - Zn)) <= 1e-12
+
+
+def test_nearest_neighbour_limit_large_p():
+    data, q = _tiny(12, 200, 60)
+    d = data[:, :2].astype(np.float64)
+    for p in (64.0, 300.0):
+        Z, _ = oracle.idw(data, q, p)
+        for j, (qx, qy) in enumerate(q.astype(np.float64)):
+            dist = np.hypot(d[:, 0] - qx, d[:, 1] - qy)
+            k = np.argmin(dist)
+            ratio = (dist[k] / np.delete(dist, k)) ** p
+            bound = np.sum(ratio * np.abs(np.delete(data[:, 2], k) - data[k, 2])) + 1e-15
+            assert abs(Z[j] - data[k, 2]) <= bound
+
+
+def test_exact_hit_rule_reproduces_data_values():
+    prob = synthetic.config_exact_hits(n=4096, m=1024, hits=64)
+    Z, hit = oracle.idw(prob["data"], prob["queries"], 2.0)
+    assert np.array_equal(np.sort(np.nonzero(hit >= 0)[0]), prob["hit_q"])
+    assert np.array_equal(hit[prob["hit_q"]], prob["hit_d"])
+    assert np.array_equal(Z[prob["hit_q"]], prob["data"][prob["hit_d"], 2].astype(np.float64))
+
+
+def test_shared_single_coordinate_is_not_a_hit():
+    # Queries that share exactly one coordinate with a data point are ordinary
+    # points of Eq. 1; only both coordinates equal make d = 0.
+    data = np.array([[0.5, 0.125, 7.0], [0.25, 0.875, 1.0], [0.75, 0.5, -2.0]], np.float32)
+    q = np.array([[0.5, 0.375], [0.625, 0.875], [0.75, 0.5]], np.float32)
+    Z, hit = oracle.idw(data, q, 2.0)
+    exact = _exact_z(data, q, 2)
+    assert list(hit) == [-1, -1, 2]
+    for j, (ze, he) in enumerate(exact):
+        assert abs(Z[j] - ze) <= 4e-16 * 7.0
+
+
+def test_negative_zero_counts_as_coincident():
+    data = np.array([[0.0, 0.5, 2.0], [1.0, 1.0, 9.0]], np.float32)
+    q = np.array([[-0.0, 0.5]], np.float32)
+    Z, hit = oracle.idw(data, q, 2.0)
+    assert hit[0] == 0 and Z[0] == 2.0
+
+
+def test_rejects_bad_p():
+    data, q = _tiny(0, 4, 2)
+    for p in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(ValueError):
+            oracle.idw(data, q, p)
+
+
+# ---------------------------------------------------------------- gradients
+
+def _loss(data, q, p, g):
+    Z, _ = oracle.idw(data, q, p)
+    return float(np.dot(g, Z))
+
+
+@pytest.mark.parametrize("p", [2.0, 2.5])
+def test_gradient_matches_central_differences(p):
+    rng = np.random.default_rng(21)
+    n = m = 96
+    data = np.empty((n, 3), np.float64)
+    data[:, :2] = synthetic.separated_xy(rng, n, 2e-3)
+    data[:, 2] = rng.standard_normal(n)
+    q = synthetic.separated_xy(rng, m, 2e-3).astype(np.float64) + 1e-3 * rng.random((m, 2))
+    g = rng.standard_normal(m)
+    G = oracle.idw_grad(data, q, p, g)
+    eps = 1e-6
+
+    def fd(arr, idx):
+        a = arr.copy(); a[idx] += eps
+        b = arr.copy(); b[idx] -= eps
+        if arr is data:
+            return (_loss(a, q, p, g) - _loss(b, q, p, g)) / (2 * eps)
+        return (_loss(data, a, p, g) - _loss(data, b, p, g)) / (2 * eps)
+
+    scale_d = max(np.abs(G["grad_xy"]).max(), np.abs(G["grad_z"]).max())
+    for i in rng.choice(n, 12, replace=False):
+        assert abs(fd(data, (i, 2)) - G["grad_z"][i]) <= 1e-6 * scale_d
+        assert abs(fd(data, (i, 0)) - G["grad_xy"][i, 0]) <= 1e-6 * scale_d
+        assert abs(fd(data, (i, 1)) - G["grad_xy"][i, 1]) <= 1e-6 * scale_d
+    scale_q = np.abs(G["grad_q"]).max()
+    for j in rng.choice(m, 12, replace=False):
+        assert abs(fd(q, (j, 0)) - G["grad_q"][j, 0]) <= 1e-6 * scale_q
+        assert abs(fd(q, (j, 1)) - G["grad_q"][j, 1]) <= 1e-6 * scale_q
+    dp = (_loss(data, q, p + eps, g) - _loss(data, q, p - eps, g)) / (2 * eps)
+    assert abs(dp - G["grad_p"]) <= 1e-6 * max(1.0, abs(dp))
+    assert np.allclose(G["Z"], oracle.idw(data, q, p)[0], rtol=0, atol=0)
+
+
+def test_gradient_z_is_partition_of_unity():
+    # sum_i dZ/dz_i = 1 for every query (weights normalised by S0), so with
+    # g = 1 the data-side z-gradient sums to m.
+    prob = synthetic.uniform_problem(300, 120, seed=31)
+    G = oracle.idw_grad(prob["data"], prob["queries"], 2.0, np.ones(120))
+    assert abs(G["grad_z"].sum() - 120.0) <= 1e-11
+    # Translating every point and query together changes nothing, so the
+    # coordinate gradients cancel: sum_i dZ/dx_i + dZ/dq = 0.
+    assert np.abs(G["grad_xy"].sum(0) + G["grad_q"].sum(0)).max() <= 1e-9 * np.abs(G["grad_q"]).max()
+
+
+def test_gradient_at_exact_hit():
+    data = np.array([[0.1, 0.2, 1.5], [0.7, 0.4, -1.0], [0.3, 0.9, 2.0]], np.float64)
+    q = np.array([[0.7, 0.4]], np.float64)
+    G = oracle.idw_grad(data, q, 2.0, np.array([3.0]))
+    assert np.array_equal(G["grad_z"], [0.0, 3.0, 0.0])
+    assert np.all(G["grad_xy"] == 0) and np.all(G["grad_q"] == 0) and G["grad_p"] == 0
