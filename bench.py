@@ -1,0 +1,340 @@
+"""Benchmark of global Shepard IDW (Eq. 1) on GB300.
+
+One step = one FP32-compensated interpolation of M = 2^20 queries against
+N = 2^20 data points (p = 2), inputs resident in HBM: staging, all-pairs
+sweep, FP64 combine, slow path.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank interpolates its own 2^20
+queries (seeded by rank) against the same replicated data; there is no
+collective on the data path (weak scaling).  Timing: barrier + synchronize on
+both sides of the K timed steps, max over ranks.
+
+Besides ``value`` (device-resident pairs/s) the line carries:
+  e2e           the same metric through the host-buffer C-ABI entry point,
+                host<->device copies of inputs and results inside the region;
+  roofline      the all-pairs sweep kernel's pairs/s (CUDA events around each
+                launch, recorded by the library) against the arithmetic-pipe
+                peak min(FMA pipe / 6 ops, MUFU / 1 op) per pair;
+  f64_plain     the plain FP64 form on the same GPU (query sample);
+  error         max |Z - Z_64| / max |z| against the FP64 oracle on a query
+                sample (the same sample the CPU baseline times);
+  cpu_baseline  the FP64 oracle on the host cores (bounded query sample);
+  clocks        nvidia-smi samples taken during the timed region.
+``--impl reference`` times the oracle alone (the CPU reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("pairs/s at N=M=2^20 p=2: FP32-comp vs FP64 plain, error ≤2e-6, "
+          "% pipe roofline")
+UNIT = "pairs/s"
+N_DEFAULT = 1 << 20
+# Doc values for compute capability 10.x (per SM per clock): 128 FP32 FMA
+# lanes, 16 MUFU lanes.  The measured rates are reported beside them.
+FFMA_PER_SM_CLK = 128.0
+MUFU_PER_SM_CLK = 16.0
+FMA_OPS_PER_PAIR = 6.0   # 2 FADD (dx, dy), FMUL, FFMA (d^2), FADD (S0), FFMA (S1)
+MUFU_OPS_PER_PAIR = 1.0  # rcp(d^2) at p = 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_reference(args, rank):
+    """CPU reference arm: the FP64 oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    import synthetic
+    prob = synthetic.config_scale(args.n)
+    data, q = prob["data"], prob["queries"]
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle.idw(data, q[:32], 2.0)
+    rate = 32 * args.n / (time.perf_counter() - t)
+    total_steps = args.steps + args.warmup
+    per_step = max(8, int(min(150.0 / total_steps, 8.0) * rate / args.n))
+    rng = np.random.default_rng(0)
+    times = []
+    for s in range(total_steps):
+        idx = rng.choice(q.shape[0], per_step, replace=False)
+        t = time.perf_counter()
+        oracle.idw(data, q[idx], 2.0, threads=cores)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    pairs = per_step * args.n
+    value = pairs * len(times) / sum(times)
+    sample = f"{per_step} random queries x all {args.n} data points per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"global Shepard IDW, N=M={args.n}, p=2, uniform [0,1)^2, "
+                               "wave field (FP64 CPU oracle on a query sample)",
+                   "n": args.n, "m": args.n, "p": 2.0},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    from paper_1402_4986_gb300 import build as libbuild
+    libbuild.build()
+
+    n = m = args.n
+    prob = synthetic.config_scale(n)
+    data_np = prob["data"]
+    # Weak scaling: rank r interpolates its own query set against the same data.
+    q_np = prob["queries"] if rank == 0 else synthetic.uniform_xy(
+        np.random.default_rng(9000 + rank), m)
+    data = torch.from_numpy(data_np).cuda()
+    q = torch.from_numpy(q_np).cuda()
+    out = torch.empty(m, device="cuda")
+    h = idw.get_handle(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        idw.interpolate(data, q, 2.0, out=out, handle=h)
+    idw.sync_status(handle=h)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: K device-resident steps
+    idw.profile_read(handle=h)
+    idw.profile_enable(True, handle=h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)   # evict inputs from L2 between steps
+        ev[k][0].record(stream)
+        idw.interpolate(data, q, 2.0, out=out, handle=h)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier()
+    clocks = sampler.stop()
+    idw.profile_enable(False, handle=h)
+    sweep_ms, sweep_launches = idw.profile_read(handle=h)
+    idw.sync_status(handle=h)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t)
+    pairs_step = float(n) * m
+    value = ws * pairs_step * args.steps / total_s
+    Z_dev = out.cpu().numpy()
+
+    # ---- end to end: host buffers through the C ABI, copies inside the region
+    d_host = torch.from_numpy(data_np).pin_memory()
+    q_host = torch.from_numpy(q_np).pin_memory()
+    o_host = torch.empty(m, dtype=torch.float32).pin_memory()
+    idw.interpolate_host(d_host, q_host, 2.0, out=o_host, handle=h)
+    e2e_steps = max(2, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        idw.interpolate_host(d_host, q_host, 2.0, out=o_host, handle=h)
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t)
+    e2e = {"value": ws * pairs_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(data_np.nbytes + q_np.nbytes),
+           "d2h_bytes_per_step": int(o_host.numel() * 4)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- FP64 plain form, same GPU, query sample (it runs ~100x slower)
+    m64 = 8192
+    d64 = data.double()
+    q64 = q[:m64].double()
+    idw.interpolate(d64, q64[:1024], 2.0, "f64", handle=h)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    idw.interpolate(d64, q64, 2.0, "f64", handle=h)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f64_value = float(n) * m64 / (e0.elapsed_time(e1) / 1e3)
+
+    # ---- pipe roofline of the sweep kernel
+    rates = idw.measure_pipe_rates(local)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    clk_mhz = clocks.get("sm_mhz") or 0.0
+    sweep_avg_s = sweep_ms / max(1, sweep_launches) / 1e3
+    achieved = pairs_step / sweep_avg_s
+
+    def peak(ffma, mufu, mhz):
+        return sms * mhz * 1e6 * min(ffma / FMA_OPS_PER_PAIR, mufu / MUFU_OPS_PER_PAIR)
+
+    peak_doc = peak(FFMA_PER_SM_CLK, MUFU_PER_SM_CLK, clk_mhz)
+    peak_meas = peak(max(rates["ffma"], rates["ffma2"]), rates["mufu_rcp"], clk_mhz)
+    roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_doc / 1e9,
+            "unit": "Gpairs/s", "frac": achieved / peak_doc if peak_doc else None,
+            "traffic": None,
+            "kernel": "fwd_f32_kernel (all-pairs sweep)",
+            "peak_basis": "min(128 FFMA / 6 ops, 16 MUFU / 1 op) per SM per clock x "
+                          f"{sms} SMs x median SM clock {clk_mhz} MHz under load",
+            "peak_measured_rates": peak_meas / 1e9,
+            "frac_of_measured_rates": achieved / peak_meas if peak_meas else None,
+            "peak_at_2070mhz": peak(FFMA_PER_SM_CLK, MUFU_PER_SM_CLK, 2070.0) / 1e9,
+            "pipe_rates_per_sm_clk": rates,
+            "sweep_ms_avg": sweep_avg_s * 1e3, "sweep_launches": sweep_launches}
+
+    # ---- FP64 oracle on the host: error check + CPU baseline on one sample
+    cpu = None
+    err = None
+    if not args.no_cpu_baseline:
+        import oracle
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        oracle.idw(data_np, q_np[:32], 2.0, threads=cores)
+        rate = 32 * n / (time.perf_counter() - t)
+        S = int(min(max(256, args.cpu_seconds * rate / n), m))
+        idx = np.sort(np.random.default_rng(1).choice(m, S, replace=False))
+        t = time.perf_counter()
+        Z64, _ = oracle.idw(data_np, q_np[idx], 2.0, threads=cores)
+        cpu_s = time.perf_counter() - t
+        err = float(np.max(np.abs(Z_dev[idx].astype(np.float64) - Z64)) /
+                    np.max(np.abs(data_np[:, 2])))
+        cpu = {"value": S * n / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{S} random queries x all {n} data points ({cpu_s:.1f} s)"}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"global Shepard IDW, N=M={n} per GPU, p=2, uniform [0,1)^2 "
+                               "points, z = sin(2 pi x) cos(2 pi y) + 0.1 N(0,1), "
+                               "FP32-compensated (FP64 combine)",
+                   "n": n, "m": m, "p": 2.0, "parallelism": f"query shards x{ws}, data replicated",
+                   "l2": "flushed between steps (256 MiB write; inputs are 36 MiB)"},
+        "e2e": e2e, "gpu_launches": 4 * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "error_vs_fp64_oracle": err,
+        "f64_plain": {"value": f64_value, "unit": UNIT,
+                      "sample": f"{m64} queries x all {n} data points"},
+        "speedup_vs_f64_plain": value / ws / f64_value,
+        "wall_s_timed_region": wall,
+        "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                    "max": max(step_ms)},
+    }
+    print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

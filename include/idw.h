@@ -1,0 +1,211 @@
+/*
+ * idw.h -- C ABI of the GB300 (sm_103a) library for global Shepard
+ * inverse-distance-weighted (IDW) interpolation.
+ *
+ * The operation (Mei & Tian, "Performance Impact of Data Layout on the
+ * GPU-accelerated IDW Interpolation", Sec. 2.1, Eq. 1): for every query
+ * (prediction point) q,
+ *
+ *     Z(q) = sum_i w_i z_i / sum_i w_i,   w_i = d(q, x_i)^(-p),
+ *
+ * over ALL n data points (standard, global IDW; Sec. 1 and Sec. 2.1), with p
+ * an arbitrary positive real (Sec. 2.1; typically 2).
+ *
+ * Conventions shared by every entry point:
+ *   - A data point is a row (x, y, z): d is the 2-D Euclidean distance in
+ *     (x, y), and z is the sampled value.  Rows are contiguous, row-major,
+ *     3 elements each (the paper's unaligned AoS record, Sec. 3.2); the
+ *     library restages them internally.  Queries are rows (x, y).
+ *   - d^(-p) is evaluated as (d^2)^(-p/2); no square root is taken.
+ *   - A query whose (x, y) equals a data point's (x, y) numerically (so
+ *     d = 0, where Eq. 1 is undefined) gets the z of the LOWEST such index.
+ *   - NaN in a query's inputs gives NaN in its result unless an exact hit
+ *     is found first; inputs are not scanned for NaN.
+ *   - Pointers named "device" are CUDA device (or managed) memory owned by
+ *     the caller; they must stay valid until the work on `stream` is done.
+ *     Every float array needs 4-byte alignment, every double array 8-byte.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Compute entry points are asynchronous: they validate their
+ *     arguments on the host, enqueue kernels and return.  A CUDA error that
+ *     occurs later is reported by a later call or by idw_sync_status().
+ *   - A handle owns a device workspace that grows on demand.  Calls on one
+ *     handle must not overlap on different streams; use one handle per
+ *     concurrently used stream.  Handles are not thread-safe.
+ *   - Sizes: 1 <= n < 2^31 and 0 <= m < 2^31; m = 0 is a no-op.
+ */
+#ifndef IDW_GB300_H
+#define IDW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idw_handle_s *idw_handle_t;
+
+typedef enum {
+    IDW_OK = 0,
+    IDW_ERR_INVALID_ARG = 1,   /* null pointer, bad size, p <= 0 or non-finite p */
+    IDW_ERR_ALIGNMENT = 2,     /* a pointer lacks the element alignment */
+    IDW_ERR_CUDA = 3,          /* a CUDA runtime call failed (see idw_last_cuda_error) */
+    IDW_ERR_NOT_FINITE_INPUT = 4,
+    IDW_ERR_WORKSPACE = 5,     /* device workspace could not be allocated */
+    IDW_ERR_UNSUPPORTED = 6,   /* device is not sm_103 or option not supported */
+    IDW_ERR_DEVICE_TIMEOUT = 7 /* a bounded wait inside a kernel gave up */
+} idw_status;
+
+typedef enum {
+    /* FP32 pair arithmetic with compensated (two-sum) accumulation; the
+     * per-query combine of partial sums and the division run in FP64.
+     * data/queries/out are float. */
+    IDW_PREC_F32_COMP = 0,
+    /* Plain FP64 throughout (the comparison form). data/queries/out are
+     * double. */
+    IDW_PREC_F64_PLAIN = 1
+} idw_precision;
+
+/* Human-readable name of a status code (static storage). */
+const char *idw_status_string(idw_status s);
+
+/* Creates a handle bound to CUDA device `device` (made current during each
+ * call).  Fails with IDW_ERR_UNSUPPORTED if the device is not compute
+ * capability 10.3. */
+idw_status idw_create(idw_handle_t *handle, int device);
+
+/* Frees the handle and its workspace after synchronising the device. */
+idw_status idw_destroy(idw_handle_t handle);
+
+/* Text of the last CUDA error seen by this handle (static storage). */
+const char *idw_last_cuda_error(idw_handle_t handle);
+
+/*
+ * Eq. 1 for m queries against n data points.
+ *   data_xyz   : device, n x 3 (x, y, z) rows; float or double per `prec`.
+ *   queries_xy : device, m x 2 (x, y) rows; same type.
+ *   p          : power parameter, finite and > 0 (Sec. 2.1).
+ *   out        : device, m results; float (F32_COMP) or double (F64_PLAIN).
+ */
+idw_status idw_interpolate(idw_handle_t handle, const void *data_xyz, int64_t n,
+                           const void *queries_xy, int64_t m, double p, idw_precision prec,
+                           void *out, void *stream);
+
+/*
+ * As idw_interpolate, and also saves what the adjoint needs:
+ *   s0_out  : device, m doubles, nullable: the weight sum S0 = sum_i w_i
+ *             (+inf at an exact hit).
+ *   hit_out : device, m int32, nullable: the exact-hit index, or -1.
+ */
+idw_status idw_interpolate_saved(idw_handle_t handle, const void *data_xyz, int64_t n,
+                                 const void *queries_xy, int64_t m, double p,
+                                 idw_precision prec, void *out, double *s0_out,
+                                 int32_t *hit_out, void *stream);
+
+/*
+ * idw_interpolate with HOST buffers: copies the inputs to the device,
+ * computes, copies the results back and synchronises `stream` before it
+ * returns.  Page-locked host memory gives the fastest copies.
+ */
+idw_status idw_interpolate_host(idw_handle_t handle, const void *data_xyz, int64_t n,
+                                const void *queries_xy, int64_t m, double p,
+                                idw_precision prec, void *out, void *stream);
+
+/*
+ * `count` independent problems (Eq. 1 for each) in one persistent launch.
+ * The arrays of pointers and sizes are HOST arrays of length `count`; the
+ * pointers they hold are device pointers laid out as in idw_interpolate.
+ * Only IDW_PREC_F32_COMP is supported.  Instances with m_k = 0 are skipped.
+ */
+idw_status idw_interpolate_batched(idw_handle_t handle, int32_t count,
+                                   const void *const *data_xyz, const int64_t *n,
+                                   const void *const *queries_xy, const int64_t *m, double p,
+                                   idw_precision prec, void *const *out, void *stream);
+
+/*
+ * Adjoint of Eq. 1 for L = sum_j g_j Z(q_j) (F32 pair arithmetic with
+ * compensated accumulation, FP64 combine).  With S0 = sum_i w_i:
+ *   dL/dz_i = sum_j g_j w_ij / S0_j
+ *   dL/dx_i = sum_j g_j (p / S0_j) (z_i - Z_j) w_ij (q_j - x_i) / d_ij^2
+ *   dL/dq_j = -g_j (p / S0_j) sum_i (z_i - Z_j) w_ij (q_j - x_i) / d_ij^2
+ *   dL/dp   = -sum_j g_j / (2 S0_j) sum_i (z_i - Z_j) w_ij ln d_ij^2
+ * At an exact hit k of query j only dL/dz_k receives g_j.
+ *   data_xyz, queries_xy : device float, as in idw_interpolate.
+ *   Z, s0, hit           : device, m each: the outputs of
+ *                          idw_interpolate_saved for the same inputs.
+ *   grad_out             : device float, m: g_j.
+ *   grad_z (n), grad_data_xy (n x 2), grad_query_xy (m x 2) : device float,
+ *   grad_p (1) : device double; each nullable (NULL skips that gradient).
+ *   The gradient buffers are overwritten, not accumulated into.
+ */
+idw_status idw_backward(idw_handle_t handle, const float *data_xyz, int64_t n,
+                        const float *queries_xy, int64_t m, double p, const float *Z,
+                        const double *s0, const int32_t *hit, const float *grad_out,
+                        float *grad_z, float *grad_data_xy, float *grad_query_xy,
+                        double *grad_p, void *stream);
+
+/* Synchronises `stream`, then reports any pending CUDA error or a bounded
+ * in-kernel wait that gave up (IDW_ERR_DEVICE_TIMEOUT), and clears it. */
+idw_status idw_sync_status(idw_handle_t handle, void *stream);
+
+/*
+ * Host-only launch plan of the single-problem forward pass (no GPU needed).
+ * The data are cut into tiles of `records_per_tile` points and the queries
+ * into tiles of `queries_per_cta`; one work unit is one (query tile, data
+ * tile) pair, and each of `grid` persistent CTAs sweeps one contiguous run
+ * of floor(units * g / grid) .. floor(units * (g + 1) / grid) units.  A query
+ * tile split across several CTAs is summed by the FP64 combine; each
+ * (query tile, CTA) piece owns partial slot (query_tile + cta).
+ */
+typedef struct {
+    int32_t queries_per_thread;
+    int32_t threads_per_cta;
+    int32_t queries_per_cta;
+    int32_t records_per_tile;
+    int64_t query_tiles;
+    int64_t data_tiles;
+    int64_t units;
+    int32_t grid;
+    int32_t max_pieces_per_query_tile;
+    int64_t partial_slots;
+    size_t workspace_bytes;
+} idw_plan_info;
+
+/* Fills `plan` for `sm_count` SMs holding `ctas_per_sm` CTAs each
+ * (0 = the library's default for the precision). */
+idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, int64_t m,
+                            double p, idw_precision prec, idw_plan_info *plan);
+
+/*
+ * Kernel timing (tracing).  While enabled, every forward call records a pair
+ * of CUDA events around its all-pairs sweep kernel on the call's stream.
+ * idw_profile_read synchronises those events, returns the summed sweep time
+ * in milliseconds and the number of sweep launches, and clears the record.
+ */
+idw_status idw_profile_enable(idw_handle_t handle, int enable);
+idw_status idw_profile_read(idw_handle_t handle, double *sweep_ms, int64_t *launches);
+
+/*
+ * Failure-detection self-test: launches one CTA that waits, through the same
+ * bounded mbarrier wait the sweep kernels use, on a barrier that nothing
+ * completes.  After about two seconds the wait gives up and sets the
+ * handle's device error word, so the next idw_sync_status() returns
+ * IDW_ERR_DEVICE_TIMEOUT while the CUDA context stays usable.
+ */
+idw_status idw_selftest_bounded_wait(idw_handle_t handle, void *stream);
+
+/*
+ * Diagnostic: measures the issue rate of the arithmetic pipes the forward
+ * pass uses, in operations per SM per clock (from in-kernel clock counters,
+ * so independent of the clock speed).  rates[0..5] receive:
+ *   FFMA (fp32), FFMA2 (packed fp32x2, counted as 2 ops), MUFU rcp,
+ *   MUFU lg2, MUFU ex2, DFMA (fp64).
+ * Synchronous; runs for a few milliseconds on `device`.
+ */
+idw_status idw_measure_pipe_rates(int device, double rates[6]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDW_GB300_H */

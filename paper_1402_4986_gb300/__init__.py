@@ -1,0 +1,283 @@
+"""GB300 (sm_103a) global Shepard IDW interpolation.
+
+Thin Python binding over the C ABI of ``include/idw.h``: it checks tensor
+shapes, dtypes and devices, passes raw pointers and the current CUDA stream
+to the library, and wraps the results.  Every step of the computation runs
+in the library's CUDA kernels; PyTorch only provides device memory, streams
+and autograd plumbing.
+
+    Z(q) = sum_i w_i z_i / sum_i w_i,   w_i = d(q, x_i)^(-p)    (Eq. 1)
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _lib
+from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
+
+__all__ = [
+    "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
+    "interpolate_batched", "backward", "IDWFunction", "idw", "plan_forward",
+    "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
+    "selftest_bounded_wait", "PREC_F32_COMP", "PREC_F64_PLAIN",
+]
+
+_PREC = {"f32c": PREC_F32_COMP, "f32_comp": PREC_F32_COMP, PREC_F32_COMP: PREC_F32_COMP,
+         "f64": PREC_F64_PLAIN, "f64_plain": PREC_F64_PLAIN, PREC_F64_PLAIN: PREC_F64_PLAIN}
+_DTYPE = {PREC_F32_COMP: torch.float32, PREC_F64_PLAIN: torch.float64}
+
+
+class Handle:
+    """Owns one ``idw_handle_t`` (and its device workspace) on one device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = _lib.load()
+        self.device = int(device)
+        h = ctypes.c_void_p()
+        _lib.check(self.lib.idw_create(ctypes.byref(h), self.device), "idw_create")
+        self.ptr = h
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self.lib.idw_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_handles: dict = {}
+_hlock = threading.Lock()
+
+
+def get_handle(device=None) -> Handle:
+    """The process-wide handle of ``device`` (current device by default)."""
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    with _hlock:
+        if dev not in _handles:
+            _handles[dev] = Handle(dev)
+        return _handles[dev]
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _prec(precision):
+    try:
+        return _PREC[precision]
+    except KeyError:
+        raise ValueError(f"unknown precision {precision!r}") from None
+
+
+def _check_inputs(data, queries, prec):
+    dt = _DTYPE[prec]
+    if data.dim() != 2 or data.shape[1] != 3:
+        raise ValueError(f"data must be (n, 3) rows (x, y, z), got {tuple(data.shape)}")
+    if queries.dim() != 2 or queries.shape[1] != 2:
+        raise ValueError(f"queries must be (m, 2) rows (x, y), got {tuple(queries.shape)}")
+    for name, t in (("data", data), ("queries", queries)):
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt} for this precision, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if data.device != queries.device:
+        raise ValueError("data and queries must be on the same device")
+
+
+def interpolate_saved(data: torch.Tensor, queries: torch.Tensor, p: float = 2.0,
+                      precision="f32c", out=None, handle: Handle | None = None):
+    """Eq. 1 plus the state the adjoint needs.
+
+    Returns (Z, S0, hit): Z[m] (float32 or float64), S0[m] float64 (the
+    weight sum, +inf at an exact hit), hit[m] int32 (exact-hit index, -1, or
+    -2 where the query was recomputed in FP64).
+    """
+    prec = _prec(precision)
+    _check_inputs(data, queries, prec)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    s0 = torch.empty(m, dtype=torch.float64, device=data.device)
+    hit = torch.empty(m, dtype=torch.int32, device=data.device)
+    st = h.lib.idw_interpolate_saved(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m,
+                                     float(p), prec, _ptr(out), _ptr(s0), _ptr(hit),
+                                     _stream(data))
+    _lib.check(st, "idw_interpolate_saved", h.ptr)
+    return out, s0, hit
+
+
+def interpolate(data: torch.Tensor, queries: torch.Tensor, p: float = 2.0, precision="f32c",
+                out: torch.Tensor | None = None, handle: Handle | None = None) -> torch.Tensor:
+    """Eq. 1 for every query: data (n,3) rows (x,y,z), queries (m,2) rows (x,y).
+
+    ``precision`` is "f32c" (FP32 pair arithmetic, compensated sums, FP64
+    combine; float32 tensors) or "f64" (plain FP64; float64 tensors).
+    """
+    prec = _prec(precision)
+    _check_inputs(data, queries, prec)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    st = h.lib.idw_interpolate(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p), prec,
+                               _ptr(out), _stream(data))
+    _lib.check(st, "idw_interpolate", h.ptr)
+    return out
+
+
+def interpolate_host(data, queries, p: float = 2.0, precision="f32c", out=None,
+                     handle: Handle | None = None, stream=None):
+    """Eq. 1 on host (CPU) tensors: the library copies in, computes and copies out."""
+    prec = _prec(precision)
+    dt = _DTYPE[prec]
+    if data.device.type != "cpu" or queries.device.type != "cpu":
+        raise ValueError("interpolate_host takes host tensors")
+    if data.dtype != dt or queries.dtype != dt or not data.is_contiguous() or \
+            not queries.is_contiguous():
+        raise ValueError(f"host inputs must be contiguous {dt}")
+    m = queries.shape[0]
+    h = handle or get_handle()
+    if out is None:
+        out = torch.empty(m, dtype=dt, pin_memory=True)
+    s = stream if stream is not None else torch.cuda.current_stream(h.device)
+    st = h.lib.idw_interpolate_host(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p),
+                                    prec, _ptr(out), ctypes.c_void_p(s.cuda_stream))
+    _lib.check(st, "idw_interpolate_host", h.ptr)
+    return out
+
+
+def interpolate_batched(datas, queries_list, p: float = 2.0, outs=None,
+                        handle: Handle | None = None):
+    """Eq. 1 for many independent problems in one call (FP32-compensated)."""
+    k = len(datas)
+    if len(queries_list) != k:
+        raise ValueError("datas and queries_list differ in length")
+    if k == 0:
+        return []
+    for d, q in zip(datas, queries_list):
+        _check_inputs(d, q, PREC_F32_COMP)
+    if outs is None:
+        outs = [torch.empty(q.shape[0], dtype=torch.float32, device=q.device) for q in queries_list]
+    h = handle or get_handle(datas[0].device)
+    P = ctypes.c_void_p * k
+    I = ctypes.c_int64 * k
+    st = h.lib.idw_interpolate_batched(
+        h.ptr, k, P(*[d.data_ptr() for d in datas]), I(*[d.shape[0] for d in datas]),
+        P(*[q.data_ptr() for q in queries_list]), I(*[q.shape[0] for q in queries_list]),
+        float(p), PREC_F32_COMP, P(*[o.data_ptr() for o in outs]), _stream(datas[0]))
+    _lib.check(st, "idw_interpolate_batched", h.ptr)
+    return outs
+
+
+def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=True,
+             need_query_xy=True, need_p=True, handle: Handle | None = None):
+    """Adjoint of Eq. 1 (see include/idw.h); returns (gz, gxy, gq, gp)."""
+    _check_inputs(data, queries, PREC_F32_COMP)
+    n, m = data.shape[0], queries.shape[0]
+    dev = data.device
+    gz = torch.empty(n, dtype=torch.float32, device=dev) if need_z else None
+    gxy = torch.empty(n, 2, dtype=torch.float32, device=dev) if need_data_xy else None
+    gq = torch.empty(m, 2, dtype=torch.float32, device=dev) if need_query_xy else None
+    gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
+    h = handle or get_handle(dev)
+    g = grad_out.contiguous().to(torch.float32)
+    st = h.lib.idw_backward(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), _ptr(Z), _ptr(s0),
+                            _ptr(hit), _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp),
+                            _stream(data))
+    _lib.check(st, "idw_backward", h.ptr)
+    return gz, gxy, gq, gp
+
+
+class IDWFunction(torch.autograd.Function):
+    """Differentiable Eq. 1 (FP32-compensated) with the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, data, queries, p):
+        pv = float(p.item()) if torch.is_tensor(p) else float(p)
+        Z, s0, hit = interpolate_saved(data.detach().contiguous(), queries.detach().contiguous(),
+                                       pv, "f32c")
+        ctx.save_for_backward(data, queries, Z, s0, hit)
+        ctx.p = pv
+        ctx.p_is_tensor = torch.is_tensor(p)
+        return Z
+
+    @staticmethod
+    def backward(ctx, grad):
+        data, queries, Z, s0, hit = ctx.saved_tensors
+        need_d, need_q, need_p = ctx.needs_input_grad
+        gz, gxy, gq, gp = backward(data.detach().contiguous(), queries.detach().contiguous(),
+                                   ctx.p, Z, s0, hit, grad, need_z=need_d, need_data_xy=need_d,
+                                   need_query_xy=need_q, need_p=need_p and ctx.p_is_tensor)
+        gdata = torch.cat([gxy, gz[:, None]], 1) if need_d else None
+        gp_out = gp.to(torch.float32).reshape(()) if (need_p and ctx.p_is_tensor) else None
+        return gdata, gq if need_q else None, gp_out
+
+
+def idw(data, queries, p=2.0):
+    """Autograd entry: Z = IDW(data, queries, p); p may be a tensor to get dL/dp."""
+    return IDWFunction.apply(data, queries, p)
+
+
+def sync_status(device=None, handle: Handle | None = None):
+    """Synchronise the current stream and raise on a pending device error."""
+    h = handle or get_handle(device)
+    s = torch.cuda.current_stream(h.device)
+    _lib.check(h.lib.idw_sync_status(h.ptr, ctypes.c_void_p(s.cuda_stream)), "idw_sync_status",
+               h.ptr)
+
+
+def profile_enable(enable: bool = True, handle: Handle | None = None):
+    """Record CUDA events around every all-pairs sweep launch of the handle."""
+    h = handle or get_handle()
+    _lib.check(h.lib.idw_profile_enable(h.ptr, int(bool(enable))), "idw_profile_enable")
+
+
+def profile_read(handle: Handle | None = None):
+    """(total sweep milliseconds, sweep launches) since the last read."""
+    h = handle or get_handle()
+    ms = ctypes.c_double()
+    k = ctypes.c_int64()
+    _lib.check(h.lib.idw_profile_read(h.ptr, ctypes.byref(ms), ctypes.byref(k)),
+               "idw_profile_read", h.ptr)
+    return ms.value, k.value
+
+
+def selftest_bounded_wait(handle: Handle | None = None):
+    """Launch the bounded-wait self-test (see include/idw.h); check with sync_status()."""
+    h = handle or get_handle()
+    s = torch.cuda.current_stream(h.device)
+    _lib.check(h.lib.idw_selftest_bounded_wait(h.ptr, ctypes.c_void_p(s.cuda_stream)),
+               "idw_selftest_bounded_wait", h.ptr)
+
+
+def plan_forward(n: int, m: int, p: float = 2.0, precision="f32c", sm_count: int = 152,
+                 ctas_per_sm: int = 0) -> dict:
+    """Host-only launch plan of the forward pass (no GPU needed)."""
+    lib = _lib.load()
+    info = PlanInfo()
+    _lib.check(lib.idw_plan_forward(sm_count, ctas_per_sm, int(n), int(m), float(p),
+                                    _prec(precision), ctypes.byref(info)), "idw_plan_forward")
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
+
+
+def measure_pipe_rates(device: int = 0) -> dict:
+    """Arithmetic-pipe issue rates in ops per SM per clock (see include/idw.h)."""
+    lib = _lib.load()
+    arr = (ctypes.c_double * 6)()
+    _lib.check(lib.idw_measure_pipe_rates(int(device), arr), "idw_measure_pipe_rates")
+    keys = ("ffma", "ffma2", "mufu_rcp", "mufu_lg2", "mufu_ex2", "dfma")
+    return dict(zip(keys, list(arr)))

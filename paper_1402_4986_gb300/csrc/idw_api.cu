@@ -1,0 +1,386 @@
+// C ABI of the IDW library (declared in include/idw.h): argument checks,
+// launch planning, workspace ownership and the host-buffer path.  Every
+// step of the computation runs in the kernels of the other translation
+// units; this file only validates, plans and enqueues.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "idw.h"
+#include "idw_device.cuh"
+#include "idw_internal.h"
+
+struct idw_handle_s {
+  int device = 0;
+  int sm_count = 0;
+  void* ws = nullptr;  // device workspace (staged tiles, partials, flag list)
+  size_t ws_bytes = 0;
+  void* io = nullptr;  // device buffers of the host-pointer entry point
+  size_t io_bytes = 0;
+  idw::Control* ctrl = nullptr;  // device control words
+  int occ_f32_pow2 = 0, occ_f32_general = 0, occ_f64 = 0;
+  char last_cuda[256] = "no error";
+  bool profiling = false;
+  std::vector<idw::SweepEvents> events;  // recorded sweep launches, oldest first
+  size_t events_used = 0;
+};
+
+namespace {
+
+using idw::Plan;
+
+constexpr int64_t kMaxCount = int64_t(1) << 31;
+
+inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Makes the handle's device current for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+idw_status cuda_fail(idw_handle_t h, cudaError_t e) {
+  if (h) {
+    std::snprintf(h->last_cuda, sizeof(h->last_cuda), "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+  }
+  return IDW_ERR_CUDA;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Launch plan of the single-problem forward pass (host arithmetic only).
+void make_plan(int sm_count, int ctas_per_sm, int64_t n, int64_t m, idw_precision prec,
+               Plan* pl) {
+  const bool f32 = prec == IDW_PREC_F32_COMP;
+  pl->threads = f32 ? idw::kThreadsF32 : idw::kThreadsF64;
+  pl->queries_per_cta = f32 ? idw::kQueriesPerCtaF32 : idw::kQueriesPerCtaF64;
+  pl->records_per_tile = f32 ? idw::kRecordsF32 : idw::kRecordsF64;
+  pl->query_tiles = (m + pl->queries_per_cta - 1) / pl->queries_per_cta;
+  pl->data_tiles = (n + pl->records_per_tile - 1) / pl->records_per_tile;
+  pl->units = pl->query_tiles * pl->data_tiles;
+  const int64_t resident = int64_t(sm_count) * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+  pl->grid = static_cast<int>(pl->units < resident ? (pl->units > 0 ? pl->units : 1) : resident);
+  pl->partial_slots = pl->query_tiles + pl->grid - 1;
+  // Upper bound on CTAs sharing one query tile; exact value by idw_plan_forward.
+  pl->max_pieces = static_cast<int>(
+      pl->units > 0 ? ((pl->data_tiles - 1) * pl->grid) / pl->units + 2 : 0);
+  const size_t tile_bytes = f32 ? idw::kTileBytesF32 : idw::kTileBytesF64;
+  pl->staged_bytes = round_up(size_t(pl->data_tiles) * tile_bytes, 256);
+  pl->partial_bytes = round_up(size_t(pl->partial_slots) * pl->queries_per_cta * 16, 256);
+  pl->list_bytes = round_up(size_t(m > 0 ? m : 1) * sizeof(int32_t), 256);
+  pl->workspace_bytes = pl->staged_bytes + pl->partial_bytes + pl->list_bytes;
+}
+
+idw_status ensure_buffer(idw_handle_t h, void** buf, size_t* have, size_t need) {
+  if (need <= *have) return IDW_OK;
+  if (*buf) {
+    cudaError_t e = cudaFree(*buf);  // synchronises: earlier work may still use it
+    *buf = nullptr;
+    *have = 0;
+    if (e != cudaSuccess) return cuda_fail(h, e);
+  }
+  const size_t bytes = round_up(need + need / 4, size_t(1) << 20);
+  cudaError_t e = cudaMalloc(buf, bytes);
+  if (e != cudaSuccess) {
+    *buf = nullptr;
+    cuda_fail(h, e);
+    return IDW_ERR_WORKSPACE;
+  }
+  *have = bytes;
+  return IDW_OK;
+}
+
+// Event pair for the next sweep launch, or nullptr when timing is off.
+const idw::SweepEvents* next_events(idw_handle_t h) {
+  if (!h->profiling) return nullptr;
+  if (h->events_used == h->events.size()) {
+    idw::SweepEvents ev;
+    if (cudaEventCreate(&ev.start) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&ev.stop) != cudaSuccess) {
+      cudaEventDestroy(ev.start);
+      return nullptr;
+    }
+    h->events.push_back(ev);
+  }
+  return &h->events[h->events_used++];
+}
+
+void destroy_events(idw_handle_t h) {
+  for (auto& ev : h->events) {
+    cudaEventDestroy(ev.start);
+    cudaEventDestroy(ev.stop);
+  }
+  h->events.clear();
+  h->events_used = 0;
+}
+
+int ctas_per_sm(idw_handle_t h, idw_precision prec, double p) {
+  if (prec == IDW_PREC_F64_PLAIN) {
+    if (!h->occ_f64) h->occ_f64 = idw::occupancy_forward_f64();
+    return h->occ_f64;
+  }
+  if (p == 2.0) {
+    if (!h->occ_f32_pow2) h->occ_f32_pow2 = idw::occupancy_forward_f32(false);
+    return h->occ_f32_pow2;
+  }
+  if (!h->occ_f32_general) h->occ_f32_general = idw::occupancy_forward_f32(true);
+  return h->occ_f32_general;
+}
+
+idw_status check_common(idw_handle_t h, const void* data, int64_t n, const void* queries,
+                        int64_t m, double p, idw_precision prec, const void* out) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  if (prec != IDW_PREC_F32_COMP && prec != IDW_PREC_F64_PLAIN) return IDW_ERR_INVALID_ARG;
+  if (n < 1 || n >= kMaxCount || m < 0 || m >= kMaxCount) return IDW_ERR_INVALID_ARG;
+  if (!(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (!data || !queries || !out) return IDW_ERR_INVALID_ARG;
+  const size_t es = prec == IDW_PREC_F32_COMP ? 4 : 8;
+  if (!aligned(data, es) || !aligned(queries, es) || !aligned(out, es)) return IDW_ERR_ALIGNMENT;
+  return IDW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* idw_status_string(idw_status s) {
+  switch (s) {
+    case IDW_OK: return "IDW_OK";
+    case IDW_ERR_INVALID_ARG: return "IDW_ERR_INVALID_ARG";
+    case IDW_ERR_ALIGNMENT: return "IDW_ERR_ALIGNMENT";
+    case IDW_ERR_CUDA: return "IDW_ERR_CUDA";
+    case IDW_ERR_NOT_FINITE_INPUT: return "IDW_ERR_NOT_FINITE_INPUT";
+    case IDW_ERR_WORKSPACE: return "IDW_ERR_WORKSPACE";
+    case IDW_ERR_UNSUPPORTED: return "IDW_ERR_UNSUPPORTED";
+    case IDW_ERR_DEVICE_TIMEOUT: return "IDW_ERR_DEVICE_TIMEOUT";
+  }
+  return "IDW_ERR_UNKNOWN";
+}
+
+idw_status idw_create(idw_handle_t* out, int device) {
+  if (!out) return IDW_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return IDW_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return IDW_ERR_UNSUPPORTED;
+  idw_handle_t h = new idw_handle_s();
+  h->device = device;
+  h->sm_count = prop.multiProcessorCount;
+  cudaError_t e = cudaMalloc(&h->ctrl, sizeof(idw::Control));
+  if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(idw::Control));
+  if (e != cudaSuccess) {
+    if (h->ctrl) cudaFree(h->ctrl);
+    delete h;
+    return IDW_ERR_CUDA;
+  }
+  *out = h;
+  return IDW_OK;
+}
+
+idw_status idw_destroy(idw_handle_t h) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  cudaDeviceSynchronize();
+  if (h->ws) cudaFree(h->ws);
+  if (h->io) cudaFree(h->io);
+  if (h->ctrl) cudaFree(h->ctrl);
+  destroy_events(h);
+  delete h;
+  return IDW_OK;
+}
+
+const char* idw_last_cuda_error(idw_handle_t h) { return h ? h->last_cuda : "null handle"; }
+
+idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, const void* queries,
+                                 int64_t m, double p, idw_precision prec, void* out,
+                                 double* s0_out, int32_t* hit_out, void* stream) {
+  idw_status st = check_common(h, data, n, queries, m, p, prec, out);
+  if (st != IDW_OK || m == 0) return st;
+  if (!aligned(s0_out, 8) || !aligned(hit_out, 4)) return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  Plan plan;
+  make_plan(h->sm_count, ctas_per_sm(h, prec, p), n, m, prec, &plan);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, plan.workspace_bytes);
+  if (st != IDW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (prec == IDW_PREC_F32_COMP) {
+    idw::F32Problem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m,
+                       p, static_cast<float*>(out), s0_out, hit_out};
+    e = idw::launch_forward_f32(pb, plan, h->ws, h->ctrl, h->sm_count, next_events(h), s);
+  } else {
+    idw::F64Problem pb{static_cast<const double*>(data), n, static_cast<const double*>(queries), m,
+                       p, static_cast<double*>(out), s0_out, hit_out};
+    e = idw::launch_forward_f64(pb, plan, h->ws, h->ctrl, h->sm_count, next_events(h), s);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return IDW_OK;
+}
+
+idw_status idw_interpolate(idw_handle_t h, const void* data, int64_t n, const void* queries,
+                           int64_t m, double p, idw_precision prec, void* out, void* stream) {
+  return idw_interpolate_saved(h, data, n, queries, m, p, prec, out, nullptr, nullptr, stream);
+}
+
+idw_status idw_interpolate_host(idw_handle_t h, const void* data, int64_t n, const void* queries,
+                                int64_t m, double p, idw_precision prec, void* out, void* stream) {
+  idw_status st = check_common(h, data, n, queries, m, p, prec, out);
+  if (st != IDW_OK || m == 0) return st;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const size_t es = prec == IDW_PREC_F32_COMP ? 4 : 8;
+  const size_t db = round_up(size_t(n) * 3 * es, 256), qb = round_up(size_t(m) * 2 * es, 256);
+  const size_t ob = round_up(size_t(m) * es, 256);
+  st = ensure_buffer(h, &h->io, &h->io_bytes, db + qb + ob);
+  if (st != IDW_OK) return st;
+  unsigned char* io = static_cast<unsigned char*>(h->io);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(io, data, size_t(n) * 3 * es, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(io + db, queries, size_t(m) * 2 * es, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  st = idw_interpolate_saved(h, io, n, io + db, m, p, prec, io + db + qb, nullptr, nullptr, stream);
+  if (st != IDW_OK) return st;
+  e = cudaMemcpyAsync(out, io + db + qb, size_t(m) * es, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return IDW_OK;
+}
+
+idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* const* data,
+                                   const int64_t* n, const void* const* queries, const int64_t* m,
+                                   double p, idw_precision prec, void* const* out, void* stream) {
+  if (!h || count < 0 || (count > 0 && (!data || !n || !queries || !m || !out)))
+    return IDW_ERR_INVALID_ARG;
+  if (prec != IDW_PREC_F32_COMP) return IDW_ERR_UNSUPPORTED;
+  for (int32_t k = 0; k < count; ++k) {
+    idw_status st = check_common(h, data[k], n[k], queries[k], m[k], p, prec, out[k]);
+    if (st != IDW_OK) return st;
+  }
+  for (int32_t k = 0; k < count; ++k) {
+    idw_status st = idw_interpolate(h, data[k], n[k], queries[k], m[k], p, prec, out[k], stream);
+    if (st != IDW_OK) return st;
+  }
+  return IDW_OK;
+}
+
+idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const float* queries,
+                        int64_t m, double p, const float* Z, const double* s0, const int32_t* hit,
+                        const float* grad_out, float* grad_z, float* grad_data_xy,
+                        float* grad_query_xy, double* grad_p, void* stream) {
+  (void)data; (void)n; (void)queries; (void)m; (void)p; (void)Z; (void)s0; (void)hit;
+  (void)grad_out; (void)grad_z; (void)grad_data_xy; (void)grad_query_xy; (void)grad_p;
+  (void)stream;
+  return h ? IDW_ERR_UNSUPPORTED : IDW_ERR_INVALID_ARG;
+}
+
+idw_status idw_sync_status(idw_handle_t h, void* stream) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  idw::Control c;
+  e = cudaMemcpy(&c, h->ctrl, sizeof(c), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (c.error != 0) {
+    cudaMemset(&h->ctrl->error, 0, sizeof(unsigned));
+    return IDW_ERR_DEVICE_TIMEOUT;
+  }
+  return IDW_OK;
+}
+
+idw_status idw_profile_enable(idw_handle_t h, int enable) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  h->profiling = enable != 0;
+  return IDW_OK;
+}
+
+idw_status idw_profile_read(idw_handle_t h, double* sweep_ms, int64_t* launches) {
+  if (!h || !sweep_ms || !launches) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  double total = 0.0;
+  for (size_t k = 0; k < h->events_used; ++k) {
+    cudaError_t e = cudaEventSynchronize(h->events[k].stop);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->events[k].start, h->events[k].stop);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    total += ms;
+  }
+  *sweep_ms = total;
+  *launches = static_cast<int64_t>(h->events_used);
+  h->events_used = 0;
+  return IDW_OK;
+}
+
+idw_status idw_selftest_bounded_wait(idw_handle_t h, void* stream) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  cudaError_t e = idw::launch_bounded_wait_selftest(h->ctrl, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+idw_status idw_plan_forward(int32_t sm_count, int32_t ctas, int64_t n, int64_t m, double p,
+                            idw_precision prec, idw_plan_info* out) {
+  if (!out || sm_count < 1 || ctas < 0 || n < 1 || n >= kMaxCount || m < 0 || m >= kMaxCount)
+    return IDW_ERR_INVALID_ARG;
+  if (!(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
+  if (prec != IDW_PREC_F32_COMP && prec != IDW_PREC_F64_PLAIN) return IDW_ERR_INVALID_ARG;
+  if (ctas == 0) ctas = prec == IDW_PREC_F32_COMP ? 2 : 4;
+  Plan pl;
+  make_plan(sm_count, ctas, n, m, prec, &pl);
+  int max_pieces = 0;
+  for (int64_t qt = 0; qt < pl.query_tiles; ++qt) {
+    const int64_t g0 = idw::cta_of_unit(qt * pl.data_tiles, pl.units, pl.grid);
+    const int64_t g1 = idw::cta_of_unit((qt + 1) * pl.data_tiles - 1, pl.units, pl.grid);
+    if (g1 - g0 + 1 > max_pieces) max_pieces = static_cast<int>(g1 - g0 + 1);
+  }
+  out->queries_per_thread = pl.queries_per_cta / pl.threads;
+  out->threads_per_cta = pl.threads;
+  out->queries_per_cta = pl.queries_per_cta;
+  out->records_per_tile = pl.records_per_tile;
+  out->query_tiles = pl.query_tiles;
+  out->data_tiles = pl.data_tiles;
+  out->units = pl.units;
+  out->grid = pl.grid;
+  out->max_pieces_per_query_tile = max_pieces;
+  out->partial_slots = pl.partial_slots;
+  out->workspace_bytes = pl.workspace_bytes;
+  return IDW_OK;
+}
+
+idw_status idw_measure_pipe_rates(int device, double rates[6]) {
+  if (!rates) return IDW_ERR_INVALID_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return IDW_ERR_CUDA;
+  cudaError_t e = idw::measure_pipe_rates(sms, rates);
+  return e == cudaSuccess ? IDW_OK : IDW_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Internal declarations shared by the kernel translation units and the C ABI
+// layer.  Not installed; the public interface is include/idw.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace idw {
+
+// ---------------------------------------------------------------- tiling
+// FP32-compensated forward: each thread holds kQueryPairs pairs of queries;
+// a data tile of kRecordsF32 points is staged as (x,x,y,y) + (z,z) records.
+constexpr int kThreadsF32 = 256;
+constexpr int kQueryPairsF32 = 4;
+constexpr int kQueriesPerCtaF32 = kThreadsF32 * 2 * kQueryPairsF32;  // 2048
+constexpr int kRecordsF32 = 256;
+constexpr int kStagesF32 = 3;
+constexpr int kChunkF32 = 16;
+constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 8 B (z,z)
+
+// Plain FP64 forward: kQueriesF64 queries per thread; tiles of (x,y) + z.
+constexpr int kThreadsF64 = 128;
+constexpr int kQueriesF64 = 8;
+constexpr int kQueriesPerCtaF64 = kThreadsF64 * kQueriesF64;  // 1024
+constexpr int kRecordsF64 = 128;
+constexpr int kStagesF64 = 3;
+constexpr size_t kTileBytesF64 = size_t(kRecordsF64) * 24;  // 16 B (x,y) + 8 B z
+
+// Queries whose FP32 weight sum falls below n * 2^-100 are recomputed in
+// FP64: below that, weights flushed to zero could matter.
+constexpr double kTinySumPerPoint = 7.888609052210118e-31;  // 2^-100
+
+// Hit codes written by the combine / slow path.
+constexpr int32_t kNoHit = -1;
+constexpr int32_t kRecomputedF64 = -2;
+
+// Device control words owned by a handle.
+struct Control {
+  unsigned flagged;  // number of queries routed to the slow path this call
+  unsigned error;    // sticky error bits (kErrWaitTimeout, ...)
+};
+
+enum WeightMode : int { kPow2 = 0, kPowGeneral = 1 };
+
+struct Plan {
+  int threads, queries_per_cta, records_per_tile;
+  int64_t query_tiles, data_tiles, units;
+  int grid;
+  int max_pieces;
+  int64_t partial_slots;
+  size_t staged_bytes, partial_bytes, list_bytes, workspace_bytes;
+};
+
+// ----------------------------------------------------------- launchers
+// All launchers enqueue on `stream` and return cudaGetLastError().
+
+// FP32-compensated single-problem forward.
+struct F32Problem {
+  const float* data;     // n x 3
+  int64_t n;
+  const float* queries;  // m x 2
+  int64_t m;
+  double p;
+  float* out;
+  double* s0_out;   // nullable
+  int32_t* hit_out; // nullable
+};
+// Optional events recorded around the all-pairs sweep kernel.
+struct SweepEvents {
+  cudaEvent_t start = nullptr, stop = nullptr;
+};
+
+cudaError_t launch_forward_f32(const F32Problem& pb, const Plan& plan, void* workspace,
+                               Control* ctrl, int sm_count, const SweepEvents* ev,
+                               cudaStream_t stream);
+int occupancy_forward_f32(bool general_p);
+
+// Plain FP64 single-problem forward.
+struct F64Problem {
+  const double* data;
+  int64_t n;
+  const double* queries;
+  int64_t m;
+  double p;
+  double* out;
+  double* s0_out;
+  int32_t* hit_out;
+};
+cudaError_t launch_forward_f64(const F64Problem& pb, const Plan& plan, void* workspace,
+                               Control* ctrl, int sm_count, const SweepEvents* ev,
+                               cudaStream_t stream);
+int occupancy_forward_f64();
+
+// Failure-detection self-test: a bounded wait on a barrier nobody completes.
+cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream);
+
+// Pipe-rate probe: returns ops per SM per clock for the 6 probed pipes.
+cudaError_t measure_pipe_rates(int sm_count, double rates[6]);
+
+}  // namespace idw
