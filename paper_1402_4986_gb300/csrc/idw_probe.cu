@@ -46,15 +46,16 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seed, ProbeO
   __syncthreads();
   const unsigned long long t0 = clock64();
 #pragma unroll 1
-  for (int it = 0; it < kProbeIters; ++it) {
+  for (int it = 0; it < kProbeIters; it += 4) {
 #pragma unroll
-    for (int c = 0; c < kChains; ++c) {
-      if (OP == kOpFfma) v[c] = fmaf(v[c], 0.999f, 0.001f);
-      if (OP == kOpFfma2) pv[c] = fma2(pv[c], a2, b2);
-      if (OP == kOpRcp) v[c] = rcp_approx(v[c]);
-      if (OP == kOpLg2) v[c] = lg2_approx(v[c]) + 2.f;   // fixed point 4
-      if (OP == kOpEx2) v[c] = ex2_approx(v[c]) * -0.5f; // bounded orbit
-      if (OP == kOpDfma) dv[c] = fma(dv[c], 0.999, 0.001);
+    for (int c = 0; c < 4 * kChains; ++c) {
+      const int k = c % kChains;  // four rounds per loop trip: little loop overhead
+      if (OP == kOpFfma) v[k] = fmaf(v[k], 0.999f, 0.001f);
+      if (OP == kOpFfma2) pv[k] = fma2(pv[k], a2, b2);
+      if (OP == kOpRcp) v[k] = rcp_approx(v[k]) + 0.5f;  // fixed point 1.28
+      if (OP == kOpLg2) v[k] = lg2_approx(v[k]) + 2.f;   // fixed point 4
+      if (OP == kOpEx2) v[k] = ex2_approx(v[k]) * -0.5f; // bounded orbit
+      if (OP == kOpDfma) dv[k] = fma(dv[k], 0.999, 0.001);
     }
   }
   __syncthreads();
