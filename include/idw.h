@@ -204,6 +204,41 @@ idw_status idw_selftest_bounded_wait(idw_handle_t handle, void *stream);
  */
 idw_status idw_measure_pipe_rates(int device, double rates[6]);
 
+/*
+ * Allocation-free FP32-compensated interpolation.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory:
+ * a host application that owns the whole device-memory budget and does not
+ * let its plug-ins allocate, or a latency-critical loop that cannot afford
+ * cudaMalloc/cudaFree (both synchronise the device).  Such callers cannot
+ * create a handle either, because idw_create allocates, so this call takes
+ * none.  It computes what idw_interpolate computes with IDW_PREC_F32_COMP,
+ * with the same kernels, on the CURRENT device.
+ *
+ *   data_xyz, queries_xy, out : device float arrays laid out as in
+ *                               idw_interpolate (caller-owned, 4-byte aligned).
+ *   stream                    : cudaStream_t as void* (NULL = legacy stream).
+ *
+ * Scratch: instead of a workspace it uses one fixed 32 MiB device array
+ * that every GPU loading the library holds until the process exits.  It
+ * never calls cudaMalloc, cudaFree or any allocating routine.  A problem
+ * whose scratch (about 24 bytes per data point, 4 bytes per query, plus
+ * 32 KiB per query tile and per persistent CTA) exceeds the array is
+ * rejected with IDW_ERR_WORKSPACE before anything is launched; on a 152-SM
+ * GB300, n = m = 262144 fits.
+ *
+ * The first call on a device sets that device up (it looks up the array's
+ * device address and clears its control words), so make that first call
+ * before any stream capture.  Every call shares the one array and it keeps
+ * the last call's contents; each call clears what must start at zero.  Calls
+ * whose work overlaps on the GPU (different streams, or concurrent host
+ * threads) race on the array: order them on one stream.  Returns
+ * IDW_ERR_INVALID_ARG, IDW_ERR_ALIGNMENT, IDW_ERR_UNSUPPORTED (not
+ * compute capability 10.3), IDW_ERR_WORKSPACE (too large) or
+ * IDW_ERR_CUDA; the kernels run asynchronously after it returns.
+ */
+idw_status idw_interpolate_noalloc(const float *data_xyz, int64_t n, const float *queries_xy,
+                                   int64_t m, double p, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,8 @@ SIGNATURES = {
     "idw_profile_enable": (c_int, [c_void_p, c_int]),
     "idw_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "idw_selftest_bounded_wait": (c_int, [c_void_p, c_void_p]),
+    "idw_interpolate_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_void_p,
+                                        c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -1,0 +1,119 @@
+// Allocation-free variant of the FP32-compensated forward pass.
+//
+// Some callers cannot allocate device memory: a host application that owns
+// the whole device-memory budget and forbids its plug-ins to allocate, or a
+// latency-critical loop that cannot afford cudaMalloc/cudaFree, which
+// synchronise the device.  Such callers cannot create a handle either
+// (idw_create allocates), so this entry point takes none.  Its scratch (the
+// staged data tiles, the per-piece partial sums, the list of queries routed
+// to the slow path and the control words) lives in one file-scope device
+// array of fixed size; the caller still passes the inputs and the output.
+//
+// The array name below is a host-side stand-in in host code, not a device
+// address: set-up asks the runtime for the real address once per device,
+// with that device current, and passes that address to the kernels.
+#include <cmath>
+#include <cstdint>
+#include <mutex>
+
+#include "idw.h"
+#include "idw_internal.h"
+
+namespace idw {
+namespace {
+
+// 32 MiB of scratch, held by every GPU that loads this module until exit.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+constexpr size_t kControlBytes = 256;  // Control words, padded to keep alignment
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceSetup {
+  bool ready = false;
+  unsigned char* scratch = nullptr;  // device address of g_noalloc_scratch
+  int sm_count = 0;
+  int occ_pow2 = 0;
+  int occ_general = 0;
+};
+
+std::mutex g_setup_mutex;
+DeviceSetup g_setup[kMaxDevices];
+
+// Once per device, with that device current: resolve the array's device
+// address, query the SM count and occupancy, and zero the control words.
+idw_status setup_current_device(DeviceSetup* out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return IDW_ERR_CUDA;
+  if (dev >= kMaxDevices) return IDW_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  DeviceSetup& s = g_setup[dev];
+  if (!s.ready) {
+    int major = 0, minor = 0;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+      return IDW_ERR_CUDA;
+    if (major != 10 || minor != 3) return IDW_ERR_UNSUPPORTED;
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || ptr == nullptr)
+      return IDW_ERR_CUDA;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return IDW_ERR_CUDA;
+    if (cudaMemset(ptr, 0, kControlBytes) != cudaSuccess) return IDW_ERR_CUDA;
+    s.scratch = static_cast<unsigned char*>(ptr);
+    s.sm_count = sms;
+    s.occ_pow2 = occupancy_forward_f32(false);
+    s.occ_general = occupancy_forward_f32(true);
+    s.ready = true;
+  }
+  *out = s;
+  return IDW_OK;
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+}  // namespace idw
+
+extern "C" idw_status idw_interpolate_noalloc(const float* data_xyz, int64_t n,
+                                              const float* queries_xy, int64_t m, double p,
+                                              float* out, void* stream) {
+  using namespace idw;
+  if (n < 1 || n >= (int64_t(1) << 31) || m < 0 || m >= (int64_t(1) << 31)) return IDW_ERR_INVALID_ARG;
+  if (!(p > 0.0) || !(p < INFINITY)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (!data_xyz || !queries_xy || !out) return IDW_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(data_xyz) | reinterpret_cast<uintptr_t>(queries_xy) |
+       reinterpret_cast<uintptr_t>(out)) % 4 != 0)
+    return IDW_ERR_ALIGNMENT;
+
+  DeviceSetup dev;
+  idw_status st = setup_current_device(&dev);
+  if (st != IDW_OK) return st;
+
+  // The same launch plan as idw_interpolate (host arithmetic only).
+  Plan pl;
+  pl.threads = kThreadsF32;
+  pl.queries_per_cta = kQueriesPerCtaF32;
+  pl.records_per_tile = kRecordsF32;
+  pl.query_tiles = (m + kQueriesPerCtaF32 - 1) / kQueriesPerCtaF32;
+  pl.data_tiles = (n + kRecordsF32 - 1) / kRecordsF32;
+  pl.units = pl.query_tiles * pl.data_tiles;
+  const int64_t resident = int64_t(dev.sm_count) * (p == 2.0 ? dev.occ_pow2 : dev.occ_general);
+  pl.grid = static_cast<int>(pl.units < resident ? pl.units : resident);
+  pl.partial_slots = pl.query_tiles + pl.grid - 1;
+  pl.max_pieces = 0;
+  pl.staged_bytes = round_up(size_t(pl.data_tiles) * kTileBytesF32, 256);
+  pl.partial_bytes = round_up(size_t(pl.partial_slots) * kQueriesPerCtaF32 * 16, 256);
+  pl.list_bytes = round_up(size_t(m) * sizeof(int32_t), 256);
+  pl.workspace_bytes = pl.staged_bytes + pl.partial_bytes + pl.list_bytes;
+  if (pl.workspace_bytes > kNoAllocScratchBytes - kControlBytes) return IDW_ERR_WORKSPACE;
+
+  Control* ctrl = reinterpret_cast<Control*>(dev.scratch);
+  F32Problem pb{data_xyz, n, queries_xy, m, p, out, nullptr, nullptr};
+  const cudaError_t e = launch_forward_f32(pb, pl, dev.scratch + kControlBytes, ctrl,
+                                           dev.sm_count, nullptr,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : IDW_ERR_CUDA;
+}
