@@ -311,7 +311,7 @@ def run_ours(args, ws, rank, local):
                                "FP32-compensated (FP64 combine)",
                    "n": n, "m": m, "p": 2.0, "parallelism": f"query shards x{ws}, data replicated",
                    "l2": "flushed between steps (256 MiB write; inputs are 36 MiB)"},
-        "e2e": e2e, "gpu_launches": 4 * args.steps,
+        "e2e": e2e, "gpu_launches": 5 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "error_vs_fp64_oracle": err,
         "f64_plain": {"value": f64_value, "unit": UNIT,

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "idw.h"
@@ -215,17 +216,21 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
   if (!aligned(s0_out, 8) || !aligned(hit_out, 4)) return IDW_ERR_ALIGNMENT;
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
-  Plan plan;
-  make_plan(h->sm_count, ctas_per_sm(h, prec, p), n, m, prec, &plan);
-  st = ensure_buffer(h, &h->ws, &h->ws_bytes, plan.workspace_bytes);
-  if (st != IDW_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
   if (prec == IDW_PREC_F32_COMP) {
     idw::F32Problem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m,
-                       p, static_cast<float*>(out), s0_out, hit_out};
-    e = idw::launch_forward_f32(pb, plan, h->ws, h->ctrl, h->sm_count, next_events(h), s);
+                       static_cast<float*>(out), s0_out, hit_out};
+    idw::BatchPlan bp;
+    idw::plan_batch_f32(&pb, 1, h->sm_count, ctas_per_sm(h, prec, p), &bp);
+    st = ensure_buffer(h, &h->ws, &h->ws_bytes, bp.workspace_bytes);
+    if (st != IDW_OK) return st;
+    e = idw::launch_batch_f32(&pb, bp, p, h->ws, h->ctrl, h->sm_count, next_events(h), s);
   } else {
+    Plan plan;
+    make_plan(h->sm_count, ctas_per_sm(h, prec, p), n, m, prec, &plan);
+    st = ensure_buffer(h, &h->ws, &h->ws_bytes, plan.workspace_bytes);
+    if (st != IDW_OK) return st;
     idw::F64Problem pb{static_cast<const double*>(data), n, static_cast<const double*>(queries), m,
                        p, static_cast<double*>(out), s0_out, hit_out};
     e = idw::launch_forward_f64(pb, plan, h->ws, h->ctrl, h->sm_count, next_events(h), s);
@@ -274,9 +279,35 @@ idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* co
     idw_status st = check_common(h, data[k], n[k], queries[k], m[k], p, prec, out[k]);
     if (st != IDW_OK) return st;
   }
+  // Problems with m = 0 have nothing to compute; the rest go in chunks of
+  // up to kBatchCap problems, one persistent launch per chunk.
+  std::vector<idw::F32Problem> probs;
+  probs.reserve(count);
   for (int32_t k = 0; k < count; ++k) {
-    idw_status st = idw_interpolate(h, data[k], n[k], queries[k], m[k], p, prec, out[k], stream);
-    if (st != IDW_OK) return st;
+    if (m[k] == 0) continue;
+    probs.push_back(idw::F32Problem{static_cast<const float*>(data[k]), n[k],
+                                    static_cast<const float*>(queries[k]), m[k],
+                                    static_cast<float*>(out[k]), nullptr, nullptr});
+  }
+  if (probs.empty()) return IDW_OK;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const int ctas = ctas_per_sm(h, prec, p);
+  std::vector<idw::BatchPlan> plans;
+  size_t need = 0;
+  for (size_t b = 0; b < probs.size(); b += idw::kBatchCap) {
+    const int c = static_cast<int>(std::min<size_t>(idw::kBatchCap, probs.size() - b));
+    plans.emplace_back();
+    idw::plan_batch_f32(&probs[b], c, h->sm_count, ctas, &plans.back());
+    need = std::max(need, plans.back().workspace_bytes);
+  }
+  idw_status st = ensure_buffer(h, &h->ws, &h->ws_bytes, need);
+  if (st != IDW_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (size_t c = 0; c < plans.size(); ++c) {
+    cudaError_t e = idw::launch_batch_f32(&probs[c * idw::kBatchCap], plans[c], p, h->ws, h->ctrl,
+                                          h->sm_count, next_events(h), s);
+    if (e != cudaSuccess) return cuda_fail(h, e);
   }
   return IDW_OK;
 }
@@ -349,6 +380,14 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas, int64_t n, int64_t m
   if (ctas == 0) ctas = prec == IDW_PREC_F32_COMP ? 2 : 4;
   Plan pl;
   make_plan(sm_count, ctas, n, m, prec, &pl);
+  if (prec == IDW_PREC_F32_COMP && m > 0) {
+    idw::F32Problem pb{nullptr, n, nullptr, m, nullptr, nullptr, nullptr};
+    idw::BatchPlan bp;
+    idw::plan_batch_f32(&pb, 1, sm_count, ctas, &bp);
+    pl.grid = bp.grid;
+    pl.partial_slots = bp.partial_slots;
+    pl.workspace_bytes = bp.workspace_bytes;
+  }
   int max_pieces = 0;
   for (int64_t qt = 0; qt < pl.query_tiles; ++qt) {
     const int64_t g0 = idw::cta_of_unit(qt * pl.data_tiles, pl.units, pl.grid);

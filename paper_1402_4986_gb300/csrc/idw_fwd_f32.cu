@@ -1,29 +1,37 @@
-// FP32-compensated forward pass of global Shepard IDW (Sec. 2.1, Eq. 1).
+// FP32-compensated forward pass of global Shepard IDW (Sec. 2.1, Eq. 1),
+// for one problem or a batch of independent problems in one launch.
 //
-// Pipeline (one call): stage data -> persistent all-pairs sweep -> FP64
-// combine -> FP64 slow path for flagged queries.
+// Pipeline (one call): coordinate range scan -> staging -> persistent
+// all-pairs sweep -> FP64 combine -> FP64 slow path for flagged queries.
 //
-// The sweep is the paper's tiled kernel (Sec. 4.2: a block loads a tile of
-// data points into shared memory and every thread sweeps it) rebuilt for
-// sm_103a:
+// The sweep is the paper's tiled kernel (Sec. 4.2: the data are read once
+// per block of prediction points, tile by tile) rebuilt for sm_103a:
 //   * each thread holds 2*kQueryPairsF32 queries in registers as pairs, so
 //     every FP32 operation is a packed fp32x2 instruction over two queries;
 //   * data tiles stream global -> shared by 1-D bulk TMA into a ring of
-//     stages guarded by mbarriers (bounded waits), and every warp reads the
-//     same record (a broadcast shared load);
+//     stages guarded by mbarriers (bounded waits); every warp reads the same
+//     record (a broadcast shared load);
 //   * the record is staged pre-duplicated as (x,x,y,y)+(z,z) so it feeds the
 //     packed instructions with no register moves (the paper's aligned AoS
 //     record, Sec. 3.3, widened for pair arithmetic);
-//   * w = d^-p without a square root: p = 2 is one MUFU reciprocal of d^2;
-//     general p is 2^(-(p/2) log2 d^2) with the product's rounding error
+//   * w = d^-p without a square root.  p = 2: one MUFU reciprocal of d^2,
+//     except that for one of the query pairs the two pairs share one
+//     reciprocal, 1/(da db), and recover 1/da = db/(da db) with two FMULs;
+//     this moves work from the MUFU pipe (the binding one) to the FMA pipe.
+//     General p: 2^(-(p/2) log2 d^2) with the product's rounding error
 //     recovered by an FMA and applied to first order;
-//   * sums run in chunks of kChunkF32 points, and each chunk sum is folded
-//     into (hi, lo) pairs by Knuth's TwoSum, so the rounding error does not
-//     grow with n;
-//   * the (query tile, data tile) work units are split evenly over a grid of
-//     co-resident CTAs (stream-K); pieces of a query tile are summed in FP64
-//     by the combine, which plays the role of the paper's in-block
-//     reduction of the improved CDP kernel (Sec. 3.1).
+//   * sums run in chunks of kChunkF32 points; each chunk sum is folded into
+//     (hi, lo) pairs by Knuth's TwoSum, so the error does not grow with n;
+//   * the (problem, query tile, data tile) work units are split evenly over
+//     a grid of co-resident CTAs (stream-K).  Pieces of a query tile are
+//     summed in FP64 by the combine, which plays the role of the paper's
+//     in-block reduction of the improved CDP kernel (Sec. 3.1).
+//   * coordinates are multiplied by a power of two per problem (exact in
+//     FP32) so the largest magnitude lies in [2^9, 2^10): Eq. 1 depends only
+//     on distance ratios, so Z is unchanged, and products of squared
+//     distances cannot overflow.
+#include <algorithm>
+#include <cfloat>
 #include <cmath>
 
 #include "idw_device.cuh"
@@ -39,67 +47,179 @@ constexpr int QT = kQueriesPerCtaF32;
 constexpr int TB = kRecordsF32;
 constexpr int ST = kStagesF32;
 constexpr int CH = kChunkF32;
+constexpr int KSHARED = 1;  // query pairs per thread that share one reciprocal (p = 2)
 constexpr uint32_t kTileBytes = static_cast<uint32_t>(kTileBytesF32);
 static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 static_assert(TB % CH == 0, "chunks tile the data tile");
+static_assert(KSHARED <= KP, "shared-reciprocal pairs are a subset of the query pairs");
 
-struct FwdArgs {
-  const unsigned char* tiles;  // data_tiles x kTileBytes
-  const float* queries;        // m x 2
-  int64_t m;
-  int64_t data_tiles;
+// Padding records of the p = 2 form sit at (2^63, 2^63): for any query with
+// |coordinate| <= 2^10, d^2 = 2^127, whose reciprocal is subnormal and
+// flushes to 0, and the shared product overflows to +inf, whose reciprocal
+// is 0.  The general form pads at +inf (its log2 is clamped).
+constexpr float kPadPow2 = 9.223372036854775808e18f;  // 2^63
+
+struct Instance {
+  const float* data;     // n x 3 rows (caller)
+  const float* queries;  // m x 2 rows (caller)
+  float* out;
+  double* s0_out;
+  int32_t* hit_out;
+  unsigned char* tiles;  // this problem's staged tiles (workspace)
+  int64_t unit_base;     // first global work unit
+  int64_t record_base;   // first global staged record
+  int32_t n, m;
+  int32_t data_tiles;
+  int32_t qtile_base;    // first global query tile
+};
+static_assert(sizeof(Instance) == 80, "instance record layout");
+
+template <int CAP>
+struct Table {
+  int32_t count;
+  int32_t pad;
+  Instance inst[CAP];
+};
+
+struct SweepArgs {
   int64_t units;
   int grid;
-  float half_p;
-  float neg_half_p;
+  float half_p, neg_half_p;
   float4* partial;  // partial_slots x QT records (S0 hi, S0 lo, S1 hi, S1 lo)
+  const float* scales;
   unsigned* err;
 };
 
-// Stages the caller's n x 3 rows into tiles of TB records: TB x (x,x,y,y)
-// then TB x (z,z).  Padding records sit at +inf with z = 0, so their weight
-// is exactly 0 in both weight forms.
-__global__ void stage_f32_kernel(const float* __restrict__ data, int64_t n, int64_t data_tiles,
-                                 unsigned char* __restrict__ tiles) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= data_tiles * TB) return;
-  const int64_t t = r / TB;
-  const int k = static_cast<int>(r % TB);
-  float x = INFINITY, y = INFINITY, z = 0.f;
-  if (r < n) {
-    x = data[3 * r];
-    y = data[3 * r + 1];
-    z = data[3 * r + 2];
+// Largest instance index whose `field` <= v (fields ascend with the index).
+template <int CAP>
+__device__ __forceinline__ int find_unit(const Table<CAP>& t, int64_t v) {
+  int lo = 0, hi = t.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.inst[mid].unit_base <= v) lo = mid; else hi = mid - 1;
   }
-  unsigned char* base = tiles + t * kTileBytes;
-  reinterpret_cast<float4*>(base)[k] = make_float4(x, x, y, y);
-  reinterpret_cast<float2*>(base + TB * 16)[k] = make_float2(z, z);
+  return lo;
+}
+template <int CAP>
+__device__ __forceinline__ int find_record(const Table<CAP>& t, int64_t v) {
+  int lo = 0, hi = t.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.inst[mid].record_base <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+template <int CAP>
+__device__ __forceinline__ int find_qtile(const Table<CAP>& t, int64_t v) {
+  int lo = 0, hi = t.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (t.inst[mid].qtile_base <= v) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Power of two that maps the largest finite |coordinate| into [2^9, 2^10).
+__device__ __forceinline__ float scale_from_max(unsigned bits) {
+  const float mx = __uint_as_float(bits);
+  if (!(mx > 0.f)) return 1.f;
+  int e = 0;
+  frexpf(mx, &e);  // mx = f 2^e, f in [0.5, 1)
+  const int k = max(-100, min(100, 10 - e));
+  return ldexpf(1.f, k);
+}
+
+__device__ __forceinline__ float mul_ftz(float a, float b) {
+  float r;
+  asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// Largest finite |x|, |y| over each problem's data and queries.
+template <int CAP>
+__global__ void __launch_bounds__(256) range_kernel(const __grid_constant__ Table<CAP> t,
+                                                    unsigned* __restrict__ maxbits) {
+  __shared__ float red[8];
+  const Instance& I = t.inst[blockIdx.y];
+  float mx = 0.f;
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const int64_t first = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  for (int64_t i = first; i < I.n; i += stride) {
+    const float a = fabsf(I.data[3 * i]), b = fabsf(I.data[3 * i + 1]);
+    if (a <= FLT_MAX) mx = fmaxf(mx, a);
+    if (b <= FLT_MAX) mx = fmaxf(mx, b);
+  }
+  for (int64_t i = first; i < I.m; i += stride) {
+    const float a = fabsf(I.queries[2 * i]), b = fabsf(I.queries[2 * i + 1]);
+    if (a <= FLT_MAX) mx = fmaxf(mx, a);
+    if (b <= FLT_MAX) mx = fmaxf(mx, b);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+    atomicMax(&maxbits[blockIdx.y], __float_as_uint(mx));  // order-preserving for x >= 0
+  }
+}
+
+// Stages each problem's n x 3 rows into tiles of TB records: TB x (x,x,y,y)
+// then TB x (z,z), coordinates scaled by the problem's power of two.
+template <int CAP, int MODE>
+__global__ void __launch_bounds__(256)
+    stage_kernel(const __grid_constant__ Table<CAP> t, int64_t total_records,
+                 const unsigned* __restrict__ maxbits, float* __restrict__ scales) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= total_records) return;
+  const int k = find_record(t, r);
+  const Instance& I = t.inst[k];
+  const int64_t lr = r - I.record_base;
+  const float s = scale_from_max(maxbits[k]);
+  if (lr == 0) scales[k] = s;
+  const float pad = MODE == kPow2 ? kPadPow2 : INFINITY;
+  float x = pad, y = pad, z = 0.f;
+  if (lr < I.n) {
+    x = I.data[3 * lr] * s;
+    y = I.data[3 * lr + 1] * s;
+    z = I.data[3 * lr + 2];
+  }
+  unsigned char* base = I.tiles + (lr / TB) * kTileBytes;
+  const int slot = static_cast<int>(lr % TB);
+  reinterpret_cast<float4*>(base)[slot] = make_float4(x, x, y, y);
+  reinterpret_cast<float2*>(base + TB * 16)[slot] = make_float2(z, z);
 }
 
 template <int MODE>
-__device__ __forceinline__ u64 weight_pair(u64 d2, u64 half_p2, u64 neg_half_p2) {
+__device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
+                                           u64 neg_half_p2) {
   float a, b;
   upk(d2, a, b);
   if (MODE == kPow2) {
+    if (shared_rcp) {
+      const float r = rcp_approx(mul_ftz(a, b));  // 1 / (da db)
+      return pk(mul_ftz(b, r), mul_ftz(a, r));
+    }
     return pk(rcp_approx(a), rcp_approx(b));
   } else {
     // L = log2 d^2, clamped so that +inf (padding) stays finite below.
     const float la = fminf(lg2_approx(a), 1048576.f);
     const float lb = fminf(lg2_approx(b), 1048576.f);
     const u64 L = pk(la, lb);
-    const u64 th = mul2(L, neg_half_p2);      // t = -(p/2) L, rounded
-    const u64 nth = mul2(L, half_p2);         // -t exactly
-    const u64 tl = fma2(L, neg_half_p2, nth); // exact rounding error of t
+    const u64 th = mul2(L, neg_half_p2);       // t = -(p/2) L, rounded
+    const u64 nth = mul2(L, half_p2);          // -t exactly
+    const u64 tl = fma2(L, neg_half_p2, nth);  // exact rounding error of t
     float ta, tb;
     upk(th, ta, tb);
     const u64 e = pk(ex2_approx(ta), ex2_approx(tb));
     const u64 c = mul2(tl, pk(0.6931471805599453f, 0.6931471805599453f));
-    return fma2(e, c, e);                     // 2^(th + tl) to first order in tl
+    return fma2(e, c, e);  // 2^(th + tl) to first order in tl
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
+template <int MODE, int CAP>
+__global__ void __launch_bounds__(NT, 2)
+    sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[ST];
 
@@ -115,11 +235,16 @@ __global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
   }
   __syncthreads();
 
-  int64_t issued = 0;  // meaningful in thread 0 only
+  // Producer (thread 0): one bulk copy per unit, STAGES units ahead.
+  int64_t issued = 0;
+  int pk_inst = find_unit(t, u0);
   auto issue = [&](int64_t local) {
+    const int64_t u = u0 + local;
+    while (pk_inst + 1 < t.count && t.inst[pk_inst + 1].unit_base <= u) ++pk_inst;
+    const Instance& I = t.inst[pk_inst];
+    const int64_t dt = (u - I.unit_base) % I.data_tiles;
     const int s = static_cast<int>(local % ST);
-    const int64_t dt = (u0 + local) % a.data_tiles;
-    bulk_load(smem_u32(smem + s * kTileBytes), a.tiles + dt * kTileBytes, kTileBytes,
+    bulk_load(smem_u32(smem + s * kTileBytes), I.tiles + dt * kTileBytes, kTileBytes,
               smem_u32(&full_bar[s]));
   };
   if (tid == 0) {
@@ -128,21 +253,26 @@ __global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
 
   const u64 hp2 = pk(a.half_p, a.half_p);
   const u64 nhp2 = pk(a.neg_half_p, a.neg_half_p);
+  int ci = find_unit(t, u0);
   int64_t i = 0;
   bool aborted = false;
   while (i < total) {
-    const int64_t qt = (u0 + i) / a.data_tiles;
-    const int64_t seg_end = min(total, (qt + 1) * a.data_tiles - u0);
+    const int64_t u = u0 + i;
+    while (ci + 1 < t.count && t.inst[ci + 1].unit_base <= u) ++ci;
+    const Instance& I = t.inst[ci];
+    const int64_t qt = (u - I.unit_base) / I.data_tiles;
+    const int64_t seg_end = min(total, I.unit_base + (qt + 1) * I.data_tiles - u0);
+    const float sc = a.scales[ci];
 
     u64 QX[KP], QY[KP], H0[KP], L0[KP], H1[KP], L1[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       const int64_t ja = qt * QT + (2 * k) * NT + tid;
       const int64_t jb = ja + NT;
-      const float xa = ja < a.m ? a.queries[2 * ja] : 0.f;
-      const float ya = ja < a.m ? a.queries[2 * ja + 1] : 0.f;
-      const float xb = jb < a.m ? a.queries[2 * jb] : 0.f;
-      const float yb = jb < a.m ? a.queries[2 * jb + 1] : 0.f;
+      const float xa = ja < I.m ? I.queries[2 * ja] * sc : 0.f;
+      const float ya = ja < I.m ? I.queries[2 * ja + 1] * sc : 0.f;
+      const float xb = jb < I.m ? I.queries[2 * jb] * sc : 0.f;
+      const float yb = jb < I.m ? I.queries[2 * jb + 1] * sc : 0.f;
       QX[k] = pk(xa, xb);
       QY[k] = pk(ya, yb);
       H0[k] = L0[k] = H1[k] = L1[k] = 0ull;
@@ -167,7 +297,7 @@ __global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
               const u64 dx = sub2f(QX[k], xy.x);
               const u64 dy = sub2f(QY[k], xy.y);
               const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
-              const u64 w = weight_pair<MODE>(d2, hp2, nhp2);
+              const u64 w = weight_pair<MODE>(d2, k < KSHARED, hp2, nhp2);
               if (r == 0) {
                 C0[k] = w;
                 C1[k] = mul2(w, zz);
@@ -196,7 +326,7 @@ __global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
     }
     if (aborted) break;
 
-    float4* P = a.partial + (qt + g) * QT;
+    float4* P = a.partial + (I.qtile_base + qt + g) * QT;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       float h0a, h0b, l0a, l0b, h1a, h1b, l1a, l1b;
@@ -219,37 +349,51 @@ __global__ void __launch_bounds__(NT, 2) fwd_f32_kernel(const FwdArgs a) {
 
 // FP64 combine of the pieces of each query: Z = S1 / S0, or a flag that
 // routes the query to the slow path (exact hit or FP32 range exceeded).
-__global__ void combine_f32_kernel(const float4* __restrict__ partial, int64_t m,
-                                   int64_t data_tiles, int64_t units, int grid, double tiny,
-                                   float* __restrict__ out, double* __restrict__ s0_out,
-                                   int32_t* __restrict__ hit_out, Control* __restrict__ ctrl,
-                                   int32_t* __restrict__ list) {
-  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= m) return;
-  const int64_t qt = j / QT, lq = j % QT;
-  const int64_t g0 = cta_of_unit(qt * data_tiles, units, grid);
-  const int64_t g1 = cta_of_unit((qt + 1) * data_tiles - 1, units, grid);
+template <int CAP>
+__global__ void __launch_bounds__(256)
+    combine_kernel(const __grid_constant__ Table<CAP> t, const float4* __restrict__ partial,
+                   int64_t total_slots, int64_t units, int grid, const float* __restrict__ scales,
+                   double p, Control* __restrict__ ctrl, int2* __restrict__ list) {
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= total_slots) return;
+  const int64_t qtg = idx / QT, lq = idx % QT;
+  const int k = find_qtile(t, qtg);
+  const Instance& I = t.inst[k];
+  const int64_t qt = qtg - I.qtile_base;
+  const int64_t j = qt * QT + lq;
+  if (j >= I.m) return;
+  const int64_t g0 = cta_of_unit(I.unit_base + qt * I.data_tiles, units, grid);
+  const int64_t g1 = cta_of_unit(I.unit_base + (qt + 1) * I.data_tiles - 1, units, grid);
   double s0 = 0.0, s1 = 0.0;
   for (int64_t g = g0; g <= g1; ++g) {
-    const float4 v = partial[(qt + g) * QT + lq];
+    const float4 v = partial[(qtg + g) * QT + lq];
     s0 += double(v.x) + double(v.y);
     s1 += double(v.z) + double(v.w);
   }
-  if (!(s0 > tiny) || !isfinite(s0) || !isfinite(s1)) {
+  if (!(s0 > kTinySumPerPoint * double(I.n)) || !isfinite(s0) || !isfinite(s1)) {
     const unsigned slot = atomicAdd(&ctrl->flagged, 1u);
-    list[slot] = static_cast<int32_t>(j);
+    list[slot] = make_int2(k, static_cast<int>(j));
     return;
   }
-  out[j] = static_cast<float>(s1 / s0);
-  if (s0_out) s0_out[j] = s0;
-  if (hit_out) hit_out[j] = kNoHit;
+  I.out[j] = static_cast<float>(s1 / s0);
+  // Weights were computed on coordinates scaled by s: w = s^-p w_true.
+  if (I.s0_out) I.s0_out[j] = s0 * pow(double(scales[k]), p);
+  if (I.hit_out) I.hit_out[j] = kNoHit;
 }
 
-template <int MODE>
-cudaError_t launch_sweep(const FwdArgs& a, cudaStream_t stream) {
-  const size_t smem = size_t(ST) * kTileBytes;
-  fwd_f32_kernel<MODE><<<a.grid, NT, smem, stream>>>(a);
-  return cudaGetLastError();
+template <int CAP>
+__global__ void __launch_bounds__(kSlowThreads)
+    slow_batch_kernel(const __grid_constant__ Table<CAP> t, double p,
+                      const Control* __restrict__ ctrl, const int2* __restrict__ list) {
+  const unsigned count = ctrl->flagged;
+  for (unsigned f = blockIdx.x; f < count; f += gridDim.x) {
+    const int2 e = list[f];
+    const Instance& I = t.inst[e.x];
+    const int64_t j = e.y;
+    slow_one_query<float, float>(I.data, I.n, I.queries[2 * j], I.queries[2 * j + 1], p,
+                                 &I.out[j], I.s0_out ? &I.s0_out[j] : nullptr,
+                                 I.hit_out ? &I.hit_out[j] : nullptr);
+  }
 }
 
 // One thread waits, with the sweep kernels' bounded wait, on a barrier whose
@@ -263,58 +407,137 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err) {
   }
 }
 
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <int CAP>
+cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p,
+                        unsigned char* ws, Control* ctrl, int sm_count, const SweepEvents* ev,
+                        cudaStream_t stream) {
+  Table<CAP> t;
+  t.count = plan.count;
+  t.pad = 0;
+  unsigned char* tiles = ws;
+  float4* partial = reinterpret_cast<float4*>(ws + plan.staged_bytes);
+  int2* list = reinterpret_cast<int2*>(ws + plan.staged_bytes + plan.partial_bytes);
+  unsigned* maxbits =
+      reinterpret_cast<unsigned*>(ws + plan.staged_bytes + plan.partial_bytes + plan.list_bytes);
+  float* scales = reinterpret_cast<float*>(maxbits + plan.count);
+  int64_t longest = 1;
+  for (int k = 0; k < plan.count; ++k) {
+    Instance& I = t.inst[k];
+    I.data = probs[k].data;
+    I.queries = probs[k].queries;
+    I.out = probs[k].out;
+    I.s0_out = probs[k].s0_out;
+    I.hit_out = probs[k].hit_out;
+    I.tiles = tiles + size_t(plan.tile_offset[k]) * kTileBytes;
+    I.unit_base = plan.unit_base[k];
+    I.record_base = plan.tile_offset[k] * TB;
+    I.n = static_cast<int32_t>(probs[k].n);
+    I.m = static_cast<int32_t>(probs[k].m);
+    I.data_tiles = static_cast<int32_t>(plan.data_tiles[k]);
+    I.qtile_base = static_cast<int32_t>(plan.qtile_base[k]);
+    longest = std::max<int64_t>(longest, std::max(probs[k].n, probs[k].m));
+  }
+  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned) * plan.count, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
+  if (e != cudaSuccess) return e;
+
+  const bool pow2 = (p == 2.0);
+  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(64, (longest + 4095) / 4096));
+  range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
+  const int64_t records = plan.total_data_tiles * TB;
+  const unsigned sgrid = static_cast<unsigned>((records + 255) / 256);
+  if (pow2)
+    stage_kernel<CAP, kPow2><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
+  else
+    stage_kernel<CAP, kPowGeneral><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
+
+  SweepArgs a;
+  a.units = plan.units;
+  a.grid = plan.grid;
+  a.half_p = static_cast<float>(0.5 * p);
+  a.neg_half_p = -a.half_p;
+  a.partial = partial;
+  a.scales = scales;
+  a.err = &ctrl->error;
+  const size_t smem = size_t(ST) * kTileBytes;
+  if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
+  if (pow2)
+    sweep_kernel<kPow2, CAP><<<plan.grid, NT, smem, stream>>>(a, t);
+  else
+    sweep_kernel<kPowGeneral, CAP><<<plan.grid, NT, smem, stream>>>(a, t);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
+
+  const int64_t slots = plan.total_query_tiles * QT;
+  combine_kernel<CAP><<<static_cast<unsigned>((slots + 255) / 256), 256, 0, stream>>>(
+      t, partial, slots, plan.units, plan.grid, scales, p, ctrl, list);
+  slow_batch_kernel<CAP><<<2 * sm_count, kSlowThreads, 0, stream>>>(t, p, ctrl, list);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream) {
-  bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(&ctrl->error);
-  return cudaGetLastError();
+void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
+                    BatchPlan* bp) {
+  bp->count = count;
+  bp->data_tiles.assign(count, 0);
+  bp->query_tiles.assign(count, 0);
+  bp->unit_base.assign(count, 0);
+  bp->qtile_base.assign(count, 0);
+  bp->tile_offset.assign(count, 0);
+  int64_t units = 0, qtiles = 0, tiles = 0, queries = 0;
+  for (int k = 0; k < count; ++k) {
+    const int64_t dt = (probs[k].n + TB - 1) / TB;
+    const int64_t qt = (probs[k].m + QT - 1) / QT;
+    bp->data_tiles[k] = dt;
+    bp->query_tiles[k] = qt;
+    bp->unit_base[k] = units;
+    bp->qtile_base[k] = qtiles;
+    bp->tile_offset[k] = tiles;
+    units += dt * qt;
+    qtiles += qt;
+    tiles += dt;
+    queries += probs[k].m;
+  }
+  bp->units = units;
+  bp->total_query_tiles = qtiles;
+  bp->total_data_tiles = tiles;
+  const int64_t resident = int64_t(sm_count) * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+  bp->grid = static_cast<int>(std::max<int64_t>(1, std::min(units, resident)));
+  bp->partial_slots = qtiles + bp->grid - 1;
+  bp->staged_bytes = round_up(size_t(tiles) * kTileBytes, 256);
+  bp->partial_bytes = round_up(size_t(bp->partial_slots) * QT * sizeof(float4), 256);
+  bp->list_bytes = round_up(size_t(std::max<int64_t>(queries, 1)) * sizeof(int2), 256);
+  bp->scale_bytes = round_up(size_t(count) * 8, 256);
+  bp->workspace_bytes = bp->staged_bytes + bp->partial_bytes + bp->list_bytes + bp->scale_bytes;
+}
+
+cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, double p,
+                             void* workspace, Control* ctrl, int sm_count,
+                             const SweepEvents* ev, cudaStream_t stream) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  if (plan.count == 1) return launch_impl<1>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+  if (plan.count <= kBatchCap)
+    return launch_impl<kBatchCap>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+  return cudaErrorInvalidValue;
 }
 
 int occupancy_forward_f32(bool general_p) {
   int blocks = 0;
   const size_t smem = size_t(ST) * kTileBytes;
   if (general_p)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fwd_f32_kernel<kPowGeneral>, NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPowGeneral, kBatchCap>,
+                                                  NT, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fwd_f32_kernel<kPow2>, NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap>, NT,
+                                                  smem);
   return blocks > 0 ? blocks : 1;
 }
 
-cudaError_t launch_forward_f32(const F32Problem& pb, const Plan& plan, void* workspace,
-                               Control* ctrl, int sm_count, const SweepEvents* ev,
-                               cudaStream_t stream) {
-  unsigned char* ws = static_cast<unsigned char*>(workspace);
-  unsigned char* tiles = ws;
-  float4* partial = reinterpret_cast<float4*>(ws + plan.staged_bytes);
-  int32_t* list = reinterpret_cast<int32_t*>(ws + plan.staged_bytes + plan.partial_bytes);
-
-  const int64_t staged = plan.data_tiles * TB;
-  stage_f32_kernel<<<static_cast<unsigned>((staged + 255) / 256), 256, 0, stream>>>(
-      pb.data, pb.n, plan.data_tiles, tiles);
-  cudaError_t e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
-  if (e != cudaSuccess) return e;
-
-  FwdArgs a;
-  a.tiles = tiles;
-  a.queries = pb.queries;
-  a.m = pb.m;
-  a.data_tiles = plan.data_tiles;
-  a.units = plan.units;
-  a.grid = plan.grid;
-  a.half_p = static_cast<float>(0.5 * pb.p);
-  a.neg_half_p = -a.half_p;
-  a.partial = partial;
-  a.err = &ctrl->error;
-  if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
-  e = (pb.p == 2.0) ? launch_sweep<kPow2>(a, stream) : launch_sweep<kPowGeneral>(a, stream);
-  if (e != cudaSuccess) return e;
-  if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
-
-  combine_f32_kernel<<<static_cast<unsigned>((pb.m + 255) / 256), 256, 0, stream>>>(
-      partial, pb.m, plan.data_tiles, plan.units, plan.grid, kTinySumPerPoint * double(pb.n),
-      pb.out, pb.s0_out, pb.hit_out, ctrl, list);
-  slow_path_kernel<float, float><<<2 * sm_count, kSlowThreads, 0, stream>>>(
-      pb.data, pb.n, pb.queries, pb.p, ctrl, list, pb.out, pb.s0_out, pb.hit_out);
+cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream) {
+  bounded_wait_selftest_kernel<<<1, 32, 0, stream>>>(&ctrl->error);
   return cudaGetLastError();
 }
 

@@ -4,20 +4,24 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace idw {
 
 // ---------------------------------------------------------------- tiling
-// FP32-compensated forward: each thread holds kQueryPairs pairs of queries;
+// FP32-compensated forward: each thread holds kQueryPairsF32 pairs of queries;
 // a data tile of kRecordsF32 points is staged as (x,x,y,y) + (z,z) records.
 constexpr int kThreadsF32 = 256;
 constexpr int kQueryPairsF32 = 4;
 constexpr int kQueriesPerCtaF32 = kThreadsF32 * 2 * kQueryPairsF32;  // 2048
 constexpr int kRecordsF32 = 256;
 constexpr int kStagesF32 = 3;
-constexpr int kChunkF32 = 16;
+constexpr int kChunkF32 = 32;
 constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 8 B (z,z)
+// Instances per batched launch (the instance table is a kernel parameter).
+constexpr int kBatchCap = 256;
 
 // Plain FP64 forward: kQueriesF64 queries per thread; tiles of (x,y) + z.
 constexpr int kThreadsF64 = 128;
@@ -43,6 +47,50 @@ struct Control {
 
 enum WeightMode : int { kPow2 = 0, kPowGeneral = 1 };
 
+// Optional events recorded around the all-pairs sweep kernel.
+struct SweepEvents {
+  cudaEvent_t start = nullptr, stop = nullptr;
+};
+
+// --------------------------------------------------- FP32 (batched) plan
+// One problem of Eq. 1 in FP32 (device pointers, caller-owned).
+struct F32Problem {
+  const float* data;     // n x 3
+  int64_t n;
+  const float* queries;  // m x 2
+  int64_t m;
+  float* out;
+  double* s0_out;    // nullable
+  int32_t* hit_out;  // nullable
+};
+
+// Launch plan of up to kBatchCap problems swept by one persistent grid.
+// Work units are (query tile, data tile) pairs numbered instance by
+// instance, query-tile-major; CTA g sweeps [g U / G, (g + 1) U / G).
+struct BatchPlan {
+  int count = 0;
+  std::vector<int64_t> data_tiles, query_tiles, unit_base, qtile_base, tile_offset;
+  int64_t units = 0, total_query_tiles = 0, total_data_tiles = 0;
+  int grid = 0;
+  int64_t partial_slots = 0;
+  size_t staged_bytes = 0, partial_bytes = 0, list_bytes = 0, scale_bytes = 0;
+  size_t workspace_bytes = 0;
+};
+
+// Host arithmetic only.  Problems must have n >= 1 and m >= 1.
+void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
+                    BatchPlan* plan);
+
+// Enqueues range scan, staging, sweep, combine and slow path for the batch.
+cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, double p,
+                             void* workspace, Control* ctrl, int sm_count,
+                             const SweepEvents* ev, cudaStream_t stream);
+int occupancy_forward_f32(bool general_p);
+
+// Failure-detection self-test: a bounded wait on a barrier nobody completes.
+cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream);
+
+// ------------------------------------------------------------ FP64 plain
 struct Plan {
   int threads, queries_per_cta, records_per_tile;
   int64_t query_tiles, data_tiles, units;
@@ -52,31 +100,6 @@ struct Plan {
   size_t staged_bytes, partial_bytes, list_bytes, workspace_bytes;
 };
 
-// ----------------------------------------------------------- launchers
-// All launchers enqueue on `stream` and return cudaGetLastError().
-
-// FP32-compensated single-problem forward.
-struct F32Problem {
-  const float* data;     // n x 3
-  int64_t n;
-  const float* queries;  // m x 2
-  int64_t m;
-  double p;
-  float* out;
-  double* s0_out;   // nullable
-  int32_t* hit_out; // nullable
-};
-// Optional events recorded around the all-pairs sweep kernel.
-struct SweepEvents {
-  cudaEvent_t start = nullptr, stop = nullptr;
-};
-
-cudaError_t launch_forward_f32(const F32Problem& pb, const Plan& plan, void* workspace,
-                               Control* ctrl, int sm_count, const SweepEvents* ev,
-                               cudaStream_t stream);
-int occupancy_forward_f32(bool general_p);
-
-// Plain FP64 single-problem forward.
 struct F64Problem {
   const double* data;
   int64_t n;
@@ -91,9 +114,6 @@ cudaError_t launch_forward_f64(const F64Problem& pb, const Plan& plan, void* wor
                                Control* ctrl, int sm_count, const SweepEvents* ev,
                                cudaStream_t stream);
 int occupancy_forward_f64();
-
-// Failure-detection self-test: a bounded wait on a barrier nobody completes.
-cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream);
 
 // Pipe-rate probe: returns ops per SM per clock for the 6 probed pipes.
 cudaError_t measure_pipe_rates(int sm_count, double rates[6]);

@@ -71,8 +71,6 @@ idw_status setup_current_device(DeviceSetup* out) {
   return IDW_OK;
 }
 
-size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
 }  // namespace
 }  // namespace idw
 
@@ -93,27 +91,13 @@ extern "C" idw_status idw_interpolate_noalloc(const float* data_xyz, int64_t n,
   if (st != IDW_OK) return st;
 
   // The same launch plan as idw_interpolate (host arithmetic only).
-  Plan pl;
-  pl.threads = kThreadsF32;
-  pl.queries_per_cta = kQueriesPerCtaF32;
-  pl.records_per_tile = kRecordsF32;
-  pl.query_tiles = (m + kQueriesPerCtaF32 - 1) / kQueriesPerCtaF32;
-  pl.data_tiles = (n + kRecordsF32 - 1) / kRecordsF32;
-  pl.units = pl.query_tiles * pl.data_tiles;
-  const int64_t resident = int64_t(dev.sm_count) * (p == 2.0 ? dev.occ_pow2 : dev.occ_general);
-  pl.grid = static_cast<int>(pl.units < resident ? pl.units : resident);
-  pl.partial_slots = pl.query_tiles + pl.grid - 1;
-  pl.max_pieces = 0;
-  pl.staged_bytes = round_up(size_t(pl.data_tiles) * kTileBytesF32, 256);
-  pl.partial_bytes = round_up(size_t(pl.partial_slots) * kQueriesPerCtaF32 * 16, 256);
-  pl.list_bytes = round_up(size_t(m) * sizeof(int32_t), 256);
-  pl.workspace_bytes = pl.staged_bytes + pl.partial_bytes + pl.list_bytes;
-  if (pl.workspace_bytes > kNoAllocScratchBytes - kControlBytes) return IDW_ERR_WORKSPACE;
+  F32Problem pb{data_xyz, n, queries_xy, m, out, nullptr, nullptr};
+  BatchPlan plan;
+  plan_batch_f32(&pb, 1, dev.sm_count, p == 2.0 ? dev.occ_pow2 : dev.occ_general, &plan);
+  if (plan.workspace_bytes > kNoAllocScratchBytes - kControlBytes) return IDW_ERR_WORKSPACE;
 
   Control* ctrl = reinterpret_cast<Control*>(dev.scratch);
-  F32Problem pb{data_xyz, n, queries_xy, m, p, out, nullptr, nullptr};
-  const cudaError_t e = launch_forward_f32(pb, pl, dev.scratch + kControlBytes, ctrl,
-                                           dev.sm_count, nullptr,
-                                           static_cast<cudaStream_t>(stream));
+  const cudaError_t e = launch_batch_f32(&pb, plan, p, dev.scratch + kControlBytes, ctrl,
+                                         dev.sm_count, nullptr, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? IDW_OK : IDW_ERR_CUDA;
 }

@@ -129,13 +129,35 @@ def test_fp32_overflow_takes_fp64_path(idw):
     data = np.empty((2000, 3), np.float32)
     data[:, :2] = rng.random((2000, 2))
     data[:, 2] = rng.standard_normal(2000)
-    data[7, 2] = np.float32(3e38)       # w * z overflows FP32 for most queries
+    data[7, 2] = np.float32(3e38)       # w * z overflows FP32 near point 7
     q = rng.random((500, 2)).astype(np.float32)
+    q[11] = data[7, :2] + np.float32(1e-4)
+    q[12] = data[7, :2] - np.float32(3e-5)
     Z64, _ = oracle.idw(data, q, 2.0)
     Z, _, hit = _run(idw, data, q, 2.0)
     assert np.count_nonzero(hit == -2) > 0
     rel = np.abs(Z.astype(np.float64) - Z64) / np.maximum(np.abs(Z64), 1e-30)
     assert np.all(np.isfinite(Z)) and np.max(rel) <= 1e-6
+
+
+@pytest.mark.parametrize("offset,scale", [(0.0, 1e-20), (1e6, 1000.0), (-3e4, 1e-3),
+                                          (0.0, 1e12), (5e-3, 1e-6)])
+def test_coordinate_ranges(idw, offset, scale):
+    """Eq. 1 depends only on distance ratios; the library rescales by a power
+    of two internally, so any coordinate range gives the FP32 bound."""
+    prob = synthetic.uniform_problem(4000, 3000, seed=17)
+    data = prob["data"].astype(np.float64)
+    q = prob["queries"].astype(np.float64)
+    data[:, :2] = data[:, :2] * scale + offset
+    q = q * scale + offset
+    data = data.astype(np.float32)
+    q = q.astype(np.float32)
+    for p in (2.0, 2.5):
+        Z64, hit64 = oracle.idw(data, q, p)
+        Z, _, hit = _run(idw, data, q, p)
+        assert np.array_equal(hit >= 0, hit64 >= 0)
+        assert _rel_err(Z, Z64, data[:, 2]) <= TOL_F32C, (offset, scale, p)
+        assert np.count_nonzero(hit == -2) <= 3
 
 
 def test_permutation_and_constant_field(idw):
