@@ -21,7 +21,7 @@ struct idw_handle_s {
   void* io = nullptr;  // device buffers of the host-pointer entry point
   size_t io_bytes = 0;
   idw::Control* ctrl = nullptr;  // device control words
-  int occ_f32_pow2 = 0, occ_f32_general = 0, occ_f64 = 0;
+  int occ_f32_pow2 = 0, occ_f32_general = 0, occ_f64 = 0, occ_bwd = 0;
   char last_cuda[256] = "no error";
   bool profiling = false;
   std::vector<idw::SweepEvents> events;  // recorded sweep launches, oldest first
@@ -316,10 +316,35 @@ idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const floa
                         int64_t m, double p, const float* Z, const double* s0, const int32_t* hit,
                         const float* grad_out, float* grad_z, float* grad_data_xy,
                         float* grad_query_xy, double* grad_p, void* stream) {
-  (void)data; (void)n; (void)queries; (void)m; (void)p; (void)Z; (void)s0; (void)hit;
-  (void)grad_out; (void)grad_z; (void)grad_data_xy; (void)grad_query_xy; (void)grad_p;
-  (void)stream;
-  return h ? IDW_ERR_UNSUPPORTED : IDW_ERR_INVALID_ARG;
+  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, Z);
+  if (st != IDW_OK) return st;
+  if (m == 0) {
+    // No query contributes: every requested gradient is zero.
+    DeviceGuard guard(h->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (grad_z) e = cudaMemsetAsync(grad_z, 0, size_t(n) * sizeof(float), s);
+    if (e == cudaSuccess && grad_data_xy)
+      e = cudaMemsetAsync(grad_data_xy, 0, size_t(n) * 2 * sizeof(float), s);
+    if (e == cudaSuccess && grad_p) e = cudaMemsetAsync(grad_p, 0, sizeof(double), s);
+    return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+  }
+  if (!s0 || !hit || !grad_out) return IDW_ERR_INVALID_ARG;
+  if (!aligned(s0, 8) || !aligned(hit, 4) || !aligned(grad_out, 4) || !aligned(grad_z, 4) ||
+      !aligned(grad_data_xy, 4) || !aligned(grad_query_xy, 4) || !aligned(grad_p, 8))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  if (!h->occ_bwd) h->occ_bwd = idw::occupancy_backward_f32();
+  idw::BwdPlan bp;
+  idw::plan_backward_f32(n, m, h->sm_count, h->occ_bwd, &bp);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, bp.workspace_bytes);
+  if (st != IDW_OK) return st;
+  idw::BwdProblem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m, p,
+                     Z, s0, hit, grad_out, grad_z, grad_data_xy, grad_query_xy, grad_p};
+  cudaError_t e = idw::launch_backward_f32(pb, bp, h->ws, h->ctrl, h->sm_count,
+                                           static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
 idw_status idw_sync_status(idw_handle_t h, void* stream) {

@@ -149,6 +149,59 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return false;
 }
 
+// ------------------------------------------------------ tile ring
+// A ring of ST shared-memory stages fed by one 1-D bulk copy per work unit.
+// Thread 0 produces; every thread consumes.  `src(u)` gives the global
+// address of work unit u's tile.  Units are numbered locally from 0 (the
+// CTA's first unit) to `total`.
+template <int ST, class Src>
+struct TileRing {
+  unsigned char* smem;
+  unsigned long long* bars;
+  uint32_t bytes;
+  unsigned* err;
+  int64_t total;
+  Src src;
+  int64_t issued;  // meaningful in thread 0 only
+
+  __device__ void start() {
+    issued = 0;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < ST; ++s) mbar_init(smem_u32(&bars[s]), 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (; issued < ST && issued < total; ++issued) issue(issued);
+  }
+  __device__ void issue(int64_t local) {
+    const int s = static_cast<int>(local % ST);
+    bulk_load(smem_u32(smem + size_t(s) * bytes), src(local), bytes, smem_u32(&bars[s]));
+  }
+  // Waits (bounded) for unit `local`; returns its stage, sets ok.
+  __device__ const unsigned char* wait(int64_t local, bool& ok) {
+    const int s = static_cast<int>(local % ST);
+    ok = mbar_wait_bounded(smem_u32(&bars[s]), static_cast<uint32_t>((local / ST) & 1), err);
+    return smem + size_t(s) * bytes;
+  }
+  // All threads are done with unit `local`'s stage: refill it, unless some
+  // thread's wait gave up (then every thread returns false).
+  __device__ bool release(bool ok) {
+    if (__syncthreads_or(!ok)) return false;
+    if (threadIdx.x == 0 && issued < total) {
+      issue(issued);
+      ++issued;
+    }
+    return true;
+  }
+  // After an abort at unit `from`: let copies still in flight land.
+  __device__ void drain(int64_t from) {
+    if (threadIdx.x != 0) return;
+    for (int64_t k = from; k < issued; ++k)
+      mbar_wait_bounded(smem_u32(&bars[k % ST]), static_cast<uint32_t>((k / ST) & 1), err);
+  }
+};
+
 // ------------------------------------------------------ stream-K split
 // Work units (query tile, data tile) are numbered query-tile-major; CTA g of
 // G sweeps units [floor(g U / G), floor((g + 1) U / G)).

@@ -90,6 +90,36 @@ int occupancy_forward_f32(bool general_p);
 // Failure-detection self-test: a bounded wait on a barrier nobody completes.
 cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream);
 
+// ------------------------------------------------------- FP32 adjoint
+struct BwdProblem {
+  const float* data;     // n x 3
+  int64_t n;
+  const float* queries;  // m x 2
+  int64_t m;
+  double p;
+  const float* Z;        // forward outputs (m)
+  const double* s0;      // saved weight sums (m)
+  const int32_t* hit;    // saved hit codes (m)
+  const float* g;        // upstream gradient (m)
+  float* grad_z;         // n, nullable
+  float* grad_xy;        // n x 2, nullable
+  float* grad_q;         // m x 2, nullable
+  double* grad_p;        // 1, nullable
+};
+
+struct BwdPlan {
+  int64_t data_tiles = 0, query_records_tiles = 0, query_reg_tiles = 0, data_reg_tiles = 0;
+  int64_t units_q = 0, units_d = 0;
+  int grid_q = 0, grid_d = 0;
+  size_t staged_bytes = 0, qtiles_bytes = 0, partial_bytes = 0, gp_bytes = 0, list_bytes = 0,
+         dlist_bytes = 0, scale_bytes = 0, workspace_bytes = 0;
+};
+
+void plan_backward_f32(int64_t n, int64_t m, int sm_count, int ctas_per_sm, BwdPlan* plan);
+cudaError_t launch_backward_f32(const BwdProblem& pb, const BwdPlan& plan, void* workspace,
+                                Control* ctrl, int sm_count, cudaStream_t stream);
+int occupancy_backward_f32();
+
 // ------------------------------------------------------------ FP64 plain
 struct Plan {
   int threads, queries_per_cta, records_per_tile;
