@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="headline",
+                    choices=["headline", "scale", "clustered", "adjoint", "batched", "all"],
+                    help="headline = the N=M=2^20 line; the others measure the other "
+                         "workloads (one JSON line each)")
     return ap.parse_args()
 
 
@@ -327,13 +331,183 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ other workloads
+
+def _events_ms(fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def _emit(workload, rows, **extra):
+    line = {"metric": "pairs/s", "unit": UNIT, "data": "synthetic", "dtype": "f32",
+            "config": {"workload": workload}, "rows": rows}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def run_scale(args):
+    """Paper-shaped sweep N = M, FP32-compensated vs plain FP64, p = 2."""
+    import torch
+    import oracle
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    rows = []
+    for n in synthetic.SCALE_SWEEP:
+        prob = synthetic.config_scale(n)
+        d = torch.from_numpy(prob["data"]).cuda()
+        q = torch.from_numpy(prob["queries"]).cuda()
+        out = torch.empty(n, device="cuda")
+        pairs = float(n) * n
+        reps = max(3, int(2e11 / pairs))
+        ms = _events_ms(lambda: idw.interpolate(d, q, 2.0, out=out), reps)
+        m64 = min(n, 8192)
+        d64, q64 = d.double(), q[:m64].double()
+        ms64 = _events_ms(lambda: idw.interpolate(d64, q64, 2.0, "f64"), 2)
+        idx = np.random.default_rng(3).choice(n, min(n, 512), replace=False)
+        Z64, _ = oracle.idw(prob["data"], prob["queries"][idx], 2.0)
+        err = float(np.max(np.abs(out.cpu().numpy()[idx] - Z64)) /
+                    np.max(np.abs(prob["data"][:, 2])))
+        rows.append({"n": n, "m": n, "f32c_pairs_s": pairs / (ms / 1e3),
+                     "f32c_ms": ms, "f64_pairs_s": float(n) * m64 / (ms64 / 1e3),
+                     "speedup_vs_f64": (pairs / ms) / (float(n) * m64 / ms64),
+                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+    _emit("paper-shaped scale sweep N=M, uniform [0,1)^2, wave field, p=2 (FP64 arm on "
+          "min(N, 8192) queries)", rows)
+
+
+def run_clustered(args):
+    """Gaussian-mixture data, 1024^2 query grid, p in {1.5, 2, 3.5}."""
+    import torch
+    import oracle
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    prob = synthetic.config_clustered()
+    d = torch.from_numpy(prob["data"]).cuda()
+    q = torch.from_numpy(prob["queries"]).cuda()
+    n, m = d.shape[0], q.shape[0]
+    out = torch.empty(m, device="cuda")
+    idx = np.random.default_rng(4).choice(m, 1024, replace=False)
+    rows = []
+    for p in prob["p_values"]:
+        ms = _events_ms(lambda: idw.interpolate(d, q, p, out=out), 5)
+        Z64, _ = oracle.idw(prob["data"], prob["queries"][idx], p)
+        err = float(np.max(np.abs(out.cpu().numpy()[idx] - Z64)) /
+                    np.max(np.abs(prob["data"][:, 2])))
+        rows.append({"p": p, "pairs_s": float(n) * m / (ms / 1e3), "ms": ms,
+                     "path": "rcp" if p == 2.0 else "log2/exp2",
+                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+    _emit("clustered: N=262144 from 64 Gaussian blobs (sigma 0.01), z = exp(-4 r^2) + "
+          "0.05 N(0,1), queries on a 1024^2 grid", rows)
+
+
+def run_adjoint(args):
+    """Forward + adjoint at N = M = 262144, p = 2.5."""
+    import torch
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    prob = synthetic.config_adjoint()
+    d = torch.from_numpy(prob["data"]).cuda()
+    q = torch.from_numpy(prob["queries"]).cuda()
+    g = torch.from_numpy(prob["grad_out"]).cuda()
+    p = prob["p"]
+    n, m = d.shape[0], q.shape[0]
+    state = {}
+
+    def fwd():
+        state["Z"], state["s0"], state["hit"] = idw.interpolate_saved(d, q, p)
+
+    def bwd():
+        idw.backward(d, q, p, state["Z"], state["s0"], state["hit"], g)
+
+    fwd_ms = _events_ms(fwd, 3)
+    bwd_ms = _events_ms(bwd, 3)
+    pairs = float(n) * m
+    _emit("adjoint: N=M=262144 uniform [0,1)^2, wave field, p=2.5, upstream grad N(0,1); "
+          "backward = query sweep + data sweep (2 pair evaluations per pair)",
+          [{"forward_ms": fwd_ms, "forward_pairs_s": pairs / (fwd_ms / 1e3),
+            "backward_ms": bwd_ms, "backward_pairs_s": pairs / (bwd_ms / 1e3),
+            "backward_pair_evaluations_s": 2 * pairs / (bwd_ms / 1e3),
+            "backward_over_forward": bwd_ms / fwd_ms}])
+
+
+def run_batched(args, headline_pairs_s=None):
+    """256 uneven problems: one persistent launch vs a per-instance loop."""
+    import torch
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    batch = synthetic.config_batch()
+    inst = batch["instances"]
+    d = [torch.from_numpy(i["data"]).cuda() for i in inst]
+    q = [torch.from_numpy(i["queries"]).cuda() for i in inst]
+    outs = [torch.empty(x.shape[0], device="cuda") for x in q]
+    pairs = float(sum(x.shape[0] * y.shape[0] for x, y in zip(d, q)))
+
+    def batched():
+        idw.interpolate_batched(d, q, 2.0, outs=outs)
+
+    def loop():
+        for dk, qk, ok in zip(d, q, outs):
+            idw.interpolate(dk, qk, 2.0, out=ok)
+
+    ms_b = _events_ms(batched, 5)
+    ms_l = _events_ms(loop, 3)
+    graph = torch.cuda.CUDAGraph()
+    batched()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batched()
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(graph):
+        batched()
+    ms_g = _events_ms(graph.replay, 5)
+    if headline_pairs_s is None:
+        big = synthetic.config_scale(1 << 20)
+        bd = torch.from_numpy(big["data"]).cuda()
+        bq = torch.from_numpy(big["queries"]).cuda()
+        bo = torch.empty(bq.shape[0], device="cuda")
+        headline_pairs_s = float(1 << 40) / (_events_ms(
+            lambda: idw.interpolate(bd, bq, 2.0, out=bo), 3) / 1e3)
+    row = {"instances": len(inst), "total_pairs": pairs,
+           "persistent_ms": ms_b, "persistent_pairs_s": pairs / (ms_b / 1e3),
+           "graph_replay_ms": ms_g, "graph_replay_pairs_s": pairs / (ms_g / 1e3),
+           "loop_ms": ms_l, "loop_pairs_s": pairs / (ms_l / 1e3),
+           "single_large_instance_pairs_s": headline_pairs_s,
+           "persistent_vs_single": (pairs / (ms_b / 1e3)) / headline_pairs_s,
+           "persistent_vs_loop": ms_l / ms_b}
+    _emit("batched: 256 problems, N_i, M_i log-uniform in [1024, 262144] (seeded), uniform "
+          "[0,1)^2, p=2, FP32-compensated; one persistent launch (also graph-captured) vs a "
+          "loop of per-instance calls; single large instance = N=M=2^20", [row])
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
-    else:
+        return
+    if args.config in ("headline", "all"):
         run_ours(args, ws, rank, local)
+    if rank != 0 or args.config == "headline":
+        return
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1402_4986_gb300 import build as libbuild
+    libbuild.build()
+    for name, fn in (("scale", run_scale), ("clustered", run_clustered),
+                     ("adjoint", run_adjoint), ("batched", run_batched)):
+        if args.config in (name, "all"):
+            fn(args)
 
 
 if __name__ == "__main__":

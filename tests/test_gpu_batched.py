@@ -85,3 +85,29 @@ def test_batch_is_deterministic(idw):
     b = idw.interpolate_batched(d, q, 2.0)
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+def test_batched_call_is_graph_capturable(idw):
+    """The batched entry point only enqueues work on the caller's stream, so a
+    CUDA graph of it replays to the same results (after one warm-up call that
+    sizes the workspace)."""
+    sizes = [(3000, 2000), (40, 7000), (12000, 900), (1, 5)]
+    probs = _problems(sizes, 1200)
+    d = [torch.from_numpy(pr["data"]).cuda() for pr in probs]
+    q = [torch.from_numpy(pr["queries"]).cuda() for pr in probs]
+    outs = [torch.empty(x.shape[0], device="cuda") for x in q]
+    eager = [o.clone() for o in idw.interpolate_batched(d, q, 2.0)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        idw.interpolate_batched(d, q, 2.0, outs=outs)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        idw.interpolate_batched(d, q, 2.0, outs=outs)
+    for o in outs:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(eager, outs):
+        assert torch.equal(a, b)
