@@ -460,6 +460,21 @@ def run_batched(args, headline_pairs_s=None):
 
     ms_b = _events_ms(batched, 5)
     ms_l = _events_ms(loop, 3)
+    # Autotuned: the first call of the size class times every sweep variant.
+    ht = idw.Handle(torch.cuda.current_device())
+    idw.set_option("autotune", 1, handle=ht)
+    t0 = time.perf_counter()
+    idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht)
+    torch.cuda.synchronize()
+    tune_s = time.perf_counter() - t0
+    ms_t = _events_ms(lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 5)
+    tuned_variant = idw.get_option("last_variant", handle=ht)
+    per_variant = {}
+    for v in range(4):
+        idw.set_option("sweep_variant", v, handle=ht)
+        per_variant[v] = pairs / (_events_ms(
+            lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 3) / 1e3)
+    ht.close()
     graph = torch.cuda.CUDAGraph()
     batched()
     torch.cuda.synchronize()
@@ -482,6 +497,8 @@ def run_batched(args, headline_pairs_s=None):
            "persistent_ms": ms_b, "persistent_pairs_s": pairs / (ms_b / 1e3),
            "graph_replay_ms": ms_g, "graph_replay_pairs_s": pairs / (ms_g / 1e3),
            "loop_ms": ms_l, "loop_pairs_s": pairs / (ms_l / 1e3),
+           "autotuned_variant": tuned_variant, "autotuned_pairs_s": pairs / (ms_t / 1e3),
+           "autotune_first_call_s": tune_s, "pairs_s_per_variant": per_variant,
            "single_large_instance_pairs_s": headline_pairs_s,
            "persistent_vs_single": (pairs / (ms_b / 1e3)) / headline_pairs_s,
            "persistent_vs_loop": ms_l / ms_b}

@@ -177,6 +177,41 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
                             double p, idw_precision prec, idw_plan_info *plan);
 
 /*
+ * Handle options (the paper has no counterpart; these tune the sweep).
+ *   IDW_OPT_AUTOTUNE            0/1 (default 0).  When 1, the first
+ *       FP32-compensated call of each size class (weight form, log2 of the
+ *       mean n and m and of the number of pairs) runs every compiled sweep
+ *       variant on the call's stream, timed with CUDA events, and keeps the
+ *       fastest for that class; calls made while the stream is being
+ *       captured use the default instead.  If the environment variable
+ *       IDW_AUTOTUNE_CACHE names a file when the handle is created, tuned
+ *       classes are read from and written to it (JSON).
+ *   IDW_OPT_SWEEP_VARIANT       -1 (default: autotuned or 0) or a variant:
+ *       0: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal;
+ *       1: 2048 queries per CTA, no shared reciprocal;
+ *       2: 2048 queries per CTA, 2 of 4 query pairs share a reciprocal;
+ *       3: 1024 queries per CTA, 1 of 4 query pairs shares a reciprocal.
+ *       The persistent grid always fills the GPU, so the number of pieces
+ *       each query tile is split into (the split-N factor) follows from the
+ *       query-tile size and the problem sizes.
+ *   IDW_OPT_FORCE_GENERAL_POWER 0/1: evaluate p = 2 through the log2/exp2
+ *       form used for other p (for comparing the two forms).
+ *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
+ *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
+ * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
+ */
+typedef enum {
+    IDW_OPT_AUTOTUNE = 1,
+    IDW_OPT_SWEEP_VARIANT = 2,
+    IDW_OPT_FORCE_GENERAL_POWER = 3,
+    IDW_OPT_LAST_VARIANT = 4,
+    IDW_OPT_TUNED_CLASSES = 5
+} idw_option;
+
+idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);
+idw_status idw_get_option(idw_handle_t handle, idw_option option, int64_t *value);
+
+/*
  * Kernel timing (tracing).  While enabled, every forward call records a pair
  * of CUDA events around its all-pairs sweep kernel on the call's stream.
  * idw_profile_read synchronises those events, returns the summed sweep time

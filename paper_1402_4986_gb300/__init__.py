@@ -22,7 +22,7 @@ __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
     "interpolate_batched", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
-    "selftest_bounded_wait", "PREC_F32_COMP", "PREC_F64_PLAIN",
+    "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
 
 _PREC = {"f32c": PREC_F32_COMP, "f32_comp": PREC_F32_COMP, PREC_F32_COMP: PREC_F32_COMP,
@@ -238,6 +238,20 @@ def sync_status(device=None, handle: Handle | None = None):
     s = torch.cuda.current_stream(h.device)
     _lib.check(h.lib.idw_sync_status(h.ptr, ctypes.c_void_p(s.cuda_stream)), "idw_sync_status",
                h.ptr)
+
+
+def set_option(name: str, value: int, handle: Handle | None = None):
+    """Set a handle option: autotune, sweep_variant, force_general_power."""
+    h = handle or get_handle()
+    _lib.check(h.lib.idw_set_option(h.ptr, _lib.OPTIONS[name], int(value)), "idw_set_option")
+
+
+def get_option(name: str, handle: Handle | None = None) -> int:
+    """Read a handle option (also last_variant, tuned_classes)."""
+    h = handle or get_handle()
+    v = ctypes.c_int64()
+    _lib.check(h.lib.idw_get_option(h.ptr, _lib.OPTIONS[name], ctypes.byref(v)), "idw_get_option")
+    return v.value
 
 
 def profile_enable(enable: bool = True, handle: Handle | None = None):

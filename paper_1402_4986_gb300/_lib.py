@@ -31,6 +31,8 @@ STATUS = {
 }
 PREC_F32_COMP = 0
 PREC_F64_PLAIN = 1
+OPTIONS = {"autotune": 1, "sweep_variant": 2, "force_general_power": 3, "last_variant": 4,
+           "tuned_classes": 5}
 
 
 class PlanInfo(ctypes.Structure):
@@ -72,6 +74,8 @@ SIGNATURES = {
     "idw_plan_forward": (c_int, [c_int32, c_int32, c_int64, c_int64, c_double, c_int,
                                  ctypes.POINTER(PlanInfo)]),
     "idw_measure_pipe_rates": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "idw_set_option": (c_int, [c_void_p, c_int, c_int64]),
+    "idw_get_option": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
     "idw_profile_enable": (c_int, [c_void_p, c_int]),
     "idw_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "idw_selftest_bounded_wait": (c_int, [c_void_p, c_void_p]),

@@ -7,6 +7,11 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
 #include <vector>
 
 #include "idw.h"
@@ -21,7 +26,13 @@ struct idw_handle_s {
   void* io = nullptr;  // device buffers of the host-pointer entry point
   size_t io_bytes = 0;
   idw::Control* ctrl = nullptr;  // device control words
-  int occ_f32_pow2 = 0, occ_f32_general = 0, occ_f64 = 0, occ_bwd = 0;
+  int occ_f64 = 0, occ_bwd = 0;
+  int occ_f32[2][idw::kNumSweepVariants] = {};  // [general p][variant]
+  // Options (idw_set_option).
+  int opt_autotune = 0, opt_variant = -1, opt_force_general = 0;
+  int last_variant = -1;
+  std::map<std::string, int> tuned;  // size class -> sweep variant
+  std::string tune_path;             // JSON cache file ("" = memory only)
   char last_cuda[256] = "no error";
   bool profiling = false;
   std::vector<idw::SweepEvents> events;  // recorded sweep launches, oldest first
@@ -125,17 +136,111 @@ void destroy_events(idw_handle_t h) {
   h->events_used = 0;
 }
 
-int ctas_per_sm(idw_handle_t h, idw_precision prec, double p) {
+bool uses_general_power(idw_handle_t h, double p) { return p != 2.0 || h->opt_force_general; }
+
+int ctas_per_sm(idw_handle_t h, idw_precision prec, double p, int variant = 0) {
   if (prec == IDW_PREC_F64_PLAIN) {
     if (!h->occ_f64) h->occ_f64 = idw::occupancy_forward_f64();
     return h->occ_f64;
   }
-  if (p == 2.0) {
-    if (!h->occ_f32_pow2) h->occ_f32_pow2 = idw::occupancy_forward_f32(false);
-    return h->occ_f32_pow2;
+  const int gen = uses_general_power(h, p) ? 1 : 0;
+  int& occ = h->occ_f32[gen][variant];
+  if (!occ) occ = idw::occupancy_forward_f32(gen != 0, variant);
+  return occ;
+}
+
+// ------------------------------------------------------------- autotuner
+// Size class of a batch: weight form, and log2 of the mean data and query
+// counts and of the total number of pairs.
+std::string size_class(idw_handle_t h, const idw::F32Problem* probs, int count, double p) {
+  double n = 0, m = 0, pairs = 0;
+  for (int k = 0; k < count; ++k) {
+    n += double(probs[k].n);
+    m += double(probs[k].m);
+    pairs += double(probs[k].n) * double(probs[k].m);
   }
-  if (!h->occ_f32_general) h->occ_f32_general = idw::occupancy_forward_f32(true);
-  return h->occ_f32_general;
+  std::ostringstream o;
+  o << "sm" << h->sm_count << (uses_general_power(h, p) ? "_gen" : "_pow2") << "_n"
+    << int(std::lround(std::log2(n / count))) << "_m" << int(std::lround(std::log2(m / count)))
+    << "_pairs" << int(std::lround(std::log2(pairs)));
+  return o.str();
+}
+
+void load_tuning(idw_handle_t h) {
+  if (h->tune_path.empty()) return;
+  std::ifstream f(h->tune_path);
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t a = line.find('"'), b = line.find('"', a + 1), c = line.find(':', b + 1);
+    if (a == std::string::npos || b == std::string::npos || c == std::string::npos) continue;
+    const int v = std::atoi(line.c_str() + c + 1);
+    if (v >= 0 && v < idw::kNumSweepVariants) h->tuned[line.substr(a + 1, b - a - 1)] = v;
+  }
+}
+
+void save_tuning(idw_handle_t h) {
+  if (h->tune_path.empty()) return;
+  const std::string tmp = h->tune_path + ".tmp";
+  {
+    std::ofstream f(tmp);
+    f << "{\n";
+    size_t k = 0;
+    for (const auto& kv : h->tuned)
+      f << "  \"" << kv.first << "\": " << kv.second << (++k < h->tuned.size() ? ",\n" : "\n");
+    f << "}\n";
+  }
+  std::rename(tmp.c_str(), h->tune_path.c_str());
+}
+
+// Sweep variant for a batch: forced, tuned (timed once per size class with
+// CUDA events, never while the stream is being captured), or the default.
+int choose_variant(idw_handle_t h, const idw::F32Problem* probs, int count, double p,
+                   cudaStream_t s) {
+  if (h->opt_variant >= 0) return h->opt_variant;
+  if (!h->opt_autotune) return 0;
+  const std::string key = size_class(h, probs, count, p);
+  auto it = h->tuned.find(key);
+  if (it != h->tuned.end()) return it->second;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+    return 0;
+  std::vector<idw::BatchPlan> plans(idw::kNumSweepVariants);
+  size_t need = 0;
+  for (int v = 0; v < idw::kNumSweepVariants; ++v) {
+    idw::plan_batch_f32(probs, count, h->sm_count, ctas_per_sm(h, IDW_PREC_F32_COMP, p, v), v,
+                        &plans[v]);
+    plans[v].force_general = h->opt_force_general != 0;
+    need = std::max(need, plans[v].workspace_bytes);
+  }
+  if (ensure_buffer(h, &h->ws, &h->ws_bytes, need) != IDW_OK) return 0;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return 0;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return 0;
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < idw::kNumSweepVariants; ++v) {
+    float ms = 0.f;
+    bool ok = true;
+    for (int rep = 0; rep < 2 && ok; ++rep) {  // the first run loads the module
+      ok = cudaEventRecord(a, s) == cudaSuccess &&
+           idw::launch_batch_f32(probs, plans[v], p, h->ws, h->ctrl, h->sm_count, nullptr, s) ==
+               cudaSuccess &&
+           cudaEventRecord(b, s) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    }
+    if (ok && (v == 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->tuned[key] = best;
+  save_tuning(h);
+  return best;
 }
 
 idw_status check_common(idw_handle_t h, const void* data, int64_t n, const void* queries,
@@ -190,6 +295,10 @@ idw_status idw_create(idw_handle_t* out, int device) {
     delete h;
     return IDW_ERR_CUDA;
   }
+  if (const char* path = std::getenv("IDW_AUTOTUNE_CACHE")) {
+    h->tune_path = path;
+    load_tuning(h);
+  }
   *out = h;
   return IDW_OK;
 }
@@ -221,10 +330,13 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
   if (prec == IDW_PREC_F32_COMP) {
     idw::F32Problem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m,
                        static_cast<float*>(out), s0_out, hit_out};
+    const int v = choose_variant(h, &pb, 1, p, s);
     idw::BatchPlan bp;
-    idw::plan_batch_f32(&pb, 1, h->sm_count, ctas_per_sm(h, prec, p), &bp);
+    idw::plan_batch_f32(&pb, 1, h->sm_count, ctas_per_sm(h, prec, p, v), v, &bp);
+    bp.force_general = h->opt_force_general != 0;
     st = ensure_buffer(h, &h->ws, &h->ws_bytes, bp.workspace_bytes);
     if (st != IDW_OK) return st;
+    h->last_variant = v;
     e = idw::launch_batch_f32(&pb, bp, p, h->ws, h->ctrl, h->sm_count, next_events(h), s);
   } else {
     Plan plan;
@@ -292,18 +404,20 @@ idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* co
   if (probs.empty()) return IDW_OK;
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
-  const int ctas = ctas_per_sm(h, prec, p);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   std::vector<idw::BatchPlan> plans;
   size_t need = 0;
   for (size_t b = 0; b < probs.size(); b += idw::kBatchCap) {
     const int c = static_cast<int>(std::min<size_t>(idw::kBatchCap, probs.size() - b));
+    const int v = choose_variant(h, &probs[b], c, p, s);
     plans.emplace_back();
-    idw::plan_batch_f32(&probs[b], c, h->sm_count, ctas, &plans.back());
+    idw::plan_batch_f32(&probs[b], c, h->sm_count, ctas_per_sm(h, prec, p, v), v, &plans.back());
+    plans.back().force_general = h->opt_force_general != 0;
     need = std::max(need, plans.back().workspace_bytes);
+    h->last_variant = v;
   }
   idw_status st = ensure_buffer(h, &h->ws, &h->ws_bytes, need);
   if (st != IDW_OK) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (size_t c = 0; c < plans.size(); ++c) {
     cudaError_t e = idw::launch_batch_f32(&probs[c * idw::kBatchCap], plans[c], p, h->ws, h->ctrl,
                                           h->sm_count, next_events(h), s);
@@ -364,6 +478,36 @@ idw_status idw_sync_status(idw_handle_t h, void* stream) {
   return IDW_OK;
 }
 
+idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
+  if (!h) return IDW_ERR_INVALID_ARG;
+  switch (opt) {
+    case IDW_OPT_AUTOTUNE:
+      h->opt_autotune = value != 0;
+      return IDW_OK;
+    case IDW_OPT_SWEEP_VARIANT:
+      if (value < -1 || value >= idw::kNumSweepVariants) return IDW_ERR_INVALID_ARG;
+      h->opt_variant = static_cast<int>(value);
+      return IDW_OK;
+    case IDW_OPT_FORCE_GENERAL_POWER:
+      h->opt_force_general = value != 0;
+      return IDW_OK;
+    default:
+      return IDW_ERR_INVALID_ARG;
+  }
+}
+
+idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
+  if (!h || !value) return IDW_ERR_INVALID_ARG;
+  switch (opt) {
+    case IDW_OPT_AUTOTUNE: *value = h->opt_autotune; return IDW_OK;
+    case IDW_OPT_SWEEP_VARIANT: *value = h->opt_variant; return IDW_OK;
+    case IDW_OPT_FORCE_GENERAL_POWER: *value = h->opt_force_general; return IDW_OK;
+    case IDW_OPT_LAST_VARIANT: *value = h->last_variant; return IDW_OK;
+    case IDW_OPT_TUNED_CLASSES: *value = static_cast<int64_t>(h->tuned.size()); return IDW_OK;
+    default: return IDW_ERR_INVALID_ARG;
+  }
+}
+
 idw_status idw_profile_enable(idw_handle_t h, int enable) {
   if (!h) return IDW_ERR_INVALID_ARG;
   h->profiling = enable != 0;
@@ -408,7 +552,7 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas, int64_t n, int64_t m
   if (prec == IDW_PREC_F32_COMP && m > 0) {
     idw::F32Problem pb{nullptr, n, nullptr, m, nullptr, nullptr, nullptr};
     idw::BatchPlan bp;
-    idw::plan_batch_f32(&pb, 1, sm_count, ctas, &bp);
+    idw::plan_batch_f32(&pb, 1, sm_count, ctas, 0, &bp);
     pl.grid = bp.grid;
     pl.partial_slots = bp.partial_slots;
     pl.workspace_bytes = bp.workspace_bytes;

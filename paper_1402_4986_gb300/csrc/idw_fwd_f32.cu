@@ -42,17 +42,25 @@
 namespace idw {
 namespace {
 
-constexpr int NT = kThreadsF32;
-constexpr int KP = kQueryPairsF32;
-constexpr int QT = kQueriesPerCtaF32;
 constexpr int TB = kRecordsF32;
 constexpr int ST = kStagesF32;
 constexpr int CH = kChunkF32;
-constexpr int KSHARED = 1;  // query pairs per thread that share one reciprocal (p = 2)
 constexpr uint32_t kTileBytes = static_cast<uint32_t>(kTileBytesF32);
 static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 static_assert(TB % CH == 0, "chunks tile the data tile");
-static_assert(KSHARED <= KP, "shared-reciprocal pairs are a subset of the query pairs");
+
+// Compiled sweep variants (the autotuner picks one per size class):
+// threads per CTA, query pairs per thread, and how many of those pairs share
+// one reciprocal per data point at p = 2.  Each keeps 128 registers/thread
+// and 16 resident warps per SM.
+template <int V> struct Var;
+template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1; };
+template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0; };
+template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 2; };
+template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1; };
+template <int V> __host__ __device__ constexpr int qt_of() { return Var<V>::NT * 2 * Var<V>::KP; }
+static_assert(kNumSweepVariants == 4, "variant table");
+static_assert(qt_of<0>() == kQueriesPerCtaF32, "default variant is the documented tiling");
 
 struct SweepArgs {
   int64_t units;
@@ -90,9 +98,10 @@ __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
   }
 }
 
-template <int MODE, int CAP>
-__global__ void __launch_bounds__(NT, 2)
+template <int MODE, int CAP, int V>
+__global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
+  constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[ST];
 
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(NT, 2)
 
 // FP64 combine of the pieces of each query: Z = S1 / S0, or a flag that
 // routes the query to the slow path (exact hit or FP32 range exceeded).
-template <int CAP>
+template <int CAP, int QT>
 __global__ void __launch_bounds__(256)
     combine_kernel(const __grid_constant__ Table<CAP> t, const float4* __restrict__ partial,
                    int64_t total_slots, int64_t units, int grid, const float* __restrict__ scales,
@@ -282,7 +291,7 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-template <int CAP>
+template <int CAP, int V>
 cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p,
                         unsigned char* ws, Control* ctrl, int sm_count, const SweepEvents* ev,
                         cudaStream_t stream) {
@@ -316,7 +325,7 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
 
-  const bool pow2 = (p == 2.0);
+  const bool pow2 = (p == 2.0) && !plan.force_general;
   const unsigned gx = static_cast<unsigned>(std::min<int64_t>(64, (longest + 4095) / 4096));
   range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
   const int64_t records = plan.total_data_tiles * TB;
@@ -336,15 +345,16 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   a.err = &ctrl->error;
   const size_t smem = size_t(ST) * kTileBytes;
   if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
+  constexpr int NT = Var<V>::NT, QT = qt_of<V>();
   if (pow2)
-    sweep_kernel<kPow2, CAP><<<plan.grid, NT, smem, stream>>>(a, t);
+    sweep_kernel<kPow2, CAP, V><<<plan.grid, NT, smem, stream>>>(a, t);
   else
-    sweep_kernel<kPowGeneral, CAP><<<plan.grid, NT, smem, stream>>>(a, t);
+    sweep_kernel<kPowGeneral, CAP, V><<<plan.grid, NT, smem, stream>>>(a, t);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
 
   const int64_t slots = plan.total_query_tiles * QT;
-  combine_kernel<CAP><<<static_cast<unsigned>((slots + 255) / 256), 256, 0, stream>>>(
+  combine_kernel<CAP, QT><<<static_cast<unsigned>((slots + 255) / 256), 256, 0, stream>>>(
       t, partial, slots, plan.units, plan.grid, scales, p, ctrl, list);
   slow_batch_kernel<CAP><<<2 * sm_count, kSlowThreads, 0, stream>>>(t, p, ctrl, list);
   return cudaGetLastError();
@@ -352,8 +362,19 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
 
 }  // namespace
 
+int sweep_variant_queries_per_cta(int variant) {
+  switch (variant) {
+    case 1: return qt_of<1>();
+    case 2: return qt_of<2>();
+    case 3: return qt_of<3>();
+    default: return qt_of<0>();
+  }
+}
+
 void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
-                    BatchPlan* bp) {
+                    int variant, BatchPlan* bp) {
+  const int QT = sweep_variant_queries_per_cta(variant);
+  bp->variant = variant;
   bp->count = count;
   bp->data_tiles.assign(count, 0);
   bp->query_tiles.assign(count, 0);
@@ -391,22 +412,42 @@ cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, dou
                              void* workspace, Control* ctrl, int sm_count,
                              const SweepEvents* ev, cudaStream_t stream) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
-  if (plan.count == 1) return launch_impl<1>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
-  if (plan.count <= kBatchCap)
-    return launch_impl<kBatchCap>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
-  return cudaErrorInvalidValue;
+  if (plan.count < 1 || plan.count > kBatchCap) return cudaErrorInvalidValue;
+  const bool one = plan.count == 1;
+#define IDW_LAUNCH(V)                                                                        \
+  return one ? launch_impl<1, V>(probs, plan, p, ws, ctrl, sm_count, ev, stream)           \
+             : launch_impl<kBatchCap, V>(probs, plan, p, ws, ctrl, sm_count, ev, stream)
+  switch (plan.variant) {
+    case 1: IDW_LAUNCH(1);
+    case 2: IDW_LAUNCH(2);
+    case 3: IDW_LAUNCH(3);
+    default: IDW_LAUNCH(0);
+  }
+#undef IDW_LAUNCH
 }
 
-int occupancy_forward_f32(bool general_p) {
+namespace {
+template <int V>
+int occupancy_variant(bool general_p) {
   int blocks = 0;
   const size_t smem = size_t(ST) * kTileBytes;
   if (general_p)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPowGeneral, kBatchCap>,
-                                                  NT, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &blocks, sweep_kernel<kPowGeneral, kBatchCap, V>, Var<V>::NT, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap>, NT,
-                                                  smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V>,
+                                                  Var<V>::NT, smem);
   return blocks > 0 ? blocks : 1;
+}
+}  // namespace
+
+int occupancy_forward_f32(bool general_p, int variant) {
+  switch (variant) {
+    case 1: return occupancy_variant<1>(general_p);
+    case 2: return occupancy_variant<2>(general_p);
+    case 3: return occupancy_variant<3>(general_p);
+    default: return occupancy_variant<0>(general_p);
+  }
 }
 
 cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream) {

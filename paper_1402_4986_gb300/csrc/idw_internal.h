@@ -22,6 +22,9 @@ constexpr int kChunkF32 = 32;
 constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 8 B (z,z)
 // Instances per batched launch (the instance table is a kernel parameter).
 constexpr int kBatchCap = 256;
+// Compiled variants of the FP32 sweep (query-tile size, shared reciprocals);
+// variant 0 is the default tiling above.
+constexpr int kNumSweepVariants = 4;
 
 // Plain FP64 forward: kQueriesF64 queries per thread; tiles of (x,y) + z.
 constexpr int kThreadsF64 = 128;
@@ -68,6 +71,8 @@ struct F32Problem {
 // Work units are (query tile, data tile) pairs numbered instance by
 // instance, query-tile-major; CTA g sweeps [g U / G, (g + 1) U / G).
 struct BatchPlan {
+  int variant = 0;
+  bool force_general = false;  // evaluate p = 2 through the log2/exp2 path
   int count = 0;
   std::vector<int64_t> data_tiles, query_tiles, unit_base, qtile_base, tile_offset;
   int64_t units = 0, total_query_tiles = 0, total_data_tiles = 0;
@@ -79,13 +84,14 @@ struct BatchPlan {
 
 // Host arithmetic only.  Problems must have n >= 1 and m >= 1.
 void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
-                    BatchPlan* plan);
+                    int variant, BatchPlan* plan);
+int sweep_variant_queries_per_cta(int variant);
 
 // Enqueues range scan, staging, sweep, combine and slow path for the batch.
 cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, double p,
                              void* workspace, Control* ctrl, int sm_count,
                              const SweepEvents* ev, cudaStream_t stream);
-int occupancy_forward_f32(bool general_p);
+int occupancy_forward_f32(bool general_p, int variant);
 
 // Failure-detection self-test: a bounded wait on a barrier nobody completes.
 cudaError_t launch_bounded_wait_selftest(Control* ctrl, cudaStream_t stream);

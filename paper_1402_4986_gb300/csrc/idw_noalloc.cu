@@ -63,8 +63,8 @@ idw_status setup_current_device(DeviceSetup* out) {
     if (cudaMemset(ptr, 0, kControlBytes) != cudaSuccess) return IDW_ERR_CUDA;
     s.scratch = static_cast<unsigned char*>(ptr);
     s.sm_count = sms;
-    s.occ_pow2 = occupancy_forward_f32(false);
-    s.occ_general = occupancy_forward_f32(true);
+    s.occ_pow2 = occupancy_forward_f32(false, 0);
+    s.occ_general = occupancy_forward_f32(true, 0);
     s.ready = true;
   }
   *out = s;
@@ -93,7 +93,7 @@ extern "C" idw_status idw_interpolate_noalloc(const float* data_xyz, int64_t n,
   // The same launch plan as idw_interpolate (host arithmetic only).
   F32Problem pb{data_xyz, n, queries_xy, m, out, nullptr, nullptr};
   BatchPlan plan;
-  plan_batch_f32(&pb, 1, dev.sm_count, p == 2.0 ? dev.occ_pow2 : dev.occ_general, &plan);
+  plan_batch_f32(&pb, 1, dev.sm_count, p == 2.0 ? dev.occ_pow2 : dev.occ_general, 0, &plan);
   if (plan.workspace_bytes > kNoAllocScratchBytes - kControlBytes) return IDW_ERR_WORKSPACE;
 
   Control* ctrl = reinterpret_cast<Control*>(dev.scratch);
