@@ -63,7 +63,8 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="headline",
-                    choices=["headline", "scale", "clustered", "adjoint", "batched", "all"],
+                    choices=["headline", "scale", "clustered", "adjoint", "batched", "layout",
+                             "all"],
                     help="headline = the N=M=2^20 line; the others measure the other "
                          "workloads (one JSON line each)")
     return ap.parse_args()
@@ -470,7 +471,7 @@ def run_batched(args, headline_pairs_s=None):
     ms_t = _events_ms(lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 5)
     tuned_variant = idw.get_option("last_variant", handle=ht)
     per_variant = {}
-    for v in range(4):
+    for v in range(5):
         idw.set_option("sweep_variant", v, handle=ht)
         per_variant[v] = pairs / (_events_ms(
             lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 3) / 1e3)
@@ -507,6 +508,37 @@ def run_batched(args, headline_pairs_s=None):
           "loop of per-instance calls; single large instance = N=M=2^20", [row])
 
 
+def run_layout(args):
+    """Staging-layout ablation of the single-problem sweep (Sec. 2.2, 3.3)."""
+    import torch
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    names = {0: "duplicated pairs (x,x,y,y)+(z,z), 24 B/point",
+             1: "aligned AoS (x,y,z,pad), 16 B/point", 2: "SoA x[],y[],z[], 12 B/point"}
+    rows = []
+    for n in (100_000, 1 << 20):
+        prob = synthetic.config_scale(n)
+        d = torch.from_numpy(prob["data"]).cuda()
+        q = torch.from_numpy(prob["queries"]).cuda()
+        out = torch.empty(n, device="cuda")
+        for p in (2.0, 3.5):
+            for layout in (0, 1, 2):
+                h = idw.Handle(torch.cuda.current_device())
+                idw.set_option("sweep_variant", 0, handle=h)
+                idw.set_option("staging_layout", layout, handle=h)
+                reps = 3 if n > 200_000 else 20
+                ms = _events_ms(lambda: idw.interpolate(d, q, p, out=out, handle=h), reps)
+                idw.profile_enable(True, handle=h)
+                idw.interpolate(d, q, p, out=out, handle=h)
+                sweep_ms, _ = idw.profile_read(handle=h)
+                h.close()
+                rows.append({"n": n, "m": n, "p": p, "layout": layout, "layout_name": names[layout],
+                             "pairs_s": float(n) * n / (ms / 1e3), "call_ms": ms,
+                             "sweep_ms": sweep_ms})
+    _emit("staging-layout ablation: same sweep (variant 0) on data tiles staged as duplicated "
+          "pairs, aligned AoS or SoA; N=M, uniform [0,1)^2, wave field", rows)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -522,7 +554,8 @@ def main():
     from paper_1402_4986_gb300 import build as libbuild
     libbuild.build()
     for name, fn in (("scale", run_scale), ("clustered", run_clustered),
-                     ("adjoint", run_adjoint), ("batched", run_batched)):
+                     ("adjoint", run_adjoint), ("batched", run_batched),
+                     ("layout", run_layout)):
         if args.config in (name, "all"):
             fn(args)
 

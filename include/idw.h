@@ -186,16 +186,27 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *       captured use the default instead.  If the environment variable
  *       IDW_AUTOTUNE_CACHE names a file when the handle is created, tuned
  *       classes are read from and written to it (JSON).
- *   IDW_OPT_SWEEP_VARIANT       -1 (default: autotuned or 0) or a variant:
+ *   IDW_OPT_SWEEP_VARIANT       -1 (default: autotuned if enabled, else 4
+ *       when its 4096-query tiles pad the queries within 1% of variant 0's,
+ *       else 0) or a variant:
  *       0: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal;
  *       1: 2048 queries per CTA, no shared reciprocal;
  *       2: 2048 queries per CTA, 2 of 4 query pairs share a reciprocal;
- *       3: 1024 queries per CTA, 1 of 4 query pairs shares a reciprocal.
+ *       3: 1024 queries per CTA, 1 of 4 query pairs shares a reciprocal;
+ *       4: 4096 queries per CTA (one 512-thread CTA per SM), as variant 0.
  *       The persistent grid always fills the GPU, so the number of pieces
  *       each query tile is split into (the split-N factor) follows from the
  *       query-tile size and the problem sizes.
  *   IDW_OPT_FORCE_GENERAL_POWER 0/1: evaluate p = 2 through the log2/exp2
  *       form used for other p (for comparing the two forms).
+ *   IDW_OPT_STAGING_LAYOUT      layout of the staged data tiles: -1 (default)
+ *       picks per weight form, 1 at p = 2 and 0 otherwise (the faster of
+ *       each on GB300); 0 duplicated pair records (x,x,y,y)+(z,z),
+ *       24 B/point; 1 the paper's aligned AoS record (x,y,z,pad),
+ *       16 B/point (Sec. 3.3); 2 SoA arrays x, y, z, 12 B/point (Sec. 2.2).
+ *       Layouts 1 and 2 build the register pairs with moves.  A forced
+ *       layout applies to single FP32 problems with sweep variant 0 (the
+ *       layout ablation) and is ignored otherwise.
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -205,7 +216,8 @@ typedef enum {
     IDW_OPT_SWEEP_VARIANT = 2,
     IDW_OPT_FORCE_GENERAL_POWER = 3,
     IDW_OPT_LAST_VARIANT = 4,
-    IDW_OPT_TUNED_CLASSES = 5
+    IDW_OPT_TUNED_CLASSES = 5,
+    IDW_OPT_STAGING_LAYOUT = 6
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

@@ -32,7 +32,7 @@ STATUS = {
 PREC_F32_COMP = 0
 PREC_F64_PLAIN = 1
 OPTIONS = {"autotune": 1, "sweep_variant": 2, "force_general_power": 3, "last_variant": 4,
-           "tuned_classes": 5}
+           "tuned_classes": 5, "staging_layout": 6}
 
 
 class PlanInfo(ctypes.Structure):

@@ -29,7 +29,7 @@ struct idw_handle_s {
   int occ_f64 = 0, occ_bwd = 0;
   int occ_f32[2][idw::kNumSweepVariants] = {};  // [general p][variant]
   // Options (idw_set_option).
-  int opt_autotune = 0, opt_variant = -1, opt_force_general = 0;
+  int opt_autotune = 0, opt_variant = -1, opt_force_general = 0, opt_layout = -1;
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
   std::string tune_path;             // JSON cache file ("" = memory only)
@@ -194,16 +194,29 @@ void save_tuning(idw_handle_t h) {
 
 // Sweep variant for a batch: forced, tuned (timed once per size class with
 // CUDA events, never while the stream is being captured), or the default.
+// Default without tuning: one 512-thread CTA per SM (variant 4) keeps all 16
+// warps of an SM in step; it is used when its 4096-query tiles pad the
+// queries no more than variant 0's 2048-query tiles do (plus 1%).
+int default_variant(const idw::F32Problem* probs, int count) {
+  const int64_t q4 = idw::sweep_variant_queries_per_cta(4), q0 = idw::sweep_variant_queries_per_cta(0);
+  double pad4 = 0, pad0 = 0;
+  for (int k = 0; k < count; ++k) {
+    pad4 += double((probs[k].m + q4 - 1) / q4 * q4);
+    pad0 += double((probs[k].m + q0 - 1) / q0 * q0);
+  }
+  return pad4 <= 1.01 * pad0 ? 4 : 0;
+}
+
 int choose_variant(idw_handle_t h, const idw::F32Problem* probs, int count, double p,
                    cudaStream_t s) {
   if (h->opt_variant >= 0) return h->opt_variant;
-  if (!h->opt_autotune) return 0;
+  if (!h->opt_autotune) return default_variant(probs, count);
   const std::string key = size_class(h, probs, count, p);
   auto it = h->tuned.find(key);
   if (it != h->tuned.end()) return it->second;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-    return 0;
+    return default_variant(probs, count);
   std::vector<idw::BatchPlan> plans(idw::kNumSweepVariants);
   size_t need = 0;
   for (int v = 0; v < idw::kNumSweepVariants; ++v) {
@@ -334,6 +347,7 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
     idw::BatchPlan bp;
     idw::plan_batch_f32(&pb, 1, h->sm_count, ctas_per_sm(h, prec, p, v), v, &bp);
     bp.force_general = h->opt_force_general != 0;
+    bp.layout = v == 0 ? h->opt_layout : -1;
     st = ensure_buffer(h, &h->ws, &h->ws_bytes, bp.workspace_bytes);
     if (st != IDW_OK) return st;
     h->last_variant = v;
@@ -491,6 +505,10 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
     case IDW_OPT_FORCE_GENERAL_POWER:
       h->opt_force_general = value != 0;
       return IDW_OK;
+    case IDW_OPT_STAGING_LAYOUT:
+      if (value < -1 || value > 2) return IDW_ERR_INVALID_ARG;
+      h->opt_layout = static_cast<int>(value);
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -504,6 +522,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_FORCE_GENERAL_POWER: *value = h->opt_force_general; return IDW_OK;
     case IDW_OPT_LAST_VARIANT: *value = h->last_variant; return IDW_OK;
     case IDW_OPT_TUNED_CLASSES: *value = static_cast<int64_t>(h->tuned.size()); return IDW_OK;
+    case IDW_OPT_STAGING_LAYOUT: *value = h->opt_layout; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

@@ -15,6 +15,17 @@ namespace {
 constexpr int kTB32 = kRecordsF32;
 constexpr uint32_t kTileBytes32 = static_cast<uint32_t>(kTileBytesF32);
 
+// Staging layouts of a data tile (the layout ablation; 0 is the default):
+//   0  duplicated pair records: kTB32 x (x,x,y,y) then kTB32 x (z,z), 24 B/point;
+//   1  aligned AoS (the paper's AoaS record): kTB32 x (x,y,z,pad), 16 B/point;
+//   2  SoA: kTB32 x x, then kTB32 x y, then kTB32 x z, 12 B/point.
+template <int LAYOUT>
+__host__ __device__ constexpr uint32_t tile_bytes_of() {
+  return LAYOUT == 0 ? 24u * kTB32 : (LAYOUT == 1 ? 16u * kTB32 : 12u * kTB32);
+}
+static_assert(tile_bytes_of<0>() == kTileBytes32, "default layout");
+static_assert(tile_bytes_of<1>() % 16 == 0 && tile_bytes_of<2>() % 16 == 0, "bulk copy sizes");
+
 // Padding records of the p = 2 form sit at (2^63, 2^63): for any query with
 // |coordinate| <= 2^10, d^2 = 2^127, whose reciprocal is subnormal and
 // flushes to 0, and the shared product overflows to +inf, whose reciprocal
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(256) range_kernel(const __grid_constant__ Tabl
 
 // Stages each problem's n x 3 rows into tiles of kTB32 records: kTB32 x (x,x,y,y)
 // then kTB32 x (z,z), coordinates scaled by the problem's power of two.
-template <int CAP, int MODE>
+template <int CAP, int MODE, int LAYOUT = 0>
 __global__ void __launch_bounds__(256)
     stage_kernel(const __grid_constant__ Table<CAP> t, int64_t total_records,
                  const unsigned* __restrict__ maxbits, float* __restrict__ scales) {
@@ -138,10 +149,19 @@ __global__ void __launch_bounds__(256)
     y = I.data[3 * lr + 1] * s;
     z = I.data[3 * lr + 2];
   }
-  unsigned char* base = I.tiles + (lr / kTB32) * kTileBytes32;
+  unsigned char* base = I.tiles + (lr / kTB32) * tile_bytes_of<LAYOUT>();
   const int slot = static_cast<int>(lr % kTB32);
-  reinterpret_cast<float4*>(base)[slot] = make_float4(x, x, y, y);
-  reinterpret_cast<float2*>(base + kTB32 * 16)[slot] = make_float2(z, z);
+  if (LAYOUT == 0) {
+    reinterpret_cast<float4*>(base)[slot] = make_float4(x, x, y, y);
+    reinterpret_cast<float2*>(base + kTB32 * 16)[slot] = make_float2(z, z);
+  } else if (LAYOUT == 1) {
+    reinterpret_cast<float4*>(base)[slot] = make_float4(x, y, z, 0.f);
+  } else {
+    float* f = reinterpret_cast<float*>(base);
+    f[slot] = x;
+    f[kTB32 + slot] = y;
+    f[2 * kTB32 + slot] = z;
+  }
 }
 
 

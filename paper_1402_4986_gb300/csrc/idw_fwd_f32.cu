@@ -20,7 +20,7 @@
 //     this moves work from the MUFU pipe (the binding one) to the FMA pipe.
 //     General p: 2^(-(p/2) log2 d^2) with the product's rounding error
 //     recovered by an FMA and applied to first order;
-//   * sums run in chunks of kChunkF32 points; each chunk sum is folded into
+//   * sums run in chunks of 64 (p = 2) or 32 points; each chunk sum is folded into
 //     (hi, lo) pairs by Knuth's TwoSum, so the error does not grow with n;
 //   * the (problem, query tile, data tile) work units are split evenly over
 //     a grid of co-resident CTAs (stream-K).  Pieces of a query tile are
@@ -44,22 +44,23 @@ namespace {
 
 constexpr int TB = kRecordsF32;
 constexpr int ST = kStagesF32;
-constexpr int CH = kChunkF32;
 constexpr uint32_t kTileBytes = static_cast<uint32_t>(kTileBytesF32);
 static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-static_assert(TB % CH == 0, "chunks tile the data tile");
+static_assert(TB % kChunkF32Pow2 == 0 && TB % kChunkF32General == 0, "chunks tile a data tile");
 
 // Compiled sweep variants (the autotuner picks one per size class):
 // threads per CTA, query pairs per thread, and how many of those pairs share
 // one reciprocal per data point at p = 2.  Each keeps 128 registers/thread
-// and 16 resident warps per SM.
+// and 16 resident warps per SM (variant 4: all 16 in one CTA, which keeps
+// them in step at every tile barrier).
 template <int V> struct Var;
 template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1; };
 template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0; };
 template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 2; };
 template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1; };
+template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1; };
 template <int V> __host__ __device__ constexpr int qt_of() { return Var<V>::NT * 2 * Var<V>::KP; }
-static_assert(kNumSweepVariants == 4, "variant table");
+static_assert(kNumSweepVariants == 5, "variant table");
 static_assert(qt_of<0>() == kQueriesPerCtaF32, "default variant is the documented tiling");
 
 struct SweepArgs {
@@ -98,10 +99,36 @@ __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
   }
 }
 
-template <int MODE, int CAP, int V>
+// The record of data point c + r of a staged tile as three register pairs
+// (x,x), (y,y), (z,z), for each staging layout.
+template <int LAYOUT>
+__device__ __forceinline__ void load_record(const unsigned char* tile, int i, u64& xx, u64& yy,
+                                            u64& zz) {
+  if (LAYOUT == 0) {
+    const ulonglong2 xy = reinterpret_cast<const ulonglong2*>(tile)[i];
+    xx = xy.x;
+    yy = xy.y;
+    zz = reinterpret_cast<const u64*>(tile + TB * 16)[i];
+  } else if (LAYOUT == 1) {
+    const float4 v = reinterpret_cast<const float4*>(tile)[i];
+    xx = pk(v.x, v.x);
+    yy = pk(v.y, v.y);
+    zz = pk(v.z, v.z);
+  } else {
+    const float* f = reinterpret_cast<const float*>(tile);
+    const float x = f[i], y = f[TB + i], z = f[2 * TB + i];
+    xx = pk(x, x);
+    yy = pk(y, y);
+    zz = pk(z, z);
+  }
+}
+
+template <int MODE, int CAP, int V, int LAYOUT = 0>
 __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
   constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
+  constexpr int CH = MODE == kPow2 ? kChunkF32Pow2 : kChunkF32General;
+  constexpr uint32_t kTileBytes = tile_bytes_of<LAYOUT>();
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[ST];
 
@@ -165,19 +192,18 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
       const uint32_t parity = static_cast<uint32_t>((i / ST) & 1);
       const bool ok = mbar_wait_bounded(smem_u32(&full_bar[s]), parity, a.err);
       if (ok) {
-        const ulonglong2* XY = reinterpret_cast<const ulonglong2*>(smem + s * kTileBytes);
-        const u64* ZZ = reinterpret_cast<const u64*>(smem + s * kTileBytes + TB * 16);
+        const unsigned char* tile = smem + s * kTileBytes;
 #pragma unroll 1
         for (int c = 0; c < TB; c += CH) {
           u64 C0[KP], C1[KP];
 #pragma unroll
           for (int r = 0; r < CH; ++r) {
-            const ulonglong2 xy = XY[c + r];
-            const u64 zz = ZZ[c + r];
+            u64 xx, yy, zz;
+            load_record<LAYOUT>(tile, c + r, xx, yy, zz);
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
-              const u64 dx = sub2f(QX[k], xy.x);
-              const u64 dy = sub2f(QY[k], xy.y);
+              const u64 dx = sub2f(QX[k], xx);
+              const u64 dy = sub2f(QY[k], yy);
               const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
               const u64 w = weight_pair<MODE>(d2, k < KSHARED, hp2, nhp2);
               if (r == 0) {
@@ -291,7 +317,7 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-template <int CAP, int V>
+template <int CAP, int V, int MODE, int LAYOUT>
 cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p,
                         unsigned char* ws, Control* ctrl, int sm_count, const SweepEvents* ev,
                         cudaStream_t stream) {
@@ -312,7 +338,7 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
     I.out = probs[k].out;
     I.s0_out = probs[k].s0_out;
     I.hit_out = probs[k].hit_out;
-    I.tiles = tiles + size_t(plan.tile_offset[k]) * kTileBytes;
+    I.tiles = tiles + size_t(plan.tile_offset[k]) * tile_bytes_of<LAYOUT>();
     I.unit_base = plan.unit_base[k];
     I.record_base = plan.tile_offset[k] * TB;
     I.n = static_cast<int32_t>(probs[k].n);
@@ -325,15 +351,11 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
 
-  const bool pow2 = (p == 2.0) && !plan.force_general;
   const unsigned gx = static_cast<unsigned>(std::min<int64_t>(64, (longest + 4095) / 4096));
   range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
   const int64_t records = plan.total_data_tiles * TB;
   const unsigned sgrid = static_cast<unsigned>((records + 255) / 256);
-  if (pow2)
-    stage_kernel<CAP, kPow2><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
-  else
-    stage_kernel<CAP, kPowGeneral><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
+  stage_kernel<CAP, MODE, LAYOUT><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
 
   SweepArgs a;
   a.units = plan.units;
@@ -343,13 +365,10 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   a.partial = partial;
   a.scales = scales;
   a.err = &ctrl->error;
-  const size_t smem = size_t(ST) * kTileBytes;
+  const size_t smem = size_t(ST) * tile_bytes_of<LAYOUT>();
   if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
   constexpr int NT = Var<V>::NT, QT = qt_of<V>();
-  if (pow2)
-    sweep_kernel<kPow2, CAP, V><<<plan.grid, NT, smem, stream>>>(a, t);
-  else
-    sweep_kernel<kPowGeneral, CAP, V><<<plan.grid, NT, smem, stream>>>(a, t);
+  sweep_kernel<MODE, CAP, V, LAYOUT><<<plan.grid, NT, smem, stream>>>(a, t);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
 
@@ -367,6 +386,7 @@ int sweep_variant_queries_per_cta(int variant) {
     case 1: return qt_of<1>();
     case 2: return qt_of<2>();
     case 3: return qt_of<3>();
+    case 4: return qt_of<4>();
     default: return qt_of<0>();
   }
 }
@@ -401,7 +421,7 @@ void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_p
   const int64_t resident = int64_t(sm_count) * (ctas_per_sm > 0 ? ctas_per_sm : 1);
   bp->grid = static_cast<int>(std::max<int64_t>(1, std::min(units, resident)));
   bp->partial_slots = qtiles + bp->grid - 1;
-  bp->staged_bytes = round_up(size_t(tiles) * kTileBytes, 256);
+  bp->staged_bytes = round_up(size_t(tiles) * kTileBytes, 256);  // the widest layout
   bp->partial_bytes = round_up(size_t(bp->partial_slots) * QT * sizeof(float4), 256);
   bp->list_bytes = round_up(size_t(std::max<int64_t>(queries, 1)) * sizeof(int2), 256);
   bp->scale_bytes = round_up(size_t(count) * 8, 256);
@@ -414,13 +434,32 @@ cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, dou
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   if (plan.count < 1 || plan.count > kBatchCap) return cudaErrorInvalidValue;
   const bool one = plan.count == 1;
+  const bool pow2 = (p == 2.0) && !plan.force_general;
+  // Default staging layout per weight form (measured fastest on GB300): the
+  // aligned AoS record at p = 2, whose one shared load per point leaves the
+  // special-function queue to the reciprocals; duplicated pair records for
+  // general p, which need no register moves.  The other layouts are built
+  // for the single-problem sweep of variant 0 (the layout ablation).
+  const int layout = plan.layout >= 0 ? plan.layout : (pow2 ? 1 : 0);
+  if (one && plan.variant == 0) {
+    if (pow2 && layout == 0) return launch_impl<1, 0, kPow2, 0>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+    if (pow2 && layout == 2) return launch_impl<1, 0, kPow2, 2>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+    if (!pow2 && layout == 1) return launch_impl<1, 0, kPowGeneral, 1>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+    if (!pow2 && layout == 2) return launch_impl<1, 0, kPowGeneral, 2>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
+  }
 #define IDW_LAUNCH(V)                                                                        \
-  return one ? launch_impl<1, V>(probs, plan, p, ws, ctrl, sm_count, ev, stream)           \
-             : launch_impl<kBatchCap, V>(probs, plan, p, ws, ctrl, sm_count, ev, stream)
+  if (pow2)                                                                                  \
+    return one ? launch_impl<1, V, kPow2, 1>(probs, plan, p, ws, ctrl, sm_count, ev, stream) \
+               : launch_impl<kBatchCap, V, kPow2, 1>(probs, plan, p, ws, ctrl, sm_count, ev,  \
+                                                      stream);                               \
+  return one ? launch_impl<1, V, kPowGeneral, 0>(probs, plan, p, ws, ctrl, sm_count, ev, stream) \
+             : launch_impl<kBatchCap, V, kPowGeneral, 0>(probs, plan, p, ws, ctrl, sm_count, ev, \
+                                                         stream)
   switch (plan.variant) {
     case 1: IDW_LAUNCH(1);
     case 2: IDW_LAUNCH(2);
     case 3: IDW_LAUNCH(3);
+    case 4: IDW_LAUNCH(4);
     default: IDW_LAUNCH(0);
   }
 #undef IDW_LAUNCH
@@ -433,9 +472,9 @@ int occupancy_variant(bool general_p) {
   const size_t smem = size_t(ST) * kTileBytes;
   if (general_p)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks, sweep_kernel<kPowGeneral, kBatchCap, V>, Var<V>::NT, smem);
+        &blocks, sweep_kernel<kPowGeneral, kBatchCap, V, 0>, Var<V>::NT, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V, 1>,
                                                   Var<V>::NT, smem);
   return blocks > 0 ? blocks : 1;
 }
@@ -446,6 +485,7 @@ int occupancy_forward_f32(bool general_p, int variant) {
     case 1: return occupancy_variant<1>(general_p);
     case 2: return occupancy_variant<2>(general_p);
     case 3: return occupancy_variant<3>(general_p);
+    case 4: return occupancy_variant<4>(general_p);
     default: return occupancy_variant<0>(general_p);
   }
 }

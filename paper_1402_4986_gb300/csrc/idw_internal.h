@@ -18,13 +18,16 @@ constexpr int kQueryPairsF32 = 4;
 constexpr int kQueriesPerCtaF32 = kThreadsF32 * 2 * kQueryPairsF32;  // 2048
 constexpr int kRecordsF32 = 256;
 constexpr int kStagesF32 = 3;
-constexpr int kChunkF32 = 32;
+// Points per chunk between TwoSum folds: longer chunks cost fewer FMA-pipe
+// operations; the general-power body is longer, so it keeps shorter chunks.
+constexpr int kChunkF32Pow2 = 64;
+constexpr int kChunkF32General = 32;
 constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 8 B (z,z)
 // Instances per batched launch (the instance table is a kernel parameter).
 constexpr int kBatchCap = 256;
 // Compiled variants of the FP32 sweep (query-tile size, shared reciprocals);
 // variant 0 is the default tiling above.
-constexpr int kNumSweepVariants = 4;
+constexpr int kNumSweepVariants = 5;
 
 // Plain FP64 forward: kQueriesF64 queries per thread; tiles of (x,y) + z.
 constexpr int kThreadsF64 = 128;
@@ -73,6 +76,7 @@ struct F32Problem {
 struct BatchPlan {
   int variant = 0;
   bool force_general = false;  // evaluate p = 2 through the log2/exp2 path
+  int layout = -1;             // data-tile staging layout; -1 = default for the weight form
   int count = 0;
   std::vector<int64_t> data_tiles, query_tiles, unit_base, qtile_base, tile_offset;
   int64_t units = 0, total_query_tiles = 0, total_data_tiles = 0;
