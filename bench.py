@@ -50,6 +50,49 @@ FFMA_PER_SM_CLK = 128.0
 MUFU_PER_SM_CLK = 16.0
 FMA_OPS_PER_PAIR = 6.0   # 2 FADD (dx, dy), FMUL, FFMA (d^2), FADD (S0), FFMA (S1)
 MUFU_OPS_PER_PAIR = 1.0  # rcp(d^2) at p = 2
+# Sharing one reciprocal between two pairs trades half a MUFU op per pair for
+# 1.5 FMA-pipe ops (1/(da db), then db r and da r).
+SHARED_FMA_PER_PAIR = 1.5
+SHARED_MUFU_SAVED_PER_PAIR = 0.5
+SWEEP_SOURCES = ("idw_fwd_f32.cu", "idw_f32_common.cuh", "idw_device.cuh", "idw_internal.h")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep_p2_n1048576_dram.md")
+
+
+def lp_pairs_per_sm_clk(ffma, mufu):
+    """Best pairs per SM per clock when any fraction f of the pairs may share
+    reciprocals: max r s.t. r (6 + 1.5 f) <= ffma and r (1 - f / 2) <= mufu."""
+    best = 0.0
+    for i in range(1001):
+        f = i / 1000.0
+        best = max(best, min(ffma / (FMA_OPS_PER_PAIR + SHARED_FMA_PER_PAIR * f),
+                             mufu / (MUFU_OPS_PER_PAIR - SHARED_MUFU_SAVED_PER_PAIR * f)))
+    return best
+
+
+def sweep_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for name in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1402_4986_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current sweep sources (else None)."""
+    try:
+        text = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None
+    vals = dict(line.split(":", 1) for line in text.splitlines()
+                if line.startswith(("traffic_bytes_per_launch:", "sweep_source_sha256:")))
+    if vals.get("sweep_source_sha256:".rstrip(":"), "").strip() != sweep_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def parse():
@@ -275,9 +318,15 @@ def run_ours(args, ws, rank, local):
 
     peak_doc = peak(FFMA_PER_SM_CLK, MUFU_PER_SM_CLK, clk_mhz)
     peak_meas = peak(max(rates["ffma"], rates["ffma2"]), rates["mufu_rcp"], clk_mhz)
+    lp = sms * clk_mhz * 1e6 * lp_pairs_per_sm_clk(FFMA_PER_SM_CLK, MUFU_PER_SM_CLK)
     roof = {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_doc / 1e9,
             "unit": "Gpairs/s", "frac": achieved / peak_doc if peak_doc else None,
-            "traffic": None,
+            "traffic": recorded_traffic(),
+            "algorithmic_bytes_per_launch": 12 * n + 8 * m + 4 * m,
+            "lp_bound": lp / 1e9, "frac_of_lp_bound": achieved / lp if lp else None,
+            "lp_basis": "max pairs/s when a fraction f of pairs shares reciprocals: "
+                        "r (6 + 1.5 f) <= 128 FMA lanes and r (1 - f/2) <= 16 MUFU lanes "
+                        "per SM per clock",
             "kernel": "fwd_f32_kernel (all-pairs sweep)",
             "peak_basis": "min(128 FFMA / 6 ops, 16 MUFU / 1 op) per SM per clock x "
                           f"{sms} SMs x median SM clock {clk_mhz} MHz under load",

@@ -29,9 +29,9 @@
 namespace idw {
 namespace {
 
-constexpr int NTA = 256;             // threads per CTA
+constexpr int NTA = 512;             // threads per CTA (one CTA per SM keeps 16 warps in step)
 constexpr int KPA = 2;               // register pairs per thread
-constexpr int RT = NTA * 2 * KPA;    // register-side points per CTA tile (1024)
+constexpr int RT = NTA * 2 * KPA;    // register-side points per CTA tile (2048)
 constexpr int CHA = 32;              // chunk length between TwoSum folds
 constexpr int STA = 3;               // ring stages
 constexpr int TQ = 256;              // query records per streamed query tile
@@ -84,7 +84,7 @@ __device__ __forceinline__ void write_piece(float2* P, int comp, int idx, u64 hi
 // Query sweep: sums over data points of (z - Z) w (q - x) / d^2 (x and y)
 // and of (z - Z) w log2 d^2, per query, in scaled coordinates.
 template <bool POW2, bool NEED_P>
-__global__ void __launch_bounds__(NTA, 2) query_adj_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(NTA, 1) query_adj_kernel(const AdjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long bars[STA];
   const int tid = threadIdx.x;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(NTA, 2) query_adj_kernel(const AdjArgs a) {
 // per data point, with c_j = g_j / S0_j (scaled), in scaled coordinates.
 // Padding and excluded queries carry c = 0 at a finite far point.
 template <bool POW2>
-__global__ void __launch_bounds__(NTA, 2) data_adj_kernel(const AdjArgs a) {
+__global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long bars[STA];
   const int tid = threadIdx.x;
