@@ -455,6 +455,15 @@ def run_clustered(args):
         rows.append({"p": p, "pairs_s": float(n) * m / (ms / 1e3), "ms": ms,
                      "path": "rcp" if p == 2.0 else "log2/exp2",
                      "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+    # p = 2 through the log2/exp2 form as well.
+    hg = idw.Handle(torch.cuda.current_device())
+    idw.set_option("force_general_power", 1, handle=hg)
+    ms = _events_ms(lambda: idw.interpolate(d, q, 2.0, out=out, handle=hg), 5)
+    Z64, _ = oracle.idw(prob["data"], prob["queries"][idx], 2.0)
+    err = float(np.max(np.abs(out.cpu().numpy()[idx] - Z64)) / np.max(np.abs(prob["data"][:, 2])))
+    hg.close()
+    rows.append({"p": 2.0, "pairs_s": float(n) * m / (ms / 1e3), "ms": ms, "path": "log2/exp2",
+                 "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
     _emit("clustered: N=262144 from 64 Gaussian blobs (sigma 0.01), z = exp(-4 r^2) + "
           "0.05 N(0,1), queries on a 1024^2 grid", rows)
 

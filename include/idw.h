@@ -191,7 +191,8 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *       else 0) or a variant:
  *       0: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal;
  *       1: 2048 queries per CTA, no shared reciprocal;
- *       2: 2048 queries per CTA, 2 of 4 query pairs share a reciprocal;
+ *       2: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal
+ *          and a second one on every other data point;
  *       3: 1024 queries per CTA, 1 of 4 query pairs shares a reciprocal;
  *       4: 4096 queries per CTA (one 512-thread CTA per SM), as variant 0.
  *       The persistent grid always fills the GPU, so the number of pieces

@@ -53,12 +53,15 @@ static_assert(TB % kChunkF32Pow2 == 0 && TB % kChunkF32General == 0, "chunks til
 // one reciprocal per data point at p = 2.  Each keeps 128 registers/thread
 // and 16 resident warps per SM (variant 4: all 16 in one CTA, which keeps
 // them in step at every tile barrier).
+// KSH pairs share on every data point; pair KALT (if >= 0) also shares on
+// every other data point, so a fraction (KSH + 0.5 [KALT >= 0]) / KP of the
+// pairs share.
 template <int V> struct Var;
-template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1; };
-template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0; };
-template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 2; };
-template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1; };
-template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1; };
+template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = -1; };
+template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0, KALT = -1; };
+template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = 1; };
+template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1, KALT = -1; };
+template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1, KALT = -1; };
 template <int V> __host__ __device__ constexpr int qt_of() { return Var<V>::NT * 2 * Var<V>::KP; }
 static_assert(kNumSweepVariants == 5, "variant table");
 static_assert(qt_of<0>() == kQueriesPerCtaF32, "default variant is the documented tiling");
@@ -127,6 +130,7 @@ template <int MODE, int CAP, int V, int LAYOUT = 0>
 __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
   constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
+  constexpr int KALT = Var<V>::KALT;
   constexpr int CH = MODE == kPow2 ? kChunkF32Pow2 : kChunkF32General;
   constexpr uint32_t kTileBytes = tile_bytes_of<LAYOUT>();
   extern __shared__ __align__(128) unsigned char smem[];
@@ -205,7 +209,8 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
               const u64 dx = sub2f(QX[k], xx);
               const u64 dy = sub2f(QY[k], yy);
               const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
-              const u64 w = weight_pair<MODE>(d2, k < KSHARED, hp2, nhp2);
+              const bool shared = k < KSHARED || (k == KALT && (r & 1));
+              const u64 w = weight_pair<MODE>(d2, shared, hp2, nhp2);
               if (r == 0) {
                 C0[k] = w;
                 C1[k] = mul2(w, zz);
