@@ -32,7 +32,7 @@ namespace {
 constexpr int NTA = 512;             // threads per CTA (one CTA per SM keeps 16 warps in step)
 constexpr int KPA = 2;               // register pairs per thread
 constexpr int RT = NTA * 2 * KPA;    // register-side points per CTA tile (2048)
-constexpr int CHA = 32;              // chunk length between TwoSum folds
+constexpr int CHA = 64;              // chunk length between TwoSum folds
 constexpr int STA = 3;               // ring stages
 constexpr int TQ = 256;              // query records per streamed query tile
 constexpr uint32_t kQTileBytes = TQ * 32;  // (qx,qx,qy,qy) + (c,c,Z,Z)
@@ -56,8 +56,10 @@ struct AdjArgs {
 };
 
 // w = (d^2)^(-p/2) and v = w / d^2 on both lanes; L = log2 d^2 when asked.
+// No clamp on log2: the query sweep masks its padding records, and the data
+// sweep's padding queries sit at a finite far point (weights underflow to 0).
 template <bool POW2, bool WANT_L>
-__device__ __forceinline__ void weights(u64 d2, const AdjArgs& a, u64& w, u64& v, u64& L) {
+__device__ __forceinline__ void weights(u64 d2, u64 nhp2, u64 nhp12, u64& w, u64& v, u64& L) {
   float da, db;
   upk(d2, da, db);
   if (POW2) {
@@ -65,11 +67,12 @@ __device__ __forceinline__ void weights(u64 d2, const AdjArgs& a, u64& w, u64& v
     v = mul2(w, w);
     if (WANT_L) L = pk(lg2_approx(da), lg2_approx(db));
   } else {
-    const float la = fminf(lg2_approx(da), 1048576.f);
-    const float lb = fminf(lg2_approx(db), 1048576.f);
-    L = pk(la, lb);
-    w = pk(ex2_approx(la * a.neg_half_p), ex2_approx(lb * a.neg_half_p));
-    v = pk(ex2_approx(la * a.neg_half_p1), ex2_approx(lb * a.neg_half_p1));
+    L = pk(lg2_approx(da), lg2_approx(db));
+    float ta, tb, ua, ub;
+    upk(mul2(L, nhp2), ta, tb);   // -(p/2) L
+    upk(mul2(L, nhp12), ua, ub);  // -(p/2 + 1) L
+    w = pk(ex2_approx(ta), ex2_approx(tb));
+    v = pk(ex2_approx(ua), ex2_approx(ub));
   }
 }
 
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(NTA, 1) query_adj_kernel(const AdjArgs a) {
   ring.start();
 
   const float s = a.scales[0];
+  const u64 NHP2 = pk(a.neg_half_p, a.neg_half_p), NHP12 = pk(a.neg_half_p1, a.neg_half_p1);
   // log2 of the unscaled d^2 = log2 of the scaled one - 2 log2 s (exact).
   const float shift = -2.f * static_cast<float>(ilogbf(s));
   const u64 SHIFT = pk(shift, shift);
@@ -145,7 +149,7 @@ __global__ void __launch_bounds__(NTA, 1) query_adj_kernel(const AdjArgs a) {
                 const u64 dy = sub2f(QY[k], xy.y);
                 const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
                 u64 w, v, L = 0ull;
-                weights<POW2, NEED_P>(d2, a, w, v, L);
+                weights<POW2, NEED_P>(d2, NHP2, NHP12, w, v, L);
                 const u64 e = sub2(zz, ZQ[k]);  // z_i - Z_j
                 const u64 ev = mul2(e, v);
                 CX[k] = fma2(ev, dx, CX[k]);
@@ -197,6 +201,7 @@ __global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
   TileRing<STA, decltype(src)> ring{smem, bars, kQTileBytes, a.err, total, src, 0};
   ring.start();
   const float s = a.scales[0];
+  const u64 NHP2 = pk(a.neg_half_p, a.neg_half_p), NHP12 = pk(a.neg_half_p1, a.neg_half_p1);
 
   int64_t i = 0;
   bool aborted = false;
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
               const u64 dy = sub2f(q.y, YD[k]);
               const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
               u64 w, v, L;
-              weights<POW2, false>(d2, a, w, v, L);
+              weights<POW2, false>(d2, NHP2, NHP12, w, v, L);
               const u64 cw = mul2(cz.x, w);
               CGZ[k] = add2(CGZ[k], cw);
               const u64 b = mul2(mul2(cz.x, sub2(ZD[k], cz.y)), v);  // c (z_i - Z_j) w / d^2
