@@ -35,7 +35,7 @@ constexpr int RT = NTA * 2 * KPA;    // register-side points per CTA tile (2048)
 constexpr int CHA = 64;              // chunk length between TwoSum folds
 constexpr int STA = 3;               // ring stages
 constexpr int TQ = 256;              // query records per streamed query tile
-constexpr uint32_t kQTileBytes = TQ * 32;  // (qx,qx,qy,qy) + (c,c,Z,Z)
+constexpr uint32_t kQTileBytes = TQ * 16;  // (qx, qy, c, Z): one shared load per query
 static_assert(kTB32 % CHA == 0 && TQ % CHA == 0, "chunks tile the streamed tiles");
 
 struct AdjArgs {
@@ -84,6 +84,49 @@ __device__ __forceinline__ void write_piece(float2* P, int comp, int idx, u64 hi
   P[comp * RT + idx + NTA] = make_float2(hb, lb);
 }
 
+// One staged data tile for the query sweep.  MASKED (the last tile of a
+// sweep only) skips the padding records; full tiles run straight-line code.
+template <bool POW2, bool NEED_P, bool MASKED>
+__device__ __forceinline__ void query_tile(const unsigned char* st, int valid, u64 NHP2, u64 NHP12,
+                                           u64 SHIFT, const u64* QX, const u64* QY,
+                                           const u64* ZQ, u64* XH, u64* XL, u64* YH, u64* YL,
+                                           u64* PH, u64* PL) {
+  const ulonglong2* XY = reinterpret_cast<const ulonglong2*>(st);
+  const u64* ZZ = reinterpret_cast<const u64*>(st + kTB32 * 16);
+#pragma unroll 1
+  for (int c = 0; c < valid; c += CHA) {
+    u64 CX[KPA], CY[KPA], CP[KPA];
+#pragma unroll
+    for (int k = 0; k < KPA; ++k) CX[k] = CY[k] = CP[k] = 0ull;
+#pragma unroll
+    for (int r = 0; r < CHA; ++r) {
+      if (!MASKED || c + r < valid) {  // uniform across the CTA
+        const ulonglong2 xy = XY[c + r];
+        const u64 zz = ZZ[c + r];
+#pragma unroll
+        for (int k = 0; k < KPA; ++k) {
+          const u64 dx = sub2f(QX[k], xy.x);
+          const u64 dy = sub2f(QY[k], xy.y);
+          const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
+          u64 w, v, L = 0ull;
+          weights<POW2, NEED_P>(d2, NHP2, NHP12, w, v, L);
+          const u64 e = sub2(zz, ZQ[k]);  // z_i - Z_j
+          const u64 ev = mul2(e, v);
+          CX[k] = fma2(ev, dx, CX[k]);
+          CY[k] = fma2(ev, dy, CY[k]);
+          if (NEED_P) CP[k] = fma2(mul2(e, w), add2(L, SHIFT), CP[k]);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPA; ++k) {
+      two_sum_acc(XH[k], XL[k], CX[k]);
+      two_sum_acc(YH[k], YL[k], CY[k]);
+      if (NEED_P) two_sum_acc(PH[k], PL[k], CP[k]);
+    }
+  }
+}
+
 // Query sweep: sums over data points of (z - Z) w (q - x) / d^2 (x and y)
 // and of (z - Z) w log2 d^2, per query, in scaled coordinates.
 template <bool POW2, bool NEED_P>
@@ -129,42 +172,13 @@ __global__ void __launch_bounds__(NTA, 1) query_adj_kernel(const AdjArgs a) {
       bool ok;
       const unsigned char* st = ring.wait(i, ok);
       if (ok) {
-        const ulonglong2* XY = reinterpret_cast<const ulonglong2*>(st);
-        const u64* ZZ = reinterpret_cast<const u64*>(st + kTB32 * 16);
         const bool last = ((u0 + i) % a.stream_tiles) == a.stream_tiles - 1;
-        const int valid = last ? static_cast<int>(last_valid) : kTB32;
-#pragma unroll 1
-        for (int c = 0; c < valid; c += CHA) {
-          u64 CX[KPA], CY[KPA], CP[KPA];
-#pragma unroll
-          for (int k = 0; k < KPA; ++k) CX[k] = CY[k] = CP[k] = 0ull;
-#pragma unroll
-          for (int r = 0; r < CHA; ++r) {
-            if (c + r < valid) {  // uniform across the CTA; false only in the last tile
-              const ulonglong2 xy = XY[c + r];
-              const u64 zz = ZZ[c + r];
-#pragma unroll
-              for (int k = 0; k < KPA; ++k) {
-                const u64 dx = sub2f(QX[k], xy.x);
-                const u64 dy = sub2f(QY[k], xy.y);
-                const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
-                u64 w, v, L = 0ull;
-                weights<POW2, NEED_P>(d2, NHP2, NHP12, w, v, L);
-                const u64 e = sub2(zz, ZQ[k]);  // z_i - Z_j
-                const u64 ev = mul2(e, v);
-                CX[k] = fma2(ev, dx, CX[k]);
-                CY[k] = fma2(ev, dy, CY[k]);
-                if (NEED_P) CP[k] = fma2(mul2(e, w), add2(L, SHIFT), CP[k]);
-              }
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < KPA; ++k) {
-            two_sum_acc(XH[k], XL[k], CX[k]);
-            two_sum_acc(YH[k], YL[k], CY[k]);
-            if (NEED_P) two_sum_acc(PH[k], PL[k], CP[k]);
-          }
-        }
+        if (last && last_valid < kTB32)
+          query_tile<POW2, NEED_P, true>(st, static_cast<int>(last_valid), NHP2, NHP12, SHIFT, QX,
+                                         QY, ZQ, XH, XL, YH, YL, PH, PL);
+        else
+          query_tile<POW2, NEED_P, false>(st, kTB32, NHP2, NHP12, SHIFT, QX, QY, ZQ, XH, XL, YH,
+                                          YL, PH, PL);
       }
       if (!ring.release(ok)) {
         aborted = true;
@@ -224,8 +238,7 @@ __global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
       bool ok;
       const unsigned char* st = ring.wait(i, ok);
       if (ok) {
-        const ulonglong2* QQ = reinterpret_cast<const ulonglong2*>(st);           // (qx,qx),(qy,qy)
-        const ulonglong2* CZ = reinterpret_cast<const ulonglong2*>(st + TQ * 16); // (c,c),(Z,Z)
+        const float4* QR = reinterpret_cast<const float4*>(st);  // (qx, qy, c, Z)
 #pragma unroll 1
         for (int c = 0; c < TQ; c += CHA) {
           u64 CGZ[KPA], CGX[KPA], CGY[KPA];
@@ -233,18 +246,19 @@ __global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
           for (int k = 0; k < KPA; ++k) CGZ[k] = CGX[k] = CGY[k] = 0ull;
 #pragma unroll
           for (int r = 0; r < CHA; ++r) {
-            const ulonglong2 q = QQ[c + r];
-            const ulonglong2 cz = CZ[c + r];
+            const float4 qr = QR[c + r];
+            const u64 qxx = pk(qr.x, qr.x), qyy = pk(qr.y, qr.y);
+            const u64 cc = pk(qr.z, qr.z), zq = pk(qr.w, qr.w);
 #pragma unroll
             for (int k = 0; k < KPA; ++k) {
-              const u64 dx = sub2f(q.x, XD[k]);  // q_j - x_i
-              const u64 dy = sub2f(q.y, YD[k]);
+              const u64 dx = sub2f(qxx, XD[k]);  // q_j - x_i
+              const u64 dy = sub2f(qyy, YD[k]);
               const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
               u64 w, v, L;
               weights<POW2, false>(d2, NHP2, NHP12, w, v, L);
-              const u64 cw = mul2(cz.x, w);
+              const u64 cw = mul2(cc, w);
               CGZ[k] = add2(CGZ[k], cw);
-              const u64 b = mul2(mul2(cz.x, sub2(ZD[k], cz.y)), v);  // c (z_i - Z_j) w / d^2
+              const u64 b = mul2(mul2(cc, sub2(ZD[k], zq)), v);  // c (z_i - Z_j) w / d^2
               CGX[k] = fma2(b, dx, CGX[k]);
               CGY[k] = fma2(b, dy, CGY[k]);
             }
@@ -274,8 +288,8 @@ __global__ void __launch_bounds__(NTA, 1) data_adj_kernel(const AdjArgs a) {
   if (aborted) ring.drain(i);
 }
 
-// Streamed query records of the data sweep: (s qx, s qx, s qy, s qy) and
-// (c, c, Z, Z), c = g / S0_scaled.  Excluded and padding queries sit at a
+// Streamed query records of the data sweep: (s qx, s qy, c, Z) with
+// c = g / S0_scaled (tiles of TQ records are consecutive).  Excluded and padding queries sit at a
 // far finite point with c = 0.
 __global__ void __launch_bounds__(256)
     stage_queries_kernel(const float* __restrict__ queries, int64_t m, int64_t records,
@@ -294,10 +308,7 @@ __global__ void __launch_bounds__(256)
     c = static_cast<float>(double(g[j]) * pow(double(s), p) / s0[j]);
     z = Z[j];
   }
-  unsigned char* base = tiles + (j / TQ) * kQTileBytes;
-  const int slot = static_cast<int>(j % TQ);
-  reinterpret_cast<float4*>(base)[slot] = make_float4(qx, qx, qy, qy);
-  reinterpret_cast<float4*>(base + TQ * 16)[slot] = make_float4(c, c, z, z);
+  reinterpret_cast<float4*>(tiles)[j] = make_float4(qx, qy, c, z);
 }
 
 __device__ __forceinline__ void piece_range(int64_t rt, int64_t stream_tiles, int64_t units,
