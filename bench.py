@@ -529,7 +529,7 @@ def run_batched(args, headline_pairs_s=None):
     ms_t = _events_ms(lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 5)
     tuned_variant = idw.get_option("last_variant", handle=ht)
     per_variant = {}
-    for v in range(5):
+    for v in range(6):
         idw.set_option("sweep_variant", v, handle=ht)
         per_variant[v] = pairs / (_events_ms(
             lambda: idw.interpolate_batched(d, q, 2.0, outs=outs, handle=ht), 3) / 1e3)

@@ -186,15 +186,18 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *       captured use the default instead.  If the environment variable
  *       IDW_AUTOTUNE_CACHE names a file when the handle is created, tuned
  *       classes are read from and written to it (JSON).
- *   IDW_OPT_SWEEP_VARIANT       -1 (default: autotuned if enabled, else 4
- *       when its 4096-query tiles pad the queries within 1% of variant 0's,
- *       else 0) or a variant:
+ *   IDW_OPT_SWEEP_VARIANT       -1 (default: autotuned if enabled; else, at
+ *       p = 2, variant 5 for problems with fewer than 4 work units of 256
+ *       points x 2048 queries per resident CTA; else 4 when its 4096-query
+ *       tiles pad the queries within 1% of variant 0's; else 0) or:
  *       0: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal;
  *       1: 2048 queries per CTA, no shared reciprocal;
  *       2: 2048 queries per CTA, 1 of 4 query pairs shares a reciprocal
  *          and a second one on every other data point;
  *       3: 1024 queries per CTA, 1 of 4 query pairs shares a reciprocal;
- *       4: 4096 queries per CTA (one 512-thread CTA per SM), as variant 0.
+ *       4: 4096 queries per CTA (one 512-thread CTA per SM), as variant 0;
+ *       5: as variant 0 with work units of 64 data points instead of 256
+ *          (p = 2 only; other p run variant 0).
  *       The persistent grid always fills the GPU, so the number of pieces
  *       each query tile is split into (the split-N factor) follows from the
  *       query-tile size and the problem sizes.

@@ -194,32 +194,49 @@ void save_tuning(idw_handle_t h) {
 
 // Sweep variant for a batch: forced, tuned (timed once per size class with
 // CUDA events, never while the stream is being captured), or the default.
-// Default without tuning: one 512-thread CTA per SM (variant 4) keeps all 16
-// warps of an SM in step; it is used when its 4096-query tiles pad the
-// queries no more than variant 0's 2048-query tiles do (plus 1%).
-int default_variant(const idw::F32Problem* probs, int count) {
+// Default without tuning.  Small p = 2 problems (fewer than four
+// 256-point work units per resident CTA) use the fine-grained variant 5, so
+// the grid stays full and balanced; otherwise one 512-thread CTA per SM
+// (variant 4) keeps all 16 warps of an SM in step, when its 4096-query
+// tiles pad the queries no more than variant 0's 2048-query tiles (+1%).
+int default_variant(idw_handle_t h, const idw::F32Problem* probs, int count, double p) {
   const int64_t q4 = idw::sweep_variant_queries_per_cta(4), q0 = idw::sweep_variant_queries_per_cta(0);
-  double pad4 = 0, pad0 = 0;
+  const int64_t tb = idw::sweep_variant_points_per_unit(0);
+  double pad4 = 0, pad0 = 0, units0 = 0;
   for (int k = 0; k < count; ++k) {
     pad4 += double((probs[k].m + q4 - 1) / q4 * q4);
     pad0 += double((probs[k].m + q0 - 1) / q0 * q0);
+    units0 += double((probs[k].m + q0 - 1) / q0) * double((probs[k].n + tb - 1) / tb);
   }
+  if (!uses_general_power(h, p) && units0 < 4.0 * h->sm_count * 2) return 5;
   return pad4 <= 1.01 * pad0 ? 4 : 0;
 }
 
+int choose_variant_unresolved(idw_handle_t h, const idw::F32Problem* probs, int count, double p,
+                              cudaStream_t s);
+
+// The sweep variant for a batch, resolved for the weight form.
 int choose_variant(idw_handle_t h, const idw::F32Problem* probs, int count, double p,
                    cudaStream_t s) {
+  return idw::resolve_sweep_variant(choose_variant_unresolved(h, probs, count, p, s),
+                                    uses_general_power(h, p));
+}
+
+int choose_variant_unresolved(idw_handle_t h, const idw::F32Problem* probs, int count, double p,
+                              cudaStream_t s) {
   if (h->opt_variant >= 0) return h->opt_variant;
-  if (!h->opt_autotune) return default_variant(probs, count);
+  if (!h->opt_autotune) return default_variant(h, probs, count, p);
   const std::string key = size_class(h, probs, count, p);
   auto it = h->tuned.find(key);
   if (it != h->tuned.end()) return it->second;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
-    return default_variant(probs, count);
+    return default_variant(h, probs, count, p);
   std::vector<idw::BatchPlan> plans(idw::kNumSweepVariants);
   size_t need = 0;
+  const bool general = uses_general_power(h, p);
   for (int v = 0; v < idw::kNumSweepVariants; ++v) {
+    if (idw::resolve_sweep_variant(v, general) != v) continue;
     idw::plan_batch_f32(probs, count, h->sm_count, ctas_per_sm(h, IDW_PREC_F32_COMP, p, v), v,
                         &plans[v]);
     plans[v].force_general = h->opt_force_general != 0;
@@ -235,6 +252,7 @@ int choose_variant(idw_handle_t h, const idw::F32Problem* probs, int count, doub
   int best = 0;
   float best_ms = 0.f;
   for (int v = 0; v < idw::kNumSweepVariants; ++v) {
+    if (idw::resolve_sweep_variant(v, general) != v) continue;
     float ms = 0.f;
     bool ok = true;
     for (int rep = 0; rep < 2 && ok; ++rep) {  // the first run loads the module

@@ -601,7 +601,7 @@ cudaError_t launch_backward_f32(const BwdProblem& pb, const BwdPlan& bp, void* w
   if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
   const int64_t longest = std::max(pb.n, pb.m);
-  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(64, (longest + 4095) / 4096));
+  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(1024, (longest + 255) / 256));
   range_kernel<1><<<dim3(gx, 1), 256, 0, stream>>>(t, maxbits);
   // Data tiles with finite far padding (both weight forms); the query sweep
   // masks the padding of its last tile, and products with it stay finite.

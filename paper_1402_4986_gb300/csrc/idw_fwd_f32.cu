@@ -56,14 +56,19 @@ static_assert(TB % kChunkF32Pow2 == 0 && TB % kChunkF32General == 0, "chunks til
 // KSH pairs share on every data point; pair KALT (if >= 0) also shares on
 // every other data point, so a fraction (KSH + 0.5 [KALT >= 0]) / KP of the
 // pairs share.
+// TBV is the number of data points per work unit: 256 (one staging tile),
+// or 64 for the fine-grained variant 5, which splits small problems into
+// four times as many units; it needs the record-contiguous aligned-AoS
+// staging (p = 2).
 template <int V> struct Var;
-template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = -1; };
-template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0, KALT = -1; };
-template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = 1; };
-template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1, KALT = -1; };
-template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1, KALT = -1; };
+template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = -1, TBV = 256; };
+template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0, KALT = -1, TBV = 256; };
+template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = 1, TBV = 256; };
+template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1, KALT = -1, TBV = 256; };
+template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1, KALT = -1, TBV = 256; };
+template <> struct Var<5> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = -1, TBV = 64; };
 template <int V> __host__ __device__ constexpr int qt_of() { return Var<V>::NT * 2 * Var<V>::KP; }
-static_assert(kNumSweepVariants == 5, "variant table");
+static_assert(kNumSweepVariants == 6, "variant table");
 static_assert(qt_of<0>() == kQueriesPerCtaF32, "default variant is the documented tiling");
 
 struct SweepArgs {
@@ -132,7 +137,12 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
   constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
   constexpr int KALT = Var<V>::KALT;
   constexpr int CH = MODE == kPow2 ? kChunkF32Pow2 : kChunkF32General;
-  constexpr uint32_t kTileBytes = tile_bytes_of<LAYOUT>();
+  constexpr int TBU = Var<V>::TBV;
+  static_assert(TBU == TB || LAYOUT == 1, "sub-tile units need record-contiguous staging");
+  static_assert(TBU % CH == 0, "chunks tile a work unit");
+  // Bytes of one work unit's data: a whole staging tile, or a slice of the
+  // record-contiguous aligned-AoS array.
+  constexpr uint32_t kTileBytes = TBU == TB ? tile_bytes_of<LAYOUT>() : TBU * 16u;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[ST];
 
@@ -198,7 +208,7 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
       if (ok) {
         const unsigned char* tile = smem + s * kTileBytes;
 #pragma unroll 1
-        for (int c = 0; c < TB; c += CH) {
+        for (int c = 0; c < TBU; c += CH) {
           u64 C0[KP], C1[KP];
 #pragma unroll
           for (int r = 0; r < CH; ++r) {
@@ -262,26 +272,49 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
 
 // FP64 combine of the pieces of each query: Z = S1 / S0, or a flag that
 // routes the query to the slow path (exact hit or FP32 range exceeded).
+// One CTA covers 32 consecutive query slots (lanes x) and splits each
+// query's pieces over 8 warps (lanes y, strided); every warp's loads are
+// coalesced across its 32 queries, and the 8 partial sums are added in a
+// fixed order, so the result is deterministic.
+constexpr int kCombineQueries = 32;
+constexpr int kCombineLanes = 8;
+
 template <int CAP, int QT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
     combine_kernel(const __grid_constant__ Table<CAP> t, const float4* __restrict__ partial,
                    int64_t total_slots, int64_t units, int grid, const float* __restrict__ scales,
                    double p, Control* __restrict__ ctrl, int2* __restrict__ list) {
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= total_slots) return;
+  __shared__ double red0[kCombineLanes][kCombineQueries], red1[kCombineLanes][kCombineQueries];
+  const int lx = threadIdx.x % kCombineQueries, ly = threadIdx.x / kCombineQueries;
+  const int64_t idx = int64_t(blockIdx.x) * kCombineQueries + lx;
+  bool valid = idx < total_slots;
   const int64_t qtg = idx / QT, lq = idx % QT;
-  const int k = find_qtile(t, qtg);
+  const int k = valid ? find_qtile(t, qtg) : 0;
   const Instance& I = t.inst[k];
   const int64_t qt = qtg - I.qtile_base;
   const int64_t j = qt * QT + lq;
-  if (j >= I.m) return;
-  const int64_t g0 = cta_of_unit(I.unit_base + qt * I.data_tiles, units, grid);
-  const int64_t g1 = cta_of_unit(I.unit_base + (qt + 1) * I.data_tiles - 1, units, grid);
+  valid = valid && j < I.m;
   double s0 = 0.0, s1 = 0.0;
-  for (int64_t g = g0; g <= g1; ++g) {
-    const float4 v = partial[(qtg + g) * QT + lq];
-    s0 += double(v.x) + double(v.y);
-    s1 += double(v.z) + double(v.w);
+  if (valid) {
+    const int64_t g0 = cta_of_unit(I.unit_base + qt * I.data_tiles, units, grid);
+    const int64_t g1 = cta_of_unit(I.unit_base + (qt + 1) * I.data_tiles - 1, units, grid);
+#pragma unroll 4
+    for (int64_t g = g0 + ly; g <= g1; g += kCombineLanes) {
+      const float4 v = partial[(qtg + g) * QT + lq];
+      s0 += double(v.x) + double(v.y);
+      s1 += double(v.z) + double(v.w);
+    }
+  }
+  red0[ly][lx] = s0;
+  red1[ly][lx] = s1;
+  __syncthreads();
+  if (ly != 0 || !valid) return;
+  s0 = red0[0][lx];
+  s1 = red1[0][lx];
+#pragma unroll
+  for (int y = 1; y < kCombineLanes; ++y) {
+    s0 += red0[y][lx];
+    s1 += red1[y][lx];
   }
   if (!(s0 > kTinySumPerPoint * double(I.n)) || !isfinite(s0) || !isfinite(s1)) {
     const unsigned slot = atomicAdd(&ctrl->flagged, 1u);
@@ -356,9 +389,9 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return e;
 
-  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(64, (longest + 4095) / 4096));
+  const unsigned gx = static_cast<unsigned>(std::min<int64_t>(1024, (longest + 255) / 256));
   range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
-  const int64_t records = plan.total_data_tiles * TB;
+  const int64_t records = plan.total_stage_tiles * TB;
   const unsigned sgrid = static_cast<unsigned>((records + 255) / 256);
   stage_kernel<CAP, MODE, LAYOUT><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
 
@@ -370,7 +403,8 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   a.partial = partial;
   a.scales = scales;
   a.err = &ctrl->error;
-  const size_t smem = size_t(ST) * tile_bytes_of<LAYOUT>();
+  const size_t smem =
+      size_t(ST) * (Var<V>::TBV == TB ? tile_bytes_of<LAYOUT>() : Var<V>::TBV * 16u);
   if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
   constexpr int NT = Var<V>::NT, QT = qt_of<V>();
   sweep_kernel<MODE, CAP, V, LAYOUT><<<plan.grid, NT, smem, stream>>>(a, t);
@@ -378,7 +412,8 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
 
   const int64_t slots = plan.total_query_tiles * QT;
-  combine_kernel<CAP, QT><<<static_cast<unsigned>((slots + 255) / 256), 256, 0, stream>>>(
+  combine_kernel<CAP, QT><<<static_cast<unsigned>((slots + kCombineQueries - 1) / kCombineQueries),
+                            kCombineQueries * kCombineLanes, 0, stream>>>(
       t, partial, slots, plan.units, plan.grid, scales, p, ctrl, list);
   slow_batch_kernel<CAP><<<2 * sm_count, kSlowThreads, 0, stream>>>(t, p, ctrl, list);
   return cudaGetLastError();
@@ -392,13 +427,29 @@ int sweep_variant_queries_per_cta(int variant) {
     case 2: return qt_of<2>();
     case 3: return qt_of<3>();
     case 4: return qt_of<4>();
+    case 5: return qt_of<5>();
     default: return qt_of<0>();
   }
+}
+
+int sweep_variant_points_per_unit(int variant) {
+  switch (variant) {
+    case 5: return Var<5>::TBV;
+    default: return TB;
+  }
+}
+
+int resolve_sweep_variant(int variant, bool general_form) {
+  if (variant < 0 || variant >= kNumSweepVariants) return 0;
+  // Sub-tile work units need the aligned-AoS staging of the p = 2 form.
+  if (general_form && sweep_variant_points_per_unit(variant) != TB) return 0;
+  return variant;
 }
 
 void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
                     int variant, BatchPlan* bp) {
   const int QT = sweep_variant_queries_per_cta(variant);
+  const int TBU = sweep_variant_points_per_unit(variant);
   bp->variant = variant;
   bp->count = count;
   bp->data_tiles.assign(count, 0);
@@ -408,7 +459,8 @@ void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_p
   bp->tile_offset.assign(count, 0);
   int64_t units = 0, qtiles = 0, tiles = 0, queries = 0;
   for (int k = 0; k < count; ++k) {
-    const int64_t dt = (probs[k].n + TB - 1) / TB;
+    const int64_t dt = (probs[k].n + TBU - 1) / TBU;  // work units along the data
+    const int64_t st = (probs[k].n + TB - 1) / TB;    // staging tiles
     const int64_t qt = (probs[k].m + QT - 1) / QT;
     bp->data_tiles[k] = dt;
     bp->query_tiles[k] = qt;
@@ -417,12 +469,12 @@ void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_p
     bp->tile_offset[k] = tiles;
     units += dt * qt;
     qtiles += qt;
-    tiles += dt;
+    tiles += st;
     queries += probs[k].m;
   }
   bp->units = units;
   bp->total_query_tiles = qtiles;
-  bp->total_data_tiles = tiles;
+  bp->total_stage_tiles = tiles;
   const int64_t resident = int64_t(sm_count) * (ctas_per_sm > 0 ? ctas_per_sm : 1);
   bp->grid = static_cast<int>(std::max<int64_t>(1, std::min(units, resident)));
   bp->partial_slots = qtiles + bp->grid - 1;
@@ -465,6 +517,12 @@ cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, dou
     case 2: IDW_LAUNCH(2);
     case 3: IDW_LAUNCH(3);
     case 4: IDW_LAUNCH(4);
+    case 5:
+      if (pow2)
+        return one ? launch_impl<1, 5, kPow2, 1>(probs, plan, p, ws, ctrl, sm_count, ev, stream)
+                   : launch_impl<kBatchCap, 5, kPow2, 1>(probs, plan, p, ws, ctrl, sm_count, ev,
+                                                         stream);
+      return cudaErrorInvalidValue;  // resolve_sweep_variant maps it away for general p
     default: IDW_LAUNCH(0);
   }
 #undef IDW_LAUNCH
@@ -475,12 +533,15 @@ template <int V>
 int occupancy_variant(bool general_p) {
   int blocks = 0;
   const size_t smem = size_t(ST) * kTileBytes;
-  if (general_p)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks, sweep_kernel<kPowGeneral, kBatchCap, V, 0>, Var<V>::NT, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V, 1>,
-                                                  Var<V>::NT, smem);
+  if constexpr (Var<V>::TBV == TB) {
+    if (general_p) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &blocks, sweep_kernel<kPowGeneral, kBatchCap, V, 0>, Var<V>::NT, smem);
+      return blocks > 0 ? blocks : 1;
+    }
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V, 1>,
+                                                Var<V>::NT, smem);
   return blocks > 0 ? blocks : 1;
 }
 }  // namespace
@@ -491,6 +552,7 @@ int occupancy_forward_f32(bool general_p, int variant) {
     case 2: return occupancy_variant<2>(general_p);
     case 3: return occupancy_variant<3>(general_p);
     case 4: return occupancy_variant<4>(general_p);
+    case 5: return general_p ? occupancy_variant<0>(true) : occupancy_variant<5>(false);
     default: return occupancy_variant<0>(general_p);
   }
 }

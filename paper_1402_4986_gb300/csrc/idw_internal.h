@@ -27,7 +27,7 @@ constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 
 constexpr int kBatchCap = 256;
 // Compiled variants of the FP32 sweep (query-tile size, shared reciprocals);
 // variant 0 is the default tiling above.
-constexpr int kNumSweepVariants = 5;
+constexpr int kNumSweepVariants = 6;
 
 // Plain FP64 forward: kQueriesF64 queries per thread; tiles of (x,y) + z.
 constexpr int kThreadsF64 = 128;
@@ -79,7 +79,7 @@ struct BatchPlan {
   int layout = -1;             // data-tile staging layout; -1 = default for the weight form
   int count = 0;
   std::vector<int64_t> data_tiles, query_tiles, unit_base, qtile_base, tile_offset;
-  int64_t units = 0, total_query_tiles = 0, total_data_tiles = 0;
+  int64_t units = 0, total_query_tiles = 0, total_stage_tiles = 0;
   int grid = 0;
   int64_t partial_slots = 0;
   size_t staged_bytes = 0, partial_bytes = 0, list_bytes = 0, scale_bytes = 0;
@@ -90,6 +90,9 @@ struct BatchPlan {
 void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_per_sm,
                     int variant, BatchPlan* plan);
 int sweep_variant_queries_per_cta(int variant);
+int sweep_variant_points_per_unit(int variant);
+// The variant actually run: sub-tile variants fall back to 0 for general p.
+int resolve_sweep_variant(int variant, bool general_form);
 
 // Enqueues range scan, staging, sweep, combine and slow path for the batch.
 cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, double p,
