@@ -107,7 +107,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "scale", "clustered", "adjoint", "batched", "layout",
-                             "all"],
+                             "paper", "all"],
                     help="headline = the N=M=2^20 line; the others measure the other "
                          "workloads (one JSON line each)")
     return ap.parse_args()
@@ -597,6 +597,43 @@ def run_layout(args):
           "pairs, aligned AoS or SoA; N=M, uniform [0,1)^2, wave field", rows)
 
 
+def run_paper(args):
+    """The paper's naive and tiled kernels in its layouts vs this library, at
+    the paper's sizes (N = M, 1K = 1024, Sec. 4.1), p = 2."""
+    import torch
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    rows = []
+    for n, fp64_too in ((10 * 1024, True), (100 * 1024, True), (1000 * 1024, False)):
+        prob = synthetic.config_scale(n)
+        d32 = torch.from_numpy(prob["data"]).cuda()
+        q32 = torch.from_numpy(prob["queries"]).cuda()
+        pairs = float(n) * n
+        reps = 1 if n > 500_000 else 3
+        ms = _events_ms(lambda: idw.interpolate(d32, q32, 2.0), reps)
+        rows.append({"n": n, "precision": "f32", "kernel": "this library (compensated)",
+                     "layout": "staged", "pairs_s": pairs / (ms / 1e3)})
+        for prec, d, q, layouts in (
+                ("f32", d32, q32, ("soa", "aos", "aoas")),
+                ("f64", d32.double(), q32.double(), ("soa", "aos", "aoas", "hybrid"))):
+            if prec == "f64" and not fp64_too:
+                continue
+            if prec == "f64":
+                ms = _events_ms(lambda: idw.interpolate(d, q, 2.0, "f64"), 1)
+                rows.append({"n": n, "precision": "f64", "kernel": "this library (plain FP64)",
+                             "layout": "hybrid", "pairs_s": pairs / (ms / 1e3)})
+            for kernel in ("naive", "tiled"):
+                for layout in layouts:
+                    pr = "f32c" if prec == "f32" else "f64"
+                    ms = _events_ms(lambda: idw.paper_interpolate(d, q, 2.0, kernel=kernel,
+                                                                  layout=layout, precision=pr),
+                                    1 if (prec == "f64" or n > 500_000) else reps)
+                    rows.append({"n": n, "precision": prec, "kernel": kernel, "layout": layout,
+                                 "pairs_s": pairs / (ms / 1e3)})
+    _emit("the paper's naive and tiled kernels (plain sums) in its layouts vs this library; "
+          "N = M in {10K, 100K, 1000K}, 1K = 1024, uniform [0,1)^2, wave field, p = 2", rows)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -613,7 +650,7 @@ def main():
     libbuild.build()
     for name, fn in (("scale", run_scale), ("clustered", run_clustered),
                      ("adjoint", run_adjoint), ("batched", run_batched),
-                     ("layout", run_layout)):
+                     ("layout", run_layout), ("paper", run_paper)):
         if args.config in (name, "all"):
             fn(args)
 

@@ -256,6 +256,39 @@ idw_status idw_selftest_bounded_wait(idw_handle_t handle, void *stream);
 idw_status idw_measure_pipe_rates(int device, double rates[6]);
 
 /*
+ * The paper's own GPU designs, as measured baselines (not the fast path):
+ *   IDW_PAPER_NAIVE : one thread per prediction point reading every data
+ *                     point from global memory (Sec. 3; data read m times);
+ *   IDW_PAPER_TILED : one thread per prediction point, each block staging
+ *                     256 data points in shared memory at a time (Sec. 4.2;
+ *                     data read m / 256 times).
+ * in the paper's data layouts (Sec. 2.2, 3.2-3.5):
+ *   IDW_LAYOUT_SOA    : x[n], y[n], z[n]
+ *   IDW_LAYOUT_AOS    : unaligned rows (x, y, z) -- the caller's rows as they are
+ *   IDW_LAYOUT_AOAS   : aligned records (x, y, z, pad) of 16 (float) or
+ *                       32 (double) bytes
+ *   IDW_LAYOUT_HYBRID : (x, y) pairs beside z[n] (the paper uses it for double)
+ * They sum plainly (no compensation) in the precision given: data, queries
+ * and out are float for IDW_PREC_F32_COMP (here: plain FP32) and double for
+ * IDW_PREC_F64_PLAIN.  p = 2 is 1/d^2, other p use pow().  A query that
+ * coincides with a data point takes the z of the lowest such index.  Other
+ * layouts than AoS are staged into the handle's workspace first.
+ * Arguments, ownership and errors as in idw_interpolate.
+ */
+typedef enum { IDW_PAPER_NAIVE = 0, IDW_PAPER_TILED = 1 } idw_paper_kernel;
+typedef enum {
+    IDW_LAYOUT_SOA = 0,
+    IDW_LAYOUT_AOS = 1,
+    IDW_LAYOUT_AOAS = 2,
+    IDW_LAYOUT_HYBRID = 3
+} idw_paper_layout;
+
+idw_status idw_paper_interpolate(idw_handle_t handle, idw_paper_kernel kernel,
+                                 idw_paper_layout layout, const void *data_xyz, int64_t n,
+                                 const void *queries_xy, int64_t m, double p, idw_precision prec,
+                                 void *out, void *stream);
+
+/*
  * Allocation-free FP32-compensated interpolation.  The paper has no
  * counterpart; this exists for callers that cannot allocate device memory:
  * a host application that owns the whole device-memory budget and does not

@@ -20,7 +20,7 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
-    "interpolate_batched", "backward", "IDWFunction", "idw", "plan_forward",
+    "interpolate_batched", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
@@ -181,6 +181,26 @@ def interpolate_batched(datas, queries_list, p: float = 2.0, outs=None,
         float(p), PREC_F32_COMP, P(*[o.data_ptr() for o in outs]), _stream(datas[0]))
     _lib.check(st, "idw_interpolate_batched", h.ptr)
     return outs
+
+
+def paper_interpolate(data, queries, p: float = 2.0, kernel: str = "tiled", layout: str = "aoas",
+                      precision="f32c", out=None, handle: Handle | None = None):
+    """The paper's naive or tiled kernel in one of its layouts (a baseline).
+
+    ``kernel`` in {"naive", "tiled"}; ``layout`` in {"soa", "aos", "aoas",
+    "hybrid"}; ``precision`` "f32c" runs plain FP32 here, "f64" plain FP64.
+    """
+    prec = _prec(precision)
+    _check_inputs(data, queries, prec)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    st = h.lib.idw_paper_interpolate(h.ptr, _lib.PAPER_KERNELS[kernel], _lib.PAPER_LAYOUTS[layout],
+                                     _ptr(data), data.shape[0], _ptr(queries), m, float(p), prec,
+                                     _ptr(out), _stream(data))
+    _lib.check(st, "idw_paper_interpolate", h.ptr)
+    return out
 
 
 def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=True,

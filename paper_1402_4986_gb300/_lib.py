@@ -31,6 +31,8 @@ STATUS = {
 }
 PREC_F32_COMP = 0
 PREC_F64_PLAIN = 1
+PAPER_KERNELS = {"naive": 0, "tiled": 1}
+PAPER_LAYOUTS = {"soa": 0, "aos": 1, "aoas": 2, "hybrid": 3}
 OPTIONS = {"autotune": 1, "sweep_variant": 2, "force_general_power": 3, "last_variant": 4,
            "tuned_classes": 5, "staging_layout": 6}
 
@@ -79,6 +81,8 @@ SIGNATURES = {
     "idw_profile_enable": (c_int, [c_void_p, c_int]),
     "idw_profile_read": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_int64)]),
     "idw_selftest_bounded_wait": (c_int, [c_void_p, c_void_p]),
+    "idw_paper_interpolate": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int64, c_void_p, c_int64,
+                                      c_double, c_int, c_void_p, c_void_p]),
     "idw_interpolate_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_void_p,
                                         c_void_p]),
 }

@@ -493,6 +493,23 @@ idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const floa
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
+idw_status idw_paper_interpolate(idw_handle_t h, idw_paper_kernel kernel, idw_paper_layout layout,
+                                 const void* data, int64_t n, const void* queries, int64_t m,
+                                 double p, idw_precision prec, void* out, void* stream) {
+  idw_status st = check_common(h, data, n, queries, m, p, prec, out);
+  if (st != IDW_OK || m == 0) return st;
+  if (kernel != IDW_PAPER_NAIVE && kernel != IDW_PAPER_TILED) return IDW_ERR_INVALID_ARG;
+  if (layout < IDW_LAYOUT_SOA || layout > IDW_LAYOUT_HYBRID) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const bool fp64 = prec == IDW_PREC_F64_PLAIN;
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, idw::paper_layout_bytes(n, fp64));
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_paper_kernel(kernel, layout, fp64, data, n, queries, m, p, out,
+                                                 h->ws, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
 idw_status idw_sync_status(idw_handle_t h, void* stream) {
   if (!h) return IDW_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);

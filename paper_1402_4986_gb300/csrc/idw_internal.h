@@ -158,6 +158,12 @@ cudaError_t launch_forward_f64(const F64Problem& pb, const Plan& plan, void* wor
                                cudaStream_t stream);
 int occupancy_forward_f64();
 
+// The paper's naive and tiled kernels (measured baselines), in its layouts.
+size_t paper_layout_bytes(int64_t n, bool fp64);
+cudaError_t launch_paper_kernel(int kernel, int layout, bool fp64, const void* rows, int64_t n,
+                                const void* queries, int64_t m, double p, void* out,
+                                void* workspace, cudaStream_t stream);
+
 // Pipe-rate probe: returns ops per SM per clock for the 6 probed pipes.
 cudaError_t measure_pipe_rates(int sm_count, double rates[6]);
 
