@@ -51,6 +51,10 @@ def bind(lib):
     lib.oracle_idw_grad.argtypes = [d, i64, d, i64, ctypes.c_double, d, d, d, d, d, d,
                                     ctypes.c_int]
     lib.oracle_idw_grad.restype = ctypes.c_int
+    lib.oracle_idw_local.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_double, d,
+                                     ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.oracle_idw_local.restype = ctypes.c_int
     return lib
 
 
@@ -103,6 +107,27 @@ def idw(data_xyz, queries_xy, p: float, threads: int = 0, return_s0: bool = Fals
     if rc < 0:
         raise ValueError("oracle_idw_forward rejected its arguments")
     return (Z, hit, S0) if return_s0 else (Z, hit)
+
+
+def idw_local(data_xyz, queries_xy, p: float, radius: float, threads: int = 0):
+    """Eq. 1 over the data points within ``radius`` of each query (FP64).
+
+    Membership is decided in FP32 as a GPU evaluates it (see idw_oracle.c).
+    Returns (Z float64[m] (NaN where no member), hit int64[m], count int32[m]).
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    m = q.shape[0]
+    Z = np.empty(m, np.float64)
+    hit = np.empty(m, np.int64)
+    count = np.empty(m, np.int32)
+    rc = lib.oracle_idw_local(_ptr(data), data.shape[0], _ptr(q), m, float(p), float(radius),
+                              _ptr(Z), hit.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              count.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_local rejected its arguments")
+    return Z, hit, count
 
 
 def idw_grad(data_xyz, queries_xy, p: float, g, threads: int = 0):

@@ -30,6 +30,16 @@
  *     rounding error is far below the tolerances it is used to check.
  *   - NaN anywhere in a query's inputs gives NaN unless an exact hit is found.
  *
+ * Local (radius-limited) variant (not the paper's method; the local Shepard
+ * interpolation of its cited related work, Sec. 1): Eq. 1 over the data
+ * points within distance R of the query only.  Readings:
+ *   - membership is decided in FP32, exactly as a GPU evaluates it:
+ *     dx = fl32(qx - x), dy = fl32(qy - y), d2 = fmaf(dy, dy, fl32(dx dx)),
+ *     member iff d2 < fl32(R^2); the weights then use the exact FP64
+ *     distances of the members;
+ *   - an exact hit anywhere returns z of the lowest coincident index;
+ *   - no member gives NaN.
+ *
  * Gradients (not in the paper; derived from Eq. 1 by the chain rule, with
  * S0 = sum w_i, S1 = sum w_i z_i, Z = S1/S0, w_i = (d_i^2)^(-p/2)):
  *   dZ/dz_i  = w_i / S0
@@ -236,6 +246,93 @@ int oracle_idw_forward(const double *data, int64_t n, const double *q, int64_t m
     if (m == 0)
         return 0;
     return parallel_for(m, nthreads, fwd_range, &c);
+}
+
+/* ------------------------------------------------------- local variant */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    double p;
+    float r2f; /* fl32(R^2) */
+    double *Z;
+    int64_t *hit;
+    int32_t *count;
+} local_ctx;
+
+/* FP32 membership test: d2 = fmaf(dy, dy, fl32(dx dx)) < fl32(R^2). */
+static int local_member(float qx, float qy, float x, float y, float r2f)
+{
+    float dx = qx - x;
+    float dy = qy - y;
+    float dxx = dx * dx;
+    float d2 = fmaf(dy, dy, dxx);
+    return d2 < r2f;
+}
+
+static void local_range(void *vctx, int64_t b, int64_t e)
+{
+    local_ctx *c = (local_ctx *)vctx;
+    for (int64_t j = b; j < e; j++) {
+        const double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+        const float qxf = (float)qx, qyf = (float)qy;
+        int64_t k = -1;
+        int32_t count = 0;
+        double d2min = INFINITY;
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            if (x == qx && y == qy) {
+                k = i;
+                break;
+            }
+            if (local_member(qxf, qyf, (float)x, (float)y, c->r2f)) {
+                const double d2 = sqdist(qx, qy, x, y);
+                if (d2 < d2min)
+                    d2min = d2;
+                count++;
+            }
+        }
+        c->hit[j] = k;
+        if (k >= 0) {
+            c->Z[j] = c->data[3 * k + 2];
+            c->count[j] = -1;
+            continue;
+        }
+        c->count[j] = count;
+        if (count == 0) {
+            c->Z[j] = NAN;
+            continue;
+        }
+        nsum s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            if (!local_member(qxf, qyf, (float)x, (float)y, c->r2f))
+                continue;
+            const double w = scaled_weight(d2min, sqdist(qx, qy, x, y), c->p);
+            nsum_add(&s0, w);
+            nsum_add(&s1, w * c->data[3 * i + 2]);
+        }
+        c->Z[j] = nsum_value(&s1) / nsum_value(&s0);
+    }
+}
+
+/*
+ * Local Eq. 1: the data points within distance `radius` of each query.
+ * Inputs as oracle_idw_forward (coordinates must be fp32 values); outputs
+ * Z[m], hit[m] (lowest coincident index or -1) and count[m] (members used,
+ * -1 at an exact hit).  Returns threads used, or -1 on bad arguments.
+ */
+int oracle_idw_local(const double *data, int64_t n, const double *q, int64_t m, double p,
+                     double radius, double *Z, int64_t *hit, int32_t *count, int nthreads)
+{
+    if (!data || !q || !Z || !hit || !count || n < 1 || m < 0 || !(p > 0.0) || !isfinite(p) ||
+        !(radius > 0.0))
+        return -1;
+    local_ctx c = {data, n, q, p, (float)(radius * radius), Z, hit, count};
+    if (m == 0)
+        return 0;
+    return parallel_for(m, nthreads, local_range, &c);
 }
 
 /* ------------------------------------------------------------ gradients */

@@ -34,6 +34,12 @@ MUTATIONS = [
     ("data-gradient uses dy for x", "nsum_add(&gx, a * dx);\n            nsum_add(&gy, a * dy);",
      "nsum_add(&gx, a * dy);\n            nsum_add(&gy, a * dy);"),
     ("z-gradient not normalised", "nsum_add(&gz, gj * w / S0);", "nsum_add(&gz, gj * w);"),
+    ("local membership not strict", "    return d2 < r2f;", "    return d2 <= r2f;"),
+    ("local membership in FP64", "    float d2 = fmaf(dy, dy, dxx);\n    return d2 < r2f;",
+     "    float d2 = fmaf(dy, dy, dxx);\n    return (double)(qx - x) * (qx - x) + (double)(qy - y) * (qy - y) < r2f;"),
+    ("local weights over all points", "            if (!local_member(qxf, qyf, (float)x, (float)y, c->r2f))\n                continue;",
+     "            (void)local_member;"),
+    ("local empty neighbourhood not NaN", "            c->Z[j] = NAN;", "            c->Z[j] = 0.0;"),
     ("exact-hit gradient dropped", "                if (c->hit[j] == i)\n                    nsum_add(&gz, gj);",
      "                if (c->hit[j] == i)\n                    nsum_add(&gz, 0.0);"),
 ]
@@ -52,6 +58,11 @@ PINS = [
     lambda: pins.test_gradient_matches_central_differences(2.5),
     pins.test_gradient_z_is_partition_of_unity,
     pins.test_gradient_at_exact_hit,
+    lambda: pins.test_local_exact_rational(0.2),
+    pins.test_local_membership_at_the_boundary,
+    pins.test_local_with_huge_radius_is_the_global_form,
+    pins.test_local_no_member_is_nan,
+    pins.test_local_membership_is_decided_in_fp32,
 ]
 
 

@@ -279,3 +279,128 @@ def test_gradient_at_exact_hit():
     G = oracle.idw_grad(data, q, 2.0, np.array([3.0]))
     assert np.array_equal(G["grad_z"], [0.0, 3.0, 0.0])
     assert np.all(G["grad_xy"] == 0) and np.all(G["grad_q"] == 0) and G["grad_p"] == 0
+
+
+# ------------------------------------------------------- local variant
+
+def _round_f32(frac):
+    """Round an exact Fraction to the nearest float32 (ties to even)."""
+    d = np.float32(float(frac))
+    best = None
+    for c in (np.nextafter(d, np.float32(-np.inf)), d, np.nextafter(d, np.float32(np.inf))):
+        if not np.isfinite(c):
+            continue
+        err = abs(Fraction(float(c)) - frac)
+        key = (err, int(np.frombuffer(np.float32(c).tobytes(), np.uint32)[0]) & 1)
+        if best is None or key < best[0]:
+            best = (key, c)
+    return best[1]
+
+
+def _local_exact(data, q, radius, p_even=2):
+    """Exact Z of Eq. 1 over the members decided by the FP32 test
+    fmaf(dy, dy, fl32(dx dx)) < fl32(R^2), emulated without rounding slips."""
+    r2f = np.float32(radius * radius)
+    out = []
+    for qx, qy in q.astype(np.float32):
+        hit = None
+        members = []
+        for i, (x, y, z) in enumerate(data.astype(np.float32)):
+            if x == qx and y == qy:
+                hit = i
+                break
+            dx = np.float32(qx - x)
+            dy = np.float32(qy - y)
+            dxx = np.float32(dx * dx)
+            d2 = _round_f32(Fraction(float(dy)) ** 2 + Fraction(float(dxx)))
+            if d2 < r2f:
+                members.append(i)
+        if hit is not None:
+            out.append((float(data[hit, 2]), hit, -1))
+            continue
+        if not members:
+            out.append((float("nan"), -1, 0))
+            continue
+        s0 = Fraction(0)
+        s1 = Fraction(0)
+        for i in members:
+            d2 = (Fraction(float(qx)) - Fraction(float(data[i, 0]))) ** 2 + \
+                 (Fraction(float(qy)) - Fraction(float(data[i, 1]))) ** 2
+            w = 1 / d2 ** (p_even // 2)
+            s0 += w
+            s1 += w * Fraction(float(data[i, 2]))
+        out.append((float(s1 / s0), -1, len(members)))
+    return out
+
+
+@pytest.mark.parametrize("radius", [0.05, 0.2, 0.6])
+def test_local_exact_rational(radius):
+    data, q = _tiny(31, 60, 25)
+    q[4] = data[17, :2]
+    Z, hit, count = oracle.idw_local(data, q, 2.0, radius)
+    for j, (ze, he, ce) in enumerate(_local_exact(data, q, radius)):
+        assert hit[j] == he and count[j] == ce, (j, hit[j], he, count[j], ce)
+        if np.isnan(ze):
+            assert np.isnan(Z[j])
+        else:
+            assert abs(Z[j] - ze) <= 4e-16 * np.abs(data[:, 2]).max()
+
+
+def test_local_membership_at_the_boundary():
+    # Points placed so that d^2 sits next to R^2: the FP32 test decides.
+    data = np.array([[0.0, 0.0, 1.0], [0.3, 0.4, 2.0], [0.30000001, 0.4, 3.0],
+                     [0.6, 0.8, 4.0], [0.5, 0.0, 5.0]], np.float32)
+    # The last query is exactly 0.5 from (0.5, 0): d^2 = R^2 = 0.25 exactly,
+    # so the strict test excludes that point at R = 0.5.
+    q = np.array([[0.0, 0.0001], [0.0, 0.0], [1.0, 0.0]], np.float32)
+    for radius in (0.5, 0.49999999, 0.5000001, 1.0):
+        Z, hit, count = oracle.idw_local(data, q, 2.0, radius)
+        for j, (ze, he, ce) in enumerate(_local_exact(data, q, radius)):
+            assert hit[j] == he and count[j] == ce, (radius, j, count[j], ce)
+        if radius == 0.5:
+            assert count[2] == 0 and np.isnan(Z[2])
+
+
+def test_local_with_huge_radius_is_the_global_form():
+    prob = synthetic.uniform_problem(700, 300, seed=33, exact_hits=4)
+    for p in (2.0, 3.5):
+        Zg, hg = oracle.idw(prob["data"], prob["queries"], p)
+        Zl, hl, cl = oracle.idw_local(prob["data"], prob["queries"], p, 1e30)
+        assert np.array_equal(Zg, Zl) and np.array_equal(hg, hl)
+        assert np.all(cl[hl < 0] == 700)
+
+
+def test_local_no_member_is_nan():
+    data = np.array([[0.0, 0.0, 1.0], [1.0, 1.0, 2.0]], np.float32)
+    q = np.array([[0.5, 0.5], [0.01, 0.0]], np.float32)
+    Z, hit, count = oracle.idw_local(data, q, 2.0, 0.1)
+    assert np.isnan(Z[0]) and count[0] == 0
+    assert Z[1] == 1.0 and count[1] == 1
+
+
+def test_local_membership_is_decided_in_fp32():
+    """Find points where the FP32 test and an exact test disagree; the oracle
+    must follow the FP32 decision (a GPU makes it the same way)."""
+    rng = np.random.default_rng(35)
+    radius = 0.3
+    r2f = np.float32(radius * radius)
+    q = np.array([[0.5, 0.5]], np.float32)
+    found = []
+    for _ in range(20000):
+        ang = rng.uniform(0, 2 * np.pi)
+        rad = radius * (1 + rng.uniform(-3e-7, 3e-7))
+        pt = np.array([0.5 + rad * np.cos(ang), 0.5 + rad * np.sin(ang)], np.float32)
+        dx = np.float32(q[0, 0] - pt[0])
+        dy = np.float32(q[0, 1] - pt[1])
+        d2f = _round_f32(Fraction(float(dy)) ** 2 + Fraction(float(np.float32(dx * dx))))
+        exact = (Fraction(float(q[0, 0])) - Fraction(float(pt[0]))) ** 2 + \
+                (Fraction(float(q[0, 1])) - Fraction(float(pt[1]))) ** 2
+        if (d2f < r2f) != (exact < Fraction(float(r2f))):
+            found.append((pt, bool(d2f < r2f)))
+        if len(found) >= 4:
+            break
+    assert found, "no disagreeing point found"
+    for pt, member in found:
+        data = np.array([[pt[0], pt[1], 7.0], [0.9, 0.9, 1.0]], np.float32)
+        Z, hit, count = oracle.idw_local(data, q, 2.0, radius)
+        assert count[0] == (1 if member else 0)
