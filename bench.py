@@ -105,9 +105,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--members", type=float, nargs="*", default=None,
+                    help="local workload only: uniform data with these mean neighbour "
+                         "counts K instead of the default sweep")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "scale", "clustered", "adjoint", "batched", "layout",
-                             "paper", "all"],
+                             "paper", "local", "all"],
                     help="headline = the N=M=2^20 line; the others measure the other "
                          "workloads (one JSON line each)")
     return ap.parse_args()
@@ -634,6 +637,46 @@ def run_paper(args):
           "N = M in {10K, 100K, 1000K}, 1K = 1024, uniform [0,1)^2, wave field, p = 2", rows)
 
 
+def run_local(args):
+    """Local (radius-limited) form: N = M = 2^20, R for K neighbours on
+    average, uniform and clustered data, p in {2, 3.5}.  Each call sorts the
+    data into the grid (with one bounding-box read-back) and gathers."""
+    import torch
+    import oracle
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    rows = []
+    cases = ((False, 32.0), (False, 8.0), (False, 128.0), (True, 32.0))
+    if args.members:
+        cases = tuple((False, float(k)) for k in args.members)
+    for clustered, members in cases:
+        prob = synthetic.config_local(members=members, clustered=clustered)
+        d = torch.from_numpy(prob["data"]).cuda()
+        q = torch.from_numpy(prob["queries"]).cuda()
+        n, m, R = d.shape[0], q.shape[0], prob["radius"]
+        out = torch.empty(m, device="cuda")
+        idx = np.random.default_rng(5).choice(m, 256, replace=False)
+        for p in (2.0, 3.5):
+            ms = _events_ms(lambda: idw.interpolate_local(d, q, p, R, out=out), 10, warm=3)
+            _, cnt = idw.interpolate_local(d, q, p, R, counts=True)
+            c = cnt.cpu().numpy()
+            pairs = float(c[c > 0].sum())
+            Z64, _, c64 = oracle.idw_local(prob["data"], prob["queries"][idx], p, R)
+            Zs = out.cpu().numpy()[idx].astype(np.float64)
+            ok = ~np.isnan(Z64)
+            err = float(np.max(np.abs(Zs[ok] - Z64[ok])) / np.max(np.abs(prob["data"][:, 2])))
+            rows.append({"data": "clustered" if clustered else "uniform", "n": n, "m": m,
+                         "radius": R, "mean_members": pairs / m, "p": p, "ms": ms,
+                         "queries_s": m / (ms / 1e3), "member_pairs_s": pairs / (ms / 1e3),
+                         "empty_queries": int((c == 0).sum()),
+                         "counts_match_oracle": bool(np.array_equal(c[idx], c64)),
+                         "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+    _emit("local (radius-limited) Eq. 1: N = M = 2^20, queries uniform on [0,1)^2, "
+          "R = sqrt(K / (pi N)); data uniform (wave field) or 64 Gaussian blobs (bump field); "
+          "time per call includes the grid build and its one read-back", rows,
+          metric="local queries/s", unit="queries/s")
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -650,7 +693,7 @@ def main():
     libbuild.build()
     for name, fn in (("scale", run_scale), ("clustered", run_clustered),
                      ("adjoint", run_adjoint), ("batched", run_batched),
-                     ("layout", run_layout), ("paper", run_paper)):
+                     ("layout", run_layout), ("paper", run_paper), ("local", run_local)):
         if args.config in (name, "all"):
             fn(args)
 

@@ -323,6 +323,46 @@ idw_status idw_paper_interpolate(idw_handle_t handle, idw_paper_kernel kernel,
 idw_status idw_interpolate_noalloc(const float *data_xyz, int64_t n, const float *queries_xy,
                                    int64_t m, double p, float *out, void *stream);
 
+/*
+ * Local (radius-limited) Shepard interpolation.  The paper computes the
+ * global form of Eq. 1 and names the local form, which uses only the data
+ * points near each prediction point, among the related work (Sec. 1).
+ * Here Z(q) is Eq. 1 over the data points within distance `radius` of q:
+ *
+ *   member i of q  iff  fl32(fmaf(dy, dy, fl32(dx * dx))) < fl32(radius^2),
+ *                       dx = fl32(qx - x_i), dy = fl32(qy - y_i),
+ *
+ * decided in FP32 on the caller's coordinates (so a point at distance R
+ * exactly, or within FP32 rounding of it, is in or out as that expression
+ * says).  Weights are d^-p in FP32 and summed in FP64 per query.  A query
+ * that coincides with a data point takes the z of the lowest such index
+ * (count -1); a query with no member gets NaN (count 0).  Data points with a
+ * non-finite coordinate are ignored; a query with one gets NaN.
+ *
+ *   data_xyz, queries_xy, out : device float arrays as in idw_interpolate.
+ *   radius                    : R > 0 (+inf gives the global form).
+ *   count_out                 : NULL, or device int32[m] receiving the number
+ *                               of members of each query (-1 at a hit).
+ *
+ * Method, all on `stream` without host synchronisation (so the call can be
+ * captured into a CUDA graph): the bounding box of the data; a uniform grid
+ * of cells about R/2 wide (at most 2048 per axis and one cell per two data
+ * points), planned by one device thread; a counting sort of the data and of
+ * the queries into the cells; then one thread per query, in cell order,
+ * walks the rows of cells its disc of radius R reaches.  Weights are summed
+ * as compensated FP32 pairs; a query whose sums leave FP32's range is
+ * redone in FP64.  Scatter positions come from atomics, so candidates may be
+ * summed in a different order from call to call: results can differ in the
+ * last bit.
+ * Workspace (the handle's): 16 bytes per data point, 16 per query and 16 per
+ * cell, for at most min(2^22, max(1024, n/2)) cells.  Errors as in
+ * idw_interpolate, plus IDW_ERR_INVALID_ARG for radius <= 0 or NaN; the
+ * kernels run asynchronously after it returns.
+ */
+idw_status idw_interpolate_local(idw_handle_t handle, const float *data_xyz, int64_t n,
+                                 const float *queries_xy, int64_t m, double p, double radius,
+                                 float *out, int32_t *count_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

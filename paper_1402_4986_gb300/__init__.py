@@ -20,7 +20,7 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
-    "interpolate_batched", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
+    "interpolate_batched", "interpolate_local", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
@@ -201,6 +201,27 @@ def paper_interpolate(data, queries, p: float = 2.0, kernel: str = "tiled", layo
                                      _ptr(out), _stream(data))
     _lib.check(st, "idw_paper_interpolate", h.ptr)
     return out
+
+
+def interpolate_local(data, queries, p: float = 2.0, radius: float = float("inf"), out=None,
+                      counts: bool = False, handle: Handle | None = None):
+    """Eq. 1 over the data points within ``radius`` of each query (FP32).
+
+    Returns ``out`` (float32[m], NaN where no data point is within R), or
+    ``(out, count)`` with ``count`` int32[m] (members per query, -1 at an
+    exact hit) when ``counts`` is true.  Synchronises the stream once.
+    """
+    _check_inputs(data, queries, PREC_F32_COMP)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=data.device)
+    cnt = torch.empty(m, dtype=torch.int32, device=data.device) if counts else None
+    st = h.lib.idw_interpolate_local(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p),
+                                     float(radius), _ptr(out), _ptr(cnt),
+                                     _stream(data))
+    _lib.check(st, "idw_interpolate_local", h.ptr)
+    return (out, cnt) if counts else out
 
 
 def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=True,

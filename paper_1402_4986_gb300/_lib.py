@@ -85,6 +85,8 @@ SIGNATURES = {
                                       c_double, c_int, c_void_p, c_void_p]),
     "idw_interpolate_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_void_p,
                                         c_void_p]),
+    "idw_interpolate_local": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
+                                      c_double, c_void_p, c_void_p, c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -17,6 +17,7 @@
 #include "idw.h"
 #include "idw_device.cuh"
 #include "idw_internal.h"
+#include "idw_local.h"
 
 struct idw_handle_s {
   int device = 0;
@@ -507,6 +508,25 @@ idw_status idw_paper_interpolate(idw_handle_t h, idw_paper_kernel kernel, idw_pa
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_paper_kernel(kernel, layout, fp64, data, n, queries, m, p, out,
                                                  h->ws, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
+                                 const float* queries, int64_t m, double p, double radius,
+                                 float* out, int32_t* count_out, void* stream) {
+  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, out);
+  if (st != IDW_OK) return st;
+  if (!(radius > 0.0)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (count_out && !aligned(count_out, 4)) return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const int64_t max_cells = idw::local_max_cells(n);
+  const idw::LocalLayout L = idw::local_layout(n, m, max_cells);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_local(data, n, queries, m, p, radius, out, count_out, h->ws, L,
+                                          h->sm_count, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 

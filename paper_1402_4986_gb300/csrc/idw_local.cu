@@ -1,0 +1,571 @@
+// Local (radius-limited) Shepard interpolation: Eq. 1 over the data points
+// within distance R of each query.  This is the local variant of the IDW
+// implementations the paper cites as related work (Sec. 1), not its global
+// method.
+//
+// Pipeline (all on the caller's stream, no host synchronisation):
+//   1. bounding box of the finite data points; the last block plans a
+//      uniform grid of cells about R/2 wide, at most 2048 per axis and at
+//      most one per two data points (coarser when the box needs it);
+//   2. counting sort of the data AND of the queries into the cells
+//      (histogram, exclusive scan, scatter of 16-byte records);
+//   3. one thread per query, in cell order, walks the rows of cells that its
+//      disc of radius R can reach (at most 5 rows of at most 5 cells), each
+//      row one contiguous run of sorted data.
+// Membership is decided in FP32 as d^2 = fmaf(dy, dy, fl32(dx dx)) <
+// fl32(R^2) on the caller's unscaled coordinates.  Weights are FP32 (MUFU
+// reciprocal at p = 2; 2^(-(p/2) log2 d^2) with an FMA-recovered exponent
+// otherwise) and both sums are carried as compensated (hi, lo) FP32 pairs
+// (Knuth's TwoSum per member, the product's rounding error by FMA), then
+// divided with one residual correction.  Sums that leave FP32's range are
+// redone in FP64 with weights scaled by d2_min^(p/2).  A query that
+// coincides with a data point takes the z of the lowest such index; an
+// empty neighbourhood gives NaN.
+//
+// Cell positions are computed in FP32 as u(v) = fl(fl(fl(v/2) - fl(x0/2)) *
+// inv2), inv2 = fl(2/h): halving is exact for normal floats and keeps the
+// difference finite for any finite coordinates, and u is monotone in v.
+// With at most 2048 cells per axis, u near the grid is off by at most
+// 2^-23 (g + 2) ~ 2^-12 cells from (v - x0)/h.  A member lies less than
+// R (1 + 2^-23) from its query (FP32 membership; R + 2^-74 where R^2 is
+// subnormal, and h >= 2^-61), so in computed cell positions it lies within
+// rho = (R/h)(1 + 2^-8) + 2^-8 of the query, which covers those errors and
+// the FP32 rounding of the reach arithmetic.  With h >= R (1 + 2^-6)/2,
+// rho < 2: a query scans rows floor(v_q) - 2 .. floor(v_q) + 2, and in each
+// the columns floor(u_q - e) .. floor(u_q + e), e = sqrt(rho^2 - dy^2), dy
+// the gap between v_q and the row.  Grids that need cells wider than 2^120
+// (R or the data's extent near FP32's limit) fall back to a single cell.
+// Scatter positions come from atomics, so the order of candidates within a
+// cell (and with it the last bits of the compensated sums) can vary between
+// calls.
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdint>
+
+#include <algorithm>
+
+#include "idw.h"
+#include "idw_device.cuh"
+#include "idw_internal.h"
+#include "idw_local.h"
+
+namespace idw {
+namespace {
+
+constexpr int kScanBlock = 1024;            // threads of a scan block
+constexpr int kScanTile = 4 * kScanBlock;  // entries of a scan tile (an int4 per thread)
+constexpr int kLocalThreads = 256;
+constexpr int kMaxCellsPerAxis = 2048;
+// A compensated weight sum below this per member may have lost flushed
+// (FTZ) weights: such queries are redone in FP64.
+constexpr float kTinyPerMember = 0x1p-100f;
+
+// Grid of cells, planned on the device.  Each call starts by setting every
+// byte of it to 0xff (keys at their identity, tickets at -1).
+struct GridDev {
+  unsigned keys[4];      // min x, min y, ~max x, ~max y (order-preserving keys)
+  unsigned box_ticket;   // blocks of the box kernel done, minus one
+  unsigned scan_ticket;  // scan tiles done, minus one
+  float hx0, hy0, inv2;  // cell position u(v) = fl(fl(fl(v/2) - h0) * inv2)
+  float rho;             // reach of R in cells, with margin (< 2)
+  int gx, gy, cells;
+};
+
+// Order-preserving unsigned key of a float (for atomic min).
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+__device__ __forceinline__ bool finite2(float x, float y) {
+  return fabsf(x) <= FLT_MAX && fabsf(y) <= FLT_MAX;
+}
+
+// Ticket counter: atomic add with acquire-release semantics at GPU scope.
+// Its release orders the caller's earlier writes before the increment; the
+// caller that draws the last ticket acquires every earlier caller's writes.
+__device__ __forceinline__ unsigned ticket_acq_rel(unsigned* counter) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+               : "=r"(old)
+               : "l"(counter)
+               : "memory");
+  return old;
+}
+
+// Cell position along one axis (same arithmetic for data and queries).
+__device__ __forceinline__ float cell_pos(float v, float h0, float inv2) {
+  return __fmul_rn(__fsub_rn(__fmul_rn(0.5f, v), h0), inv2);
+}
+// floor(u) clamped to [lo, hi] (u may be +-inf for far queries, never NaN).
+__device__ __forceinline__ int clamp_floor(float u, int lo, int hi) {
+  return static_cast<int>(fminf(fmaxf(floorf(u), float(lo)), float(hi)));
+}
+
+// Grid for the box in grid->keys (one thread).
+__device__ void plan_grid(GridDev* grid, double radius, double inv_max_cells) {
+  const unsigned k0 = __ldcg(&grid->keys[0]), k1 = __ldcg(&grid->keys[1]);
+  const unsigned k2 = __ldcg(&grid->keys[2]), k3 = __ldcg(&grid->keys[3]);
+  int gx = 1, gy = 1;
+  float hx0 = 0.f, hy0 = 0.f, inv2 = 0.f, rho = 1.f;  // inv2 = 0: one cell
+  if (k0 != 0xffffffffu) {  // some finite data point
+    const float xmin = key_float(k0), ymin = key_float(k1);
+    const float xmax = key_float(~k2), ymax = key_float(~k3);
+    const double ex = double(xmax) - xmin, ey = double(ymax) - ymin;
+    double h = fmax(fmax(radius * (0.5 + 0x1p-7), 0x1p-61),
+                    fmax(ex * (1.0 / (kMaxCellsPerAxis - 1)), ey * (1.0 / (kMaxCellsPerAxis - 1))));
+    h = fmax(h, sqrt(ex * ey * inv_max_cells));
+    const float cap = float(kMaxCellsPerAxis - 1), max_cells = float(1.0 / inv_max_cells);
+    for (int it = 0; it < 64 && h <= 0x1p120; ++it, h *= 1.25) {
+      const float i2 = 2.f * __frcp_rn(__double2float_ru(h));
+      const float ux = floorf(cell_pos(xmax, 0.5f * xmin, i2));
+      const float uy = floorf(cell_pos(ymax, 0.5f * ymin, i2));
+      if (ux <= cap && uy <= cap && (ux + 1.f) * (uy + 1.f) <= max_cells) {
+        gx = int(ux) + 1;
+        gy = int(uy) + 1;
+        hx0 = 0.5f * xmin;
+        hy0 = 0.5f * ymin;
+        inv2 = i2;
+        // h <= 2^120 and h >= R (1 + 2^-6)/2, so R fits a float.
+        rho = __fmaf_ru(__fmul_ru(__double2float_ru(radius), i2), 0.5f + 0x1p-9f, 0x1p-8f);
+        break;
+      }
+    }
+  }
+  grid->hx0 = hx0;
+  grid->hy0 = hy0;
+  grid->inv2 = inv2;
+  grid->rho = rho;
+  grid->gx = gx;
+  grid->gy = gy;
+  grid->cells = gx * gy;
+}
+
+// Bounding box of the finite data points; the last block to finish plans
+// the grid.
+__global__ void __launch_bounds__(256)
+    box_plan_kernel(const float* __restrict__ data, int64_t n, GridDev* __restrict__ grid,
+                    double radius, double inv_max_cells) {
+  __shared__ unsigned part[4][8];
+  __shared__ bool last;
+  unsigned k0 = 0xffffffffu, k1 = 0xffffffffu, k2 = 0xffffffffu, k3 = 0xffffffffu;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    const float x = data[3 * i], y = data[3 * i + 1];
+    if (finite2(x, y)) {
+      k0 = min(k0, float_key(x));
+      k1 = min(k1, float_key(y));
+      k2 = min(k2, ~float_key(x));
+      k3 = min(k3, ~float_key(y));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    k0 = min(k0, __shfl_xor_sync(0xffffffffu, k0, o));
+    k1 = min(k1, __shfl_xor_sync(0xffffffffu, k1, o));
+    k2 = min(k2, __shfl_xor_sync(0xffffffffu, k2, o));
+    k3 = min(k3, __shfl_xor_sync(0xffffffffu, k3, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    part[0][wid] = k0;
+    part[1][wid] = k1;
+    part[2][wid] = k2;
+    part[3][wid] = k3;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned k = 0xffffffffu;
+    for (int w = 0; w < 8; ++w) k = min(k, part[threadIdx.x][w]);
+    atomicMin(&grid->keys[threadIdx.x], k);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&grid->box_ticket, 1u) + 1u == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    plan_grid(grid, radius, inv_max_cells);
+  }
+}
+
+// Zeroes both histograms over cells + 1 entries rounded up to a multiple of
+// four (the scan reads them as int4).
+__global__ void __launch_bounds__(256)
+    zero_counts_kernel(const GridDev* __restrict__ grid, int32_t* __restrict__ counts_d,
+                       int32_t* __restrict__ counts_q) {
+  const int len = (grid->cells + 1 + 3) & ~3;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) {
+    counts_d[i] = 0;
+    counts_q[i] = 0;
+  }
+}
+
+// Cell of a data point (-1: a non-finite point, in no cell) and sorting
+// bucket of a query (its cell clamped into the grid).
+__device__ __forceinline__ int data_cell(const GridDev& g, float x, float y) {
+  if (!finite2(x, y)) return -1;
+  const int cx = clamp_floor(cell_pos(x, g.hx0, g.inv2), 0, g.gx - 1);
+  const int cy = clamp_floor(cell_pos(y, g.hy0, g.inv2), 0, g.gy - 1);
+  return cy * g.gx + cx;
+}
+__device__ __forceinline__ int query_bucket(const GridDev& g, float x, float y) {
+  if (!finite2(x, y)) return 0;
+  const int cx = clamp_floor(cell_pos(x, g.hx0, g.inv2), 0, g.gx - 1);
+  const int cy = clamp_floor(cell_pos(y, g.hy0, g.inv2), 0, g.gy - 1);
+  return cy * g.gx + cx;
+}
+
+// Threads [0, n) count data points, [n, n + m) count queries.
+__global__ void __launch_bounds__(256)
+    count_kernel(const GridDev* __restrict__ grid, const float* __restrict__ data, int64_t n,
+                 const float* __restrict__ queries, int64_t m, int32_t* __restrict__ counts_d,
+                 int32_t* __restrict__ counts_q) {
+  const GridDev g = *grid;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const int c = data_cell(g, data[3 * i], data[3 * i + 1]);
+    if (c >= 0) atomicAdd(&counts_d[c], 1);
+  } else if (i < n + m) {
+    const int64_t j = i - n;
+    atomicAdd(&counts_q[query_bucket(g, queries[2 * j], queries[2 * j + 1])], 1);
+  }
+}
+
+// Exclusive scan of one value per thread over a kScanBlock-thread block;
+// `total` receives the block's sum.  `warp_tot` holds kScanBlock / 32 ints.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp_tot,
+                                                        int32_t& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t w = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    warp_tot[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  total = warp_tot[kScanBlock / 32 - 1];
+  return (wid > 0 ? warp_tot[wid - 1] : 0) + incl - v;
+}
+
+// Exclusive scan of both histograms (blockIdx.y: 0 data, 1 queries), one
+// tile of kScanTile entries per block (four consecutive entries per thread),
+// over cells + 1 entries.  Each tile writes its local prefix to starts[],
+// clears the counts (they become the scatter cursors) and records its total;
+// the block that finishes last turns the totals into tile bases (exclusive
+// scan in place), so that a cell starts at starts[i] + base[i / kScanTile].
+// The histogram arrays hold a multiple of four entries, 16-byte aligned.
+__global__ void __launch_bounds__(kScanBlock)
+    scan_kernel(GridDev* __restrict__ grid, int32_t* __restrict__ counts_d,
+                int32_t* __restrict__ counts_q, int32_t* __restrict__ starts_d,
+                int32_t* __restrict__ starts_q, int32_t* __restrict__ sums, int max_tiles) {
+  __shared__ int32_t warp_tot[kScanBlock / 32];
+  __shared__ bool last;
+  const int len = grid->cells + 1;
+  const int ntiles = (len + kScanTile - 1) / kScanTile;
+  if (int(blockIdx.x) >= ntiles) return;  // tile beyond the grid
+  int4* in = reinterpret_cast<int4*>(blockIdx.y ? counts_q : counts_d);
+  int4* out = reinterpret_cast<int4*>(blockIdx.y ? starts_q : starts_d);
+  const int i4 = blockIdx.x * kScanBlock + threadIdx.x;  // int4 index
+  int4 v = make_int4(0, 0, 0, 0);
+  if (4 * i4 < len) {
+    v = in[i4];
+    in[i4] = make_int4(0, 0, 0, 0);
+  }
+  // Entries past len are zero: the arrays are cleared up to a multiple of 4.
+  int32_t total;
+  const int32_t before = block_exclusive_scan(v.x + v.y + v.z + v.w, warp_tot, total);
+  if (4 * i4 < len)
+    out[i4] = make_int4(before, before + v.x, before + v.x + v.y, before + v.x + v.y + v.z);
+  if (threadIdx.x == 0) {
+    sums[blockIdx.y * max_tiles + blockIdx.x] = total;  // published by the ticket
+    last = ticket_acq_rel(&grid->scan_ticket) + 1u == unsigned(2 * ntiles - 1);
+  }
+  __syncthreads();  // the last block's threads read after thread 0's acquire
+  if (!last) return;
+  const int per = (ntiles + kScanBlock - 1) / kScanBlock;
+  for (int y = 0; y < 2; ++y) {
+    int32_t* sb = sums + y * max_tiles;
+    const int b0 = min(ntiles, int(threadIdx.x) * per), b1 = min(ntiles, b0 + per);
+    int32_t acc = 0;
+    for (int b = b0; b < b1; ++b) acc += __ldcg(&sb[b]);
+    __syncthreads();  // warp_tot is reused
+    int32_t run = block_exclusive_scan(acc, warp_tot, total);
+    for (int b = b0; b < b1; ++b) {
+      const int32_t t = __ldcg(&sb[b]);
+      sb[b] = run;
+      run += t;
+    }
+  }
+}
+
+__device__ __forceinline__ int cell_start(const int32_t* __restrict__ starts,
+                                          const int32_t* __restrict__ base, int i) {
+  return starts[i] + base[i / kScanTile];
+}
+
+// Threads [0, n) place data points as (x, y, z, index), [n, n + m) place
+// queries as (x, y, index, 0).
+__global__ void __launch_bounds__(256)
+    scatter_kernel(const GridDev* __restrict__ grid, const float* __restrict__ data, int64_t n,
+                   const float* __restrict__ queries, int64_t m,
+                   const int32_t* __restrict__ starts_d, const int32_t* __restrict__ starts_q,
+                   const int32_t* __restrict__ sums, int max_tiles,
+                   int32_t* __restrict__ cursor_d, int32_t* __restrict__ cursor_q,
+                   float4* __restrict__ sorted, float4* __restrict__ qrec) {
+  const GridDev g = *grid;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float x = data[3 * i], y = data[3 * i + 1];
+    const int c = data_cell(g, x, y);
+    if (c < 0) return;
+    const int pos = cell_start(starts_d, sums, c) + atomicAdd(&cursor_d[c], 1);
+    sorted[pos] = make_float4(x, y, data[3 * i + 2], __int_as_float(static_cast<int>(i)));
+  } else if (i < n + m) {
+    const int64_t j = i - n;
+    const float x = queries[2 * j], y = queries[2 * j + 1];
+    const int b = query_bucket(g, x, y);
+    const int pos = cell_start(starts_q, sums + max_tiles, b) + atomicAdd(&cursor_q[b], 1);
+    qrec[pos] = make_float4(x, y, __int_as_float(static_cast<int>(j)), 0.f);
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ float local_weight(float d2, float hp, float nhp) {
+  if (MODE == kPow2) return rcp_approx(d2);
+  const float L = lg2_approx(d2);
+  const float th = L * nhp;
+  const float tl = fmaf(L, nhp, L * hp);  // exact rounding error of th
+  const float e = ex2_approx(th);
+  return fmaf(e, tl * 0.6931471805599453f, e);
+}
+
+// MUFU square root (relative error ~2^-22, subnormal input flushed to 0).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ float fp32_d2(float qx, float qy, float x, float y) {
+  const float dx = __fsub_rn(qx, x), dy = __fsub_rn(qy, y);
+  return __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+}
+
+// The runs of sorted data a query's disc of radius R can reach: at most
+// five rows, each one contiguous run [a[r], b[r]) (empty runs have a == b).
+// All runs are looked up before any is walked, so their loads overlap.
+// The reach e of a row comes from the MUFU square root: its error (and a
+// flushed subnormal rho^2 - dy^2, where no member can lie) is far inside
+// rho's margin.
+struct Runs {
+  int a[5], b[5];
+
+  __device__ __forceinline__ Runs(const GridDev& g, float qx, float qy,
+                                  const int32_t* __restrict__ starts,
+                                  const int32_t* __restrict__ base) {
+    int y0 = 0, y1 = -1;
+    float u = 0.f, v = 0.f;
+    if (finite2(qx, qy)) {
+      u = cell_pos(qx, g.hx0, g.inv2);
+      v = cell_pos(qy, g.hy0, g.inv2);
+      const int cy = clamp_floor(v, -3, g.gy + 2);
+      y0 = cy - 2;
+      y1 = min(g.gy - 1, cy + 2);
+    }
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+      const int yy = y0 + r;
+      const float dy = fmaxf(0.f, fmaxf(float(yy) - v, v - float(yy + 1)));
+      const float e = sqrt_approx(fmaxf(0.f, __fmaf_rn(-dy, dy, g.rho * g.rho)));
+      const int xa = clamp_floor(u - e, 0, g.gx), xb = clamp_floor(u + e, -1, g.gx - 1);
+      a[r] = b[r] = 0;
+      if (yy >= 0 && yy <= y1 && dy < g.rho && xa <= xb) {
+        a[r] = cell_start(starts, base, yy * g.gx + xa);
+        b[r] = cell_start(starts, base, yy * g.gx + xb + 1);
+      }
+    }
+  }
+};
+
+// One thread per query, in cell order.  r2t is fl32(R^2), or the least
+// subnormal when that is 0 (then only exact hits count).
+template <int MODE>
+__global__ void __launch_bounds__(kLocalThreads)
+    local_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
+                       const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
+                       const float4* __restrict__ qrec, int64_t m, double p, float r2f,
+                       float r2t, float* __restrict__ out, int32_t* __restrict__ count_out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= m) return;
+  const float4 r = qrec[t];
+  const float qx = r.x, qy = r.y;
+  const int j = __float_as_int(r.z);
+  const Runs runs(*grid, qx, qy, starts, base);
+  const float hp = static_cast<float>(0.5 * p), nhp = -hp;
+
+  u64 hi = 0, lo = 0;  // (sum w, sum w z) and their TwoSum errors
+  float pe = 0.f;      // rounding errors of the products w z
+  int cnt = 0, best = INT_MAX;
+  float bestz = 0.f;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    for (int k = runs.a[r]; k < runs.b[r]; ++k) {
+      const float4 v = sorted[k];
+      const float d2 = fp32_d2(qx, qy, v.x, v.y);
+      if (d2 < r2t) {
+        if (d2 == 0.f && v.x == qx && v.y == qy) {
+          const int idx = __float_as_int(v.w);
+          if (idx < best) {
+            best = idx;
+            bestz = v.z;
+          }
+        } else if (d2 < r2f) {
+          const float w = local_weight<MODE>(d2, hp, nhp);
+          const float wz = __fmul_rn(w, v.z);
+          pe = __fadd_rn(pe, __fmaf_rn(w, v.z, -wz));
+          two_sum_acc(hi, lo, pk(w, wz));
+          ++cnt;
+        }
+      }
+    }
+  }
+  if (best != INT_MAX) {
+    out[j] = bestz;
+    if (count_out) count_out[j] = -1;
+    return;
+  }
+  if (count_out) count_out[j] = cnt;
+  if (cnt == 0) {
+    out[j] = __int_as_float(0x7fc00000);  // NaN: no data point within R
+    return;
+  }
+  float h0, h1, l0, l1;
+  upk(hi, h0, h1);
+  upk(lo, l0, l1);
+  l1 = __fadd_rn(l1, pe);
+  if (h0 >= kTinyPerMember * float(cnt) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
+      fabsf(l1) <= FLT_MAX) {
+    // Z = (h1 + l1) / (h0 + l0): quotient, then one residual correction.
+    const float z0 = __fdiv_rn(h1, h0);
+    const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
+    out[j] = __fmaf_rn(res, rcp_approx(h0), z0);
+    return;
+  }
+  // Outside FP32's range: FP64, weights scaled by d2_min^(p/2).
+  double dmin = INFINITY;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    for (int k = runs.a[r]; k < runs.b[r]; ++k) {
+      const float4 v = sorted[k];
+      if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
+        const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+        dmin = fmin(dmin, ex * ex + ey * ey);
+      }
+    }
+  }
+  double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    for (int k = runs.a[r]; k < runs.b[r]; ++k) {
+      const float4 v = sorted[k];
+      if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
+        const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+        const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+        s0 += w;
+        s1 += w * double(v.z);
+      }
+    }
+  }
+  out[j] = static_cast<float>(s1 / s0);
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int scan_tiles_of(int64_t max_cells) {
+  return static_cast<int>((max_cells + 1 + kScanTile - 1) / kScanTile);
+}
+
+}  // namespace
+
+// At least two data points per cell on average: finer cells cost more row
+// lookups per query than the candidates they save.
+int64_t local_max_cells(int64_t n) {
+  return std::min<int64_t>(int64_t(kMaxCellsPerAxis) * kMaxCellsPerAxis,
+                           std::max<int64_t>(1024, n / 2));
+}
+
+LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells) {
+  LocalLayout L;
+  L.max_cells = max_cells;
+  const size_t len = size_t(max_cells + 1 + 3) / 4 * 16;  // whole int4s
+  size_t off = 0;
+  L.off_grid = off;       off += round_up(sizeof(GridDev), 256);
+  L.off_counts_d = off;   off += round_up(len, 256);
+  L.off_counts_q = off;   off += round_up(len, 256);
+  L.off_starts_d = off;   off += round_up(len, 256);
+  L.off_starts_q = off;   off += round_up(len, 256);
+  L.off_sums = off;       off += round_up(size_t(2 * scan_tiles_of(max_cells)) * 4, 256);
+  L.off_sorted = off;     off += round_up(size_t(n) * 16, 256);
+  L.off_qrec = off;       off += round_up(size_t(m) * 16, 256);
+  L.bytes = off;
+  return L;
+}
+
+cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
+                         double radius, float* out, int32_t* count_out, void* workspace,
+                         const LocalLayout& L, int sm_count, cudaStream_t s) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  GridDev* grid = reinterpret_cast<GridDev*>(ws + L.off_grid);
+  int32_t* counts_d = reinterpret_cast<int32_t*>(ws + L.off_counts_d);
+  int32_t* counts_q = reinterpret_cast<int32_t*>(ws + L.off_counts_q);
+  int32_t* starts_d = reinterpret_cast<int32_t*>(ws + L.off_starts_d);
+  int32_t* starts_q = reinterpret_cast<int32_t*>(ws + L.off_starts_q);
+  int32_t* sums = reinterpret_cast<int32_t*>(ws + L.off_sums);
+  float4* sorted = reinterpret_cast<float4*>(ws + L.off_sorted);
+  float4* qrec = reinterpret_cast<float4*>(ws + L.off_qrec);
+  const int max_tiles = scan_tiles_of(L.max_cells);
+
+  cudaError_t e = cudaMemsetAsync(grid, 0xff, sizeof(GridDev), s);
+  if (e != cudaSuccess) return e;
+  const unsigned bgrid = static_cast<unsigned>(
+      std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count) * 4, (n + 255) / 256)));
+  box_plan_kernel<<<bgrid, 256, 0, s>>>(data, n, grid, radius, 1.0 / double(L.max_cells));
+  const unsigned zgrid = static_cast<unsigned>(
+      std::min<int64_t>(int64_t(sm_count) * 8, (L.max_cells + 4 + 255) / 256));
+  zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts_d, counts_q);
+  const unsigned pgrid = static_cast<unsigned>((n + m + 255) / 256);
+  count_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, counts_d, counts_q);
+  scan_kernel<<<dim3(max_tiles, 2), kScanBlock, 0, s>>>(grid, counts_d, counts_q, starts_d,
+                                                        starts_q, sums, max_tiles);
+  scatter_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, starts_d, starts_q, sums,
+                                       max_tiles, counts_d, counts_q, sorted, qrec);
+  const float r2f = static_cast<float>(radius * radius);
+  const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
+  const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
+  if (p == 2.0)
+    local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(grid, sorted, starts_d, sums, qrec,
+                                                               m, p, r2f, r2t, out, count_out);
+  else
+    local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
+  return cudaGetLastError();
+}
+
+}  // namespace idw

@@ -1,0 +1,30 @@
+// Internal interface of the local (radius-limited) form: workspace layout
+// and the launch sequence (the grid of cells is planned on the device).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace idw {
+
+// Byte offsets of the local form's scratch inside one workspace.
+struct LocalLayout {
+  int64_t max_cells = 0;
+  size_t off_grid = 0, off_counts_d = 0, off_counts_q = 0, off_starts_d = 0, off_starts_q = 0;
+  size_t off_sums = 0, off_sorted = 0, off_qrec = 0;
+  size_t bytes = 0;
+};
+
+// Cap on the number of cells for n data points (bounds the workspace).
+int64_t local_max_cells(int64_t n);
+LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells);
+
+// Enqueues the whole local form on `s`: bounding box, grid plan, counting
+// sort of data and queries, gather.  No host synchronisation.
+cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
+                         double radius, float* out, int32_t* count_out, void* workspace,
+                         const LocalLayout& L, int sm_count, cudaStream_t s);
+
+}  // namespace idw

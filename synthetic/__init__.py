@@ -17,6 +17,8 @@ every workload here is synthetic.  Recipes:
                   equal weights; samples outside [0,1)^2 are kept as drawn
   grid            g x g cell centres ((i + 0.5)/g, (j + 0.5)/g)
   batch           instance sizes log-uniform in [lo, hi], drawn independently
+  local           uniform data and queries, radius R chosen so that a query
+                  has K data points within R on average: pi R^2 N = K
 """
 from __future__ import annotations
 
@@ -164,3 +166,22 @@ def batch_sizes(seed: int = DEFAULT_SEED + 5, count: int = 256, lo: int = 1024, 
     ln = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
     lm = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
     return ln, lm
+
+
+def local_radius(n: int, members: float) -> float:
+    """R with pi R^2 n = members: the mean neighbour count of uniform data on
+    the unit square (ignoring the boundary)."""
+    return float(np.sqrt(members / (np.pi * n)))
+
+
+def config_local(seed: int = DEFAULT_SEED + 6, n: int = 1 << 20, m: int = 1 << 20,
+                 members: float = 32.0, clustered: bool = False):
+    """Local (radius-limited) workload: N data, M queries, R for ``members``
+    neighbours on average; uniform data with the wave field, or the mixture
+    with the bump field when ``clustered``.  p = 2."""
+    rng = _rng(seed)
+    xy = mixture_xy(rng, n) if clustered else uniform_xy(rng, n)
+    z = field_bump(rng, xy) if clustered else field_wave(rng, xy)
+    data = pack_xyz(xy, z)
+    return {"data": data, "queries": uniform_xy(rng, m), "radius": local_radius(n, members),
+            "p": 2.0}

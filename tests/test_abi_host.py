@@ -56,6 +56,7 @@ def test_null_handle_is_rejected(lib):
     assert lib.idw_interpolate(None, None, 10, None, 10, 2.0, 0, None, None) == 1
     assert lib.idw_destroy(None) == 1
     assert lib.idw_sync_status(None, None) == 1
+    assert lib.idw_interpolate_local(None, None, 10, None, 10, 2.0, 0.1, None, None, None) == 1
     out = ctypes.c_void_p()
     assert lib.idw_create(None, 0) == 1
 
@@ -143,3 +144,5 @@ def test_binding_rejects_host_tensors_for_device_entry():
         idw.interpolate(d, q)
     with pytest.raises(ValueError):
         idw.interpolate(torch.zeros(4, 2), q)
+    with pytest.raises(ValueError):
+        idw.interpolate_local(d, q, 2.0, 0.1)
