@@ -16,11 +16,11 @@
 // fl32(R^2) on the caller's unscaled coordinates.  Weights are FP32 (MUFU
 // reciprocal at p = 2; 2^(-(p/2) log2 d^2) with an FMA-recovered exponent
 // otherwise) and both sums are carried as compensated (hi, lo) FP32 pairs
-// (Knuth's TwoSum per member, the product's rounding error by FMA), then
-// divided with one residual correction.  Sums that leave FP32's range are
-// redone in FP64 with weights scaled by d2_min^(p/2).  A query that
-// coincides with a data point takes the z of the lowest such index; an
-// empty neighbourhood gives NaN.
+// (Knuth's TwoSum per member), then divided with one residual correction.
+// Sums that leave FP32's range, and queries that coincide with a data point
+// (infinite weight), go to an FP64 pass: an exact hit takes the z of the
+// lowest coincident index, other sums are redone with weights scaled by
+// d2_min^(p/2).  An empty neighbourhood gives NaN.
 //
 // Cell positions are computed in FP32 as u(v) = fl(fl(fl(v/2) - fl(x0/2)) *
 // inv2), inv2 = fl(2/h): halving is exact for normal floats and keeps the
@@ -404,8 +404,13 @@ struct Runs {
   }
 };
 
-// One thread per query, in cell order.  r2t is fl32(R^2), or the least
-// subnormal when that is 0 (then only exact hits count).
+// One thread per query, in cell order.  The fast loop takes every candidate
+// with d^2 < r2t, r2t = fl32(R^2) (or the least subnormal when that is 0,
+// so that only d^2 == 0 passes), and sums its FP32 weight.  A coincident
+// point (d^2 == 0) has an infinite or NaN weight, so a query with an exact
+// hit, or with sums outside FP32's range, falls through to the FP64 pass,
+// which takes the z of the lowest coincident index or recomputes the sums
+// with weights scaled by d2_min^(p/2).
 template <int MODE>
 __global__ void __launch_bounds__(kLocalThreads)
     local_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
@@ -420,69 +425,68 @@ __global__ void __launch_bounds__(kLocalThreads)
   const Runs runs(*grid, qx, qy, starts, base);
   const float hp = static_cast<float>(0.5 * p), nhp = -hp;
 
-  u64 hi = 0, lo = 0;  // (sum w, sum w z) and their TwoSum errors
-  float pe = 0.f;      // rounding errors of the products w z
-  int cnt = 0, best = INT_MAX;
-  float bestz = 0.f;
+  // (sum w, sum w z) and their TwoSum errors.  The products w z are rounded
+  // once (2^-24), below the error of the MUFU weights themselves (2^-23).
+  u64 hi = 0, lo = 0;
+  int cnt = 0;
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
+#pragma unroll 2
     for (int k = runs.a[r]; k < runs.b[r]; ++k) {
       const float4 v = sorted[k];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       if (d2 < r2t) {
-        if (d2 == 0.f && v.x == qx && v.y == qy) {
-          const int idx = __float_as_int(v.w);
-          if (idx < best) {
-            best = idx;
-            bestz = v.z;
-          }
-        } else if (d2 < r2f) {
-          const float w = local_weight<MODE>(d2, hp, nhp);
-          const float wz = __fmul_rn(w, v.z);
-          pe = __fadd_rn(pe, __fmaf_rn(w, v.z, -wz));
-          two_sum_acc(hi, lo, pk(w, wz));
-          ++cnt;
-        }
+        const float w = local_weight<MODE>(d2, hp, nhp);
+        two_sum_acc(hi, lo, pk(w, __fmul_rn(w, v.z)));
+        ++cnt;
       }
     }
   }
-  if (best != INT_MAX) {
-    out[j] = bestz;
-    if (count_out) count_out[j] = -1;
-    return;
-  }
-  if (count_out) count_out[j] = cnt;
-  if (cnt == 0) {
-    out[j] = __int_as_float(0x7fc00000);  // NaN: no data point within R
+  if (cnt == 0) {  // no member and no coincident point
+    out[j] = __int_as_float(0x7fc00000);
+    if (count_out) count_out[j] = 0;
     return;
   }
   float h0, h1, l0, l1;
   upk(hi, h0, h1);
   upk(lo, l0, l1);
-  l1 = __fadd_rn(l1, pe);
   if (h0 >= kTinyPerMember * float(cnt) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
       fabsf(l1) <= FLT_MAX) {
     // Z = (h1 + l1) / (h0 + l0): quotient, then one residual correction.
     const float z0 = __fdiv_rn(h1, h0);
     const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
     out[j] = __fmaf_rn(res, rcp_approx(h0), z0);
+    if (count_out) count_out[j] = cnt;
     return;
   }
-  // Outside FP32's range: FP64, weights scaled by d2_min^(p/2).
+  // FP64 pass: exact hits first, then the members' d2_min.
+  int best = INT_MAX, members = 0;
+  float bestz = 0.f;
   double dmin = INFINITY;
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
+  for (int r = 0; r < 5; ++r)
     for (int k = runs.a[r]; k < runs.b[r]; ++k) {
       const float4 v = sorted[k];
-      if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
+      if (v.x == qx && v.y == qy) {
+        const int idx = __float_as_int(v.w);
+        if (idx < best) {
+          best = idx;
+          bestz = v.z;
+        }
+      } else if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
         const double ex = double(qx) - v.x, ey = double(qy) - v.y;
         dmin = fmin(dmin, ex * ex + ey * ey);
+        ++members;
       }
     }
+  if (best != INT_MAX || members == 0) {
+    out[j] = best != INT_MAX ? bestz : __int_as_float(0x7fc00000);
+    if (count_out) count_out[j] = best != INT_MAX ? -1 : 0;
+    return;
   }
   double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-  for (int r = 0; r < 5; ++r) {
+  for (int r = 0; r < 5; ++r)
     for (int k = runs.a[r]; k < runs.b[r]; ++k) {
       const float4 v = sorted[k];
       if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
@@ -492,8 +496,8 @@ __global__ void __launch_bounds__(kLocalThreads)
         s1 += w * double(v.z);
       }
     }
-  }
   out[j] = static_cast<float>(s1 / s0);
+  if (count_out) count_out[j] = members;
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
