@@ -55,6 +55,11 @@ def bind(lib):
                                      ctypes.POINTER(ctypes.c_int64),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     lib.oracle_idw_local.restype = ctypes.c_int
+    lib.oracle_idw_knn.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_int, d,
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_float),
+                                   ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.oracle_idw_knn.restype = ctypes.c_int
     return lib
 
 
@@ -128,6 +133,33 @@ def idw_local(data_xyz, queries_xy, p: float, radius: float, threads: int = 0):
     if rc < 0:
         raise ValueError("oracle_idw_local rejected its arguments")
     return Z, hit, count
+
+
+def idw_knn(data_xyz, queries_xy, p: float, k: int, threads: int = 0):
+    """Eq. 1 over the k data points nearest to each query (FP64 weights).
+
+    Nearness is ranked by (FP32 d2, index) as a GPU evaluates it (see
+    idw_oracle.c).  Returns a dict with Z float64[m] (NaN where nothing is
+    selected), hit int64[m], kd2 float32[m], nbr int64[m, k] (key order, -1
+    padded) and count int32[m].
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    m = q.shape[0]
+    Z = np.empty(m, np.float64)
+    hit = np.empty(m, np.int64)
+    kd2 = np.empty(m, np.float32)
+    nbr = np.empty((m, int(k)), np.int64)
+    count = np.empty(m, np.int32)
+    rc = lib.oracle_idw_knn(_ptr(data), data.shape[0], _ptr(q), m, float(p), int(k), _ptr(Z),
+                            hit.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            kd2.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                            nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                            count.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_knn rejected its arguments")
+    return {"Z": Z, "hit": hit, "kd2": kd2, "nbr": nbr, "count": count}
 
 
 def idw_grad(data_xyz, queries_xy, p: float, g, threads: int = 0):

@@ -38,7 +38,19 @@
  *     member iff d2 < fl32(R^2); the weights then use the exact FP64
  *     distances of the members;
  *   - an exact hit anywhere returns z of the lowest coincident index;
- *   - no member gives NaN.
+ *   - no member gives NaN;
+ *   - data points with a non-finite coordinate are ignored (neither hits
+ *     nor members).
+ *
+ * k-nearest-neighbour variant (the other local form of the related work,
+ * Sec. 1): Eq. 1 over the k data points nearest to the query.  Readings:
+ *   - "nearest" ranks finite data points by the key (d2, index), d2 the same
+ *     FP32 expression as the local membership test, so ties go to the lower
+ *     index and both implementations select the same set;
+ *   - the weights use the exact FP64 distances of the selected points;
+ *   - an exact hit returns z of the lowest coincident index (the selection
+ *     is still reported);
+ *   - fewer than k finite points: all of them; none: NaN.
  *
  * Gradients (not in the paper; derived from Eq. 1 by the chain rule, with
  * S0 = sum w_i, S1 = sum w_i z_i, Z = S1/S0, w_i = (d_i^2)^(-p/2)):
@@ -282,6 +294,8 @@ static void local_range(void *vctx, int64_t b, int64_t e)
         double d2min = INFINITY;
         for (int64_t i = 0; i < c->n; i++) {
             const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            if (!isfinite(x) || !isfinite(y))
+                continue; /* ignored: neither a hit nor a member */
             if (x == qx && y == qy) {
                 k = i;
                 break;
@@ -333,6 +347,173 @@ int oracle_idw_local(const double *data, int64_t n, const double *q, int64_t m, 
     if (m == 0)
         return 0;
     return parallel_for(m, nthreads, local_range, &c);
+}
+
+/* ------------------------------------------------------- k-NN variant */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    double p;
+    int k;
+    double *Z;
+    int64_t *hit;
+    float *kd2;
+    int64_t *nbr;
+    int32_t *count;
+} knn_ctx;
+
+static float fp32_d2(float qx, float qy, float x, float y)
+{
+    float dx = qx - x;
+    float dy = qy - y;
+    float dxx = dx * dx;
+    return fmaf(dy, dy, dxx);
+}
+
+/* Key order: smaller d2 first, then smaller index. */
+static int key_less(float da, int64_t ia, float db, int64_t ib)
+{
+    return da < db || (da == db && ia < ib);
+}
+
+/* Max-heap on the key, size `size`, stored in (hd, hi). */
+static void heap_sift_down(float *hd, int64_t *hi, int size, int at)
+{
+    for (;;) {
+        int l = 2 * at + 1, r = l + 1, big = at;
+        if (l < size && key_less(hd[big], hi[big], hd[l], hi[l]))
+            big = l;
+        if (r < size && key_less(hd[big], hi[big], hd[r], hi[r]))
+            big = r;
+        if (big == at)
+            return;
+        float td = hd[at];
+        int64_t ti = hi[at];
+        hd[at] = hd[big];
+        hi[at] = hi[big];
+        hd[big] = td;
+        hi[big] = ti;
+        at = big;
+    }
+}
+
+static void heap_sift_up(float *hd, int64_t *hi, int at)
+{
+    while (at > 0) {
+        int parent = (at - 1) / 2;
+        if (!key_less(hd[parent], hi[parent], hd[at], hi[at]))
+            return;
+        float td = hd[at];
+        int64_t ti = hi[at];
+        hd[at] = hd[parent];
+        hi[at] = hi[parent];
+        hd[parent] = td;
+        hi[parent] = ti;
+        at = parent;
+    }
+}
+
+static void knn_range(void *vctx, int64_t b, int64_t e)
+{
+    knn_ctx *c = (knn_ctx *)vctx;
+    const int k = c->k;
+    float *hd = (float *)malloc(sizeof(float) * (size_t)k);
+    int64_t *hi = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    if (!hd || !hi) {
+        free(hd);
+        free(hi);
+        for (int64_t j = b; j < e; j++)
+            c->Z[j] = NAN, c->count[j] = -2;
+        return;
+    }
+    for (int64_t j = b; j < e; j++) {
+        const double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+        const float qxf = (float)qx, qyf = (float)qy;
+        int64_t hit = -1;
+        int size = 0;
+        if (isfinite(qx) && isfinite(qy)) {
+            for (int64_t i = 0; i < c->n; i++) {
+                const double x = c->data[3 * i], y = c->data[3 * i + 1];
+                if (!isfinite(x) || !isfinite(y))
+                    continue;
+                if (hit < 0 && x == qx && y == qy)
+                    hit = i;
+                const float d2 = fp32_d2(qxf, qyf, (float)x, (float)y);
+                if (size < k) {
+                    hd[size] = d2;
+                    hi[size] = i;
+                    heap_sift_up(hd, hi, size);
+                    size++;
+                } else if (key_less(d2, i, hd[0], hi[0])) {
+                    hd[0] = d2;
+                    hi[0] = i;
+                    heap_sift_down(hd, hi, size, 0);
+                }
+            }
+        }
+        /* Report the selection in key order (heap sort, ascending). */
+        int64_t *out = c->nbr + (size_t)j * (size_t)k;
+        for (int t = 0; t < k; t++)
+            out[t] = -1;
+        c->kd2[j] = size > 0 ? hd[0] : NAN;
+        for (int s = size; s > 0; s--) {
+            out[s - 1] = hi[0];
+            hd[0] = hd[s - 1];
+            hi[0] = hi[s - 1];
+            heap_sift_down(hd, hi, s - 1, 0);
+        }
+        c->hit[j] = hit;
+        c->count[j] = size;
+        if (hit >= 0) {
+            c->Z[j] = c->data[3 * hit + 2];
+            continue;
+        }
+        if (size == 0) {
+            c->Z[j] = NAN;
+            continue;
+        }
+        double d2min = INFINITY;
+        for (int t = 0; t < size; t++) {
+            const int64_t i = out[t];
+            const double d2 = sqdist(qx, qy, c->data[3 * i], c->data[3 * i + 1]);
+            if (d2 < d2min)
+                d2min = d2;
+        }
+        nsum s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+        for (int t = 0; t < size; t++) {
+            const int64_t i = out[t];
+            const double w = scaled_weight(d2min, sqdist(qx, qy, c->data[3 * i], c->data[3 * i + 1]),
+                                           c->p);
+            nsum_add(&s0, w);
+            nsum_add(&s1, w * c->data[3 * i + 2]);
+        }
+        c->Z[j] = nsum_value(&s1) / nsum_value(&s0);
+    }
+    free(hd);
+    free(hi);
+}
+
+/*
+ * k-NN Eq. 1: the k data points nearest to each query by the key
+ * (fl32 d2, index).  Outputs Z[m], hit[m] (lowest coincident index or -1),
+ * kd2[m] (the FP32 d2 of the last selected point, NaN if none), nbr[m*k]
+ * (selected indices in key order, -1 padded) and count[m] (points
+ * selected: min(k, finite points), 0 for a non-finite query).  Returns
+ * threads used, or -1 on bad arguments.
+ */
+int oracle_idw_knn(const double *data, int64_t n, const double *q, int64_t m, double p, int k,
+                   double *Z, int64_t *hit, float *kd2, int64_t *nbr, int32_t *count,
+                   int nthreads)
+{
+    if (!data || !q || !Z || !hit || !kd2 || !nbr || !count || n < 1 || m < 0 || k < 1 ||
+        !(p > 0.0) || !isfinite(p))
+        return -1;
+    knn_ctx c = {data, n, q, p, k, Z, hit, kd2, nbr, count};
+    if (m == 0)
+        return 0;
+    return parallel_for(m, nthreads, knn_range, &c);
 }
 
 /* ------------------------------------------------------------ gradients */

@@ -39,7 +39,19 @@ MUTATIONS = [
      "    float d2 = fmaf(dy, dy, dxx);\n    return (double)(qx - x) * (qx - x) + (double)(qy - y) * (qy - y) < r2f;"),
     ("local weights over all points", "            if (!local_member(qxf, qyf, (float)x, (float)y, c->r2f))\n                continue;",
      "            (void)local_member;"),
-    ("local empty neighbourhood not NaN", "            c->Z[j] = NAN;", "            c->Z[j] = 0.0;"),
+    ("local empty neighbourhood not NaN", "        if (count == 0) {\n            c->Z[j] = NAN;",
+     "        if (count == 0) {\n            c->Z[j] = 0.0;"),
+    ("knn ties to the higher index", "return da < db || (da == db && ia < ib);",
+     "return da < db || (da == db && ia > ib);"),
+    ("knn keys in FP64", "    float dxx = dx * dx;\n    return fmaf(dy, dy, dxx);",
+     "    float dxx = dx * dx;\n    (void)dxx;\n    return (float)((double)(qx - x) * (qx - x) + (double)(qy - y) * (qy - y));"),
+    ("knn keeps k - 1", "                if (size < k) {", "                if (size < k - 1) {"),
+    ("knn hit loses precedence", "        if (hit >= 0) {\n            c->Z[j] = c->data[3 * hit + 2];",
+     "        if (hit >= 0 && 0) {\n            c->Z[j] = c->data[3 * hit + 2];"),
+    ("local hit on non-finite points", "            if (!isfinite(x) || !isfinite(y))\n                continue; /* ignored: neither a hit nor a member */",
+     "            if (0)\n                continue;"),
+    ("knn ignores non-finite check", "                if (!isfinite(x) || !isfinite(y))\n                    continue;\n                if (hit < 0",
+     "                if (hit < 0"),
     ("exact-hit gradient dropped", "                if (c->hit[j] == i)\n                    nsum_add(&gz, gj);",
      "                if (c->hit[j] == i)\n                    nsum_add(&gz, 0.0);"),
 ]
@@ -63,6 +75,13 @@ PINS = [
     pins.test_local_with_huge_radius_is_the_global_form,
     pins.test_local_no_member_is_nan,
     pins.test_local_membership_is_decided_in_fp32,
+    lambda: pins.test_knn_exact_rational(3),
+    pins.test_knn_ties_go_to_the_lower_index,
+    pins.test_knn_with_k_at_least_n_is_the_global_form,
+    pins.test_knn_k1_is_the_nearest_neighbour,
+    pins.test_knn_selection_is_decided_in_fp32,
+    pins.test_knn_non_finite_inputs,
+    pins.test_local_ignores_non_finite_points,
 ]
 
 

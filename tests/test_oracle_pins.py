@@ -404,3 +404,148 @@ def test_local_membership_is_decided_in_fp32():
         data = np.array([[pt[0], pt[1], 7.0], [0.9, 0.9, 1.0]], np.float32)
         Z, hit, count = oracle.idw_local(data, q, 2.0, radius)
         assert count[0] == (1 if member else 0)
+
+
+# ---------------------------------------------------------------- k-NN form
+
+def _fp32_key(qx, qy, x, y):
+    """FP32 d^2 = fmaf(dy, dy, fl32(dx dx)), emulated exactly."""
+    dx = np.float32(np.float32(qx) - np.float32(x))
+    dy = np.float32(np.float32(qy) - np.float32(y))
+    dxx = np.float32(dx * dx)
+    return _round_f32(Fraction(float(dy)) ** 2 + Fraction(float(dxx)))
+
+
+def _knn_exact(data, q, k, p_even=2):
+    """Exact selection by the key (FP32 d^2, index) and exact rational Z."""
+    out = []
+    for qx, qy in q.astype(np.float32):
+        fin = [i for i in range(data.shape[0])
+               if np.isfinite(data[i, 0]) and np.isfinite(data[i, 1])]
+        if not (np.isfinite(qx) and np.isfinite(qy)):
+            out.append((float("nan"), -1, [], 0))
+            continue
+        hit = next((i for i in fin if data[i, 0] == qx and data[i, 1] == qy), -1)
+        keys = sorted((float(_fp32_key(qx, qy, data[i, 0], data[i, 1])), i) for i in fin)
+        sel = [i for _, i in keys[:k]]
+        if hit >= 0:
+            out.append((float(data[hit, 2]), hit, sel, len(sel)))
+            continue
+        s0 = Fraction(0)
+        s1 = Fraction(0)
+        for i in sel:
+            d2 = (Fraction(float(qx)) - Fraction(float(data[i, 0]))) ** 2 + \
+                 (Fraction(float(qy)) - Fraction(float(data[i, 1]))) ** 2
+            w = 1 / d2 ** (p_even // 2)
+            s0 += w
+            s1 += w * Fraction(float(data[i, 2]))
+        out.append((float(s1 / s0) if sel else float("nan"), -1, sel, len(sel)))
+    return out
+
+
+def _check_knn(data, q, k, p_even=2):
+    r = oracle.idw_knn(data, q, float(p_even), k)
+    zmax = np.nanmax(np.abs(data[:, 2]))
+    for j, (ze, he, sel, ce) in enumerate(_knn_exact(data, q, k, p_even)):
+        assert r["hit"][j] == he and r["count"][j] == ce, (j, r["hit"][j], he, r["count"][j], ce)
+        got = [int(i) for i in r["nbr"][j] if i >= 0]
+        assert got == sel, (j, got, sel)
+        assert np.all(r["nbr"][j][len(sel):] == -1)
+        if np.isnan(ze):
+            assert np.isnan(r["Z"][j])
+        else:
+            assert abs(r["Z"][j] - ze) <= 4e-16 * zmax, (j, r["Z"][j], ze)
+    return r
+
+
+@pytest.mark.parametrize("k", [1, 3, 7, 16])
+def test_knn_exact_rational(k):
+    data, q = _tiny(41, 40, 20)
+    q[3] = data[11, :2]  # an exact hit
+    for p_even in (2, 4):
+        _check_knn(data, q, k, p_even)
+
+
+def test_knn_ties_go_to_the_lower_index():
+    # Four points exactly 1/4 from the query (FP32 keys equal), one nearer,
+    # one farther; indices arranged so that the tie order is visible.
+    data = np.array([[0.75, 0.5, 1.0], [0.5, 0.25, 2.0], [0.5, 0.5625, 3.0],
+                     [0.25, 0.5, 4.0], [0.5, 0.75, 5.0], [0.9, 0.9, 6.0]], np.float32)
+    q = np.array([[0.5, 0.5]], np.float32)
+    for k, sel in ((1, [2]), (2, [2, 0]), (3, [2, 0, 1]), (4, [2, 0, 1, 3]), (6, [2, 0, 1, 3, 4, 5])):
+        r = _check_knn(data, q, k)
+        assert [int(i) for i in r["nbr"][0] if i >= 0] == sel
+    r = oracle.idw_knn(data, q, 2.0, 2)
+    # Z over {2, 0} at distances 1/16 and 1/4: weights 256 and 16.
+    assert r["Z"][0] == (256 * 3.0 + 16 * 1.0) / (256 + 16)
+    assert r["kd2"][0] == np.float32(0.0625)
+
+
+def test_knn_with_k_at_least_n_is_the_global_form():
+    prob = synthetic.uniform_problem(300, 120, seed=43, exact_hits=3)
+    for p in (2.0, 3.5):
+        Zg, hg = oracle.idw(prob["data"], prob["queries"], p)
+        for k in (300, 305):
+            r = oracle.idw_knn(prob["data"], prob["queries"], p, k)
+            assert np.array_equal(r["hit"], hg)
+            assert np.all(r["count"] == 300)
+            assert np.max(np.abs(r["Z"] - Zg)) <= 1e-15 * np.abs(prob["data"][:, 2]).max()
+
+
+def test_knn_k1_is_the_nearest_neighbour():
+    data, q = _tiny(44, 500, 200)
+    r = oracle.idw_knn(data, q, 2.0, 1)
+    for j in range(q.shape[0]):
+        keys = [(float(_fp32_key(q[j, 0], q[j, 1], x, y)), i) for i, (x, y, _) in enumerate(data)]
+        i = min(keys)[1]
+        assert r["nbr"][j, 0] == i and r["Z"][j] == np.float64(data[i, 2])
+
+
+def test_knn_selection_is_decided_in_fp32():
+    """Find two points whose FP32 keys rank differently from their exact
+    distances; the oracle must follow the FP32 key (a GPU ranks the same)."""
+    rng = np.random.default_rng(45)
+    q = np.array([[0.5, 0.5]], np.float32)
+    found = 0
+    for _ in range(40000):
+        r0 = 0.3 * (1 + rng.uniform(-2e-7, 2e-7))
+        a0, a1 = rng.uniform(0, 2 * np.pi, 2)
+        pa = np.array([0.5 + r0 * np.cos(a0), 0.5 + r0 * np.sin(a0)], np.float32)
+        pb = np.array([0.5 + 0.3 * np.cos(a1), 0.5 + 0.3 * np.sin(a1)], np.float32)
+        ka, kb = _fp32_key(q[0, 0], q[0, 1], *pa), _fp32_key(q[0, 0], q[0, 1], *pb)
+        ea = (Fraction(float(q[0, 0])) - Fraction(float(pa[0]))) ** 2 + \
+             (Fraction(float(q[0, 1])) - Fraction(float(pa[1]))) ** 2
+        eb = (Fraction(float(q[0, 0])) - Fraction(float(pb[0]))) ** 2 + \
+             (Fraction(float(q[0, 1])) - Fraction(float(pb[1]))) ** 2
+        fp32_first = (float(ka), 0) < (float(kb), 1)
+        if ea == eb or fp32_first == (ea < eb):
+            continue
+        # pa at index 0, pb at index 1: the FP32 key order (ties: index 0
+        # first) disagrees with the exact order.
+        data = np.array([[pa[0], pa[1], 1.0], [pb[0], pb[1], 2.0]], np.float32)
+        r = oracle.idw_knn(data, q, 2.0, 1)
+        want = 0 if fp32_first else 1
+        assert r["nbr"][0, 0] == want
+        found += 1
+        if found >= 4:
+            break
+    assert found, "no disagreeing pair found"
+
+
+def test_knn_non_finite_inputs():
+    data = np.array([[np.nan, 0.5, 9.0], [0.5, np.inf, 9.0], [0.1, 0.1, 1.0],
+                     [0.9, 0.9, 2.0], [0.2, 0.2, 3.0]], np.float32)
+    q = np.array([[0.15, 0.15], [np.nan, 0.5], [0.5, np.inf]], np.float32)
+    r = _check_knn(data, q, 4)
+    assert r["count"][0] == 3 and np.all(r["count"][1:] == 0)
+    assert np.isnan(r["Z"][1]) and np.isnan(r["Z"][2]) and np.isnan(r["kd2"][1])
+
+
+def test_local_ignores_non_finite_points():
+    # A data point with a non-finite coordinate is neither a hit nor a
+    # member, even for a query with the same (non-finite) coordinates.
+    data = np.array([[np.inf, 0.5, 9.0], [np.nan, 0.2, 8.0], [0.1, 0.1, 1.0]], np.float32)
+    q = np.array([[np.inf, 0.5], [0.1, 0.12]], np.float32)
+    Z, hit, count = oracle.idw_local(data, q, 2.0, 0.5)
+    assert np.isnan(Z[0]) and hit[0] == -1 and count[0] == 0
+    assert Z[1] == 1.0 and count[1] == 1
