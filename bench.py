@@ -106,11 +106,11 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=float, nargs="*", default=None,
-                    help="local workload only: uniform data with these mean neighbour "
-                         "counts K instead of the default sweep")
+                    help="local / knn workloads only: uniform data with these neighbour "
+                         "counts (K, or k) instead of the default sweep")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "scale", "clustered", "adjoint", "batched", "layout",
-                             "paper", "local", "all"],
+                             "paper", "local", "knn", "all"],
                     help="headline = the N=M=2^20 line; the others measure the other "
                          "workloads (one JSON line each)")
     return ap.parse_args()
@@ -677,6 +677,40 @@ def run_local(args):
           metric="local queries/s", unit="queries/s")
 
 
+def run_knn(args):
+    """k-nearest-neighbour form: N = M = 2^20, k in {8, 32, 64}, uniform and
+    clustered data, p in {2, 3.5}.  Each call builds the grid and searches."""
+    import torch
+    import oracle
+    import synthetic
+    import paper_1402_4986_gb300 as idw
+    rows = []
+    ks = tuple(int(k) for k in args.members) if args.members else (8, 32, 64)
+    cases = [(False, k) for k in ks] + ([] if args.members else [(True, 32)])
+    for clustered, k in cases:
+        prob = synthetic.config_local(clustered=clustered)
+        d = torch.from_numpy(prob["data"]).cuda()
+        q = torch.from_numpy(prob["queries"]).cuda()
+        n, m = d.shape[0], q.shape[0]
+        out = torch.empty(m, device="cuda")
+        idx = np.random.default_rng(6).choice(m, 128, replace=False)
+        for p in (2.0, 3.5):
+            ms = _events_ms(lambda: idw.interpolate_knn(d, q, p, k, out=out), 10, warm=3)
+            r = oracle.idw_knn(prob["data"], prob["queries"][idx], p, k)
+            _, nbr = idw.interpolate_knn(d, q, p, k, neighbours=True)
+            err = float(np.max(np.abs(out.cpu().numpy()[idx] - r["Z"])) /
+                        np.max(np.abs(prob["data"][:, 2])))
+            rows.append({"data": "clustered" if clustered else "uniform", "n": n, "m": m, "k": k,
+                         "p": p, "ms": ms, "queries_s": m / (ms / 1e3),
+                         "neighbour_pairs_s": float(m) * k / (ms / 1e3),
+                         "neighbours_match_oracle": bool(np.array_equal(
+                             nbr.cpu().numpy()[idx], r["nbr"])),
+                         "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+    _emit("k-nearest-neighbour Eq. 1: N = M = 2^20, queries uniform on [0,1)^2; data uniform "
+          "(wave field) or 64 Gaussian blobs (bump field); time per call includes the grid build",
+          rows, metric="knn queries/s", unit="queries/s")
+
+
 def main():
     args = parse()
     ws, rank, local = dist_env()
@@ -693,7 +727,8 @@ def main():
     libbuild.build()
     for name, fn in (("scale", run_scale), ("clustered", run_clustered),
                      ("adjoint", run_adjoint), ("batched", run_batched),
-                     ("layout", run_layout), ("paper", run_paper), ("local", run_local)):
+                     ("layout", run_layout), ("paper", run_paper), ("local", run_local),
+                     ("knn", run_knn)):
         if args.config in (name, "all"):
             fn(args)
 

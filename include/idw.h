@@ -363,6 +363,41 @@ idw_status idw_interpolate_local(idw_handle_t handle, const float *data_xyz, int
                                  const float *queries_xy, int64_t m, double p, double radius,
                                  float *out, int32_t *count_out, void *stream);
 
+/*
+ * k-nearest-neighbour Shepard interpolation, the other local form of the
+ * related work the paper cites (Sec. 1): Z(q) is Eq. 1 over the k finite
+ * data points nearest to q.  Nearness is the key (d2, index) with
+ *
+ *   d2 = fl32(fmaf(dy, dy, fl32(dx * dx))),  dx = fl32(qx - x_i), dy = fl32(qy - y_i),
+ *
+ * ranked ascending, so exact ties go to the lower data index and the
+ * selection is one definite set.  Weights are d^-p from the selected keys
+ * (FP32, summed as compensated pairs; FP64 where the sums leave FP32's
+ * range).  A query that coincides with a data point takes the z of the
+ * lowest such index (the selection is still reported).  Fewer than k finite
+ * points: all of them.  Non-finite data points are ignored; a non-finite
+ * query gets NaN and selects nothing.
+ *
+ *   data_xyz, queries_xy, out : device float arrays as in idw_interpolate.
+ *   k                         : 1 <= k <= 64.
+ *   nbr_out                   : NULL, or device int32[m * k]: row j holds the
+ *                               selected data indices in key order, -1 padded.
+ *   kd2_out                   : NULL, or device float[m]: the k-th (largest
+ *                               selected) key's d2, NaN when nothing is selected.
+ *
+ * Method, on `stream` without host synchronisation (graph-capturable): the
+ * grid build of idw_interpolate_local with cells sized for k points at the
+ * data's mean density, then one thread per query (in cell order) searches
+ * square rings of cells around the grid cell nearest to it, keeping the k
+ * best keys in shared memory, and stops once the k-th key is below a
+ * conservative FP32 lower bound on the key of any point not yet seen.
+ * Workspace as idw_interpolate_local.  Errors as in idw_interpolate, plus
+ * IDW_ERR_INVALID_ARG for k outside [1, 64].
+ */
+idw_status idw_interpolate_knn(idw_handle_t handle, const float *data_xyz, int64_t n,
+                               const float *queries_xy, int64_t m, double p, int32_t k,
+                               float *out, int32_t *nbr_out, float *kd2_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

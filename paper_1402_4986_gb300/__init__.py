@@ -20,7 +20,7 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
-    "interpolate_batched", "interpolate_local", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
+    "interpolate_batched", "interpolate_local", "interpolate_knn", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
@@ -222,6 +222,29 @@ def interpolate_local(data, queries, p: float = 2.0, radius: float = float("inf"
                                      _stream(data))
     _lib.check(st, "idw_interpolate_local", h.ptr)
     return (out, cnt) if counts else out
+
+
+def interpolate_knn(data, queries, p: float = 2.0, k: int = 16, out=None,
+                    neighbours: bool = False, kth_d2: bool = False,
+                    handle: Handle | None = None):
+    """Eq. 1 over the k data points nearest to each query (FP32).
+
+    Returns ``out`` (float32[m]); with ``neighbours`` also int32[m, k] (the
+    selected indices in key order, -1 padded) and with ``kth_d2`` also
+    float32[m] (the k-th key's squared distance), in that order.
+    """
+    _check_inputs(data, queries, PREC_F32_COMP)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=data.device)
+    nbr = torch.empty(m, int(k), dtype=torch.int32, device=data.device) if neighbours else None
+    kd2 = torch.empty(m, dtype=torch.float32, device=data.device) if kth_d2 else None
+    st = h.lib.idw_interpolate_knn(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p),
+                                   int(k), _ptr(out), _ptr(nbr), _ptr(kd2), _stream(data))
+    _lib.check(st, "idw_interpolate_knn", h.ptr)
+    res = (out,) + ((nbr,) if neighbours else ()) + ((kd2,) if kth_d2 else ())
+    return res if len(res) > 1 else out
 
 
 def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=True,

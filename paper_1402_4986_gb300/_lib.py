@@ -87,6 +87,8 @@ SIGNATURES = {
                                         c_void_p]),
     "idw_interpolate_local": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                       c_double, c_void_p, c_void_p, c_void_p]),
+    "idw_interpolate_knn": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
+                                    c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -530,6 +530,25 @@ idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
+idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, const float* queries,
+                               int64_t m, double p, int32_t k, float* out, int32_t* nbr_out,
+                               float* kd2_out, void* stream) {
+  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, out);
+  if (st != IDW_OK) return st;
+  if (k < 1 || k > idw::kKnnMax) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if ((nbr_out && !aligned(nbr_out, 4)) || (kd2_out && !aligned(kd2_out, 4)))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_knn(data, n, queries, m, p, k, out, nbr_out, kd2_out, h->ws, L,
+                                        h->sm_count, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
 idw_status idw_sync_status(idw_handle_t h, void* stream) {
   if (!h) return IDW_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);

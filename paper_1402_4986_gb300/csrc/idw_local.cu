@@ -105,8 +105,12 @@ __device__ __forceinline__ int clamp_floor(float u, int lo, int hi) {
   return static_cast<int>(fminf(fmaxf(floorf(u), float(lo)), float(hi)));
 }
 
-// Grid for the box in grid->keys (one thread).
-__device__ void plan_grid(GridDev* grid, double radius, double inv_max_cells) {
+// Grid for the box in grid->keys (one thread).  For the k-NN form
+// (knn_k > 0) the cells are sized as for a radius holding k points at the
+// data's mean density over the box, sqrt(k area / (pi n)); the radius only
+// sets the cell size there, not the result.
+__device__ void plan_grid(GridDev* grid, double radius, double inv_max_cells, int knn_k,
+                          int64_t n) {
   const unsigned k0 = __ldcg(&grid->keys[0]), k1 = __ldcg(&grid->keys[1]);
   const unsigned k2 = __ldcg(&grid->keys[2]), k3 = __ldcg(&grid->keys[3]);
   int gx = 1, gy = 1;
@@ -115,6 +119,14 @@ __device__ void plan_grid(GridDev* grid, double radius, double inv_max_cells) {
     const float xmin = key_float(k0), ymin = key_float(k1);
     const float xmax = key_float(~k2), ymax = key_float(~k3);
     const double ex = double(xmax) - xmin, ey = double(ymax) - ymin;
+    if (knn_k > 0) {
+      if (ex * ey > 0.0)
+        radius = sqrt(double(knn_k) * ex * ey / (3.141592653589793 * double(n)));
+      else if (fmax(ex, ey) > 0.0)
+        radius = fmax(ex, ey) * double(knn_k) / (2.0 * double(n));  // points on a line
+      else
+        radius = 1.0;  // all points coincide: one cell
+    }
     double h = fmax(fmax(radius * (0.5 + 0x1p-7), 0x1p-61),
                     fmax(ex * (1.0 / (kMaxCellsPerAxis - 1)), ey * (1.0 / (kMaxCellsPerAxis - 1))));
     h = fmax(h, sqrt(ex * ey * inv_max_cells));
@@ -148,7 +160,7 @@ __device__ void plan_grid(GridDev* grid, double radius, double inv_max_cells) {
 // the grid.
 __global__ void __launch_bounds__(256)
     box_plan_kernel(const float* __restrict__ data, int64_t n, GridDev* __restrict__ grid,
-                    double radius, double inv_max_cells) {
+                    double radius, double inv_max_cells, int knn_k) {
   __shared__ unsigned part[4][8];
   __shared__ bool last;
   unsigned k0 = 0xffffffffu, k1 = 0xffffffffu, k2 = 0xffffffffu, k3 = 0xffffffffu;
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    plan_grid(grid, radius, inv_max_cells);
+    plan_grid(grid, radius, inv_max_cells, knn_k, n);
   }
 }
 
@@ -500,6 +512,208 @@ __global__ void __launch_bounds__(kLocalThreads)
   if (count_out) count_out[j] = members;
 }
 
+// ------------------------------------------------------------- k-NN form
+//
+// One thread per query, in cell order, searches square rings of cells around
+// the grid cell nearest to it and keeps the k smallest keys (FP32 d^2, data
+// index) in shared memory (slot s of thread t at [s * kKnnThreads + t]:
+// conflict-free), with the worst key tracked in registers.  After each ring
+// it stops once the k-th key is below a lower bound on the key of any point
+// not yet seen.  Such a point lies in the grid's box and outside the searched
+// square, on one of its sides that still has grid cells; with ax, ay the
+// query's distance to the box along each axis and D the distance to that
+// side (cell units, each minus a margin mg = (|u| + |v|) 2^-22 + 2^-9 for
+// the cell-position errors), its true distance is at least
+// h sqrt(max(ax, D)^2 + ay^2) (or the y analogue), and its FP32 key at
+// least that squared times (1 - 2^-18), minus 2^-126.  An exact tie with the
+// k-th key needs a strictly larger bound, so ties by index are never
+// decided by a point the search skipped.
+
+constexpr int kKnnThreads = 128;
+
+struct KnnTop {
+  float* d;    // keys' d^2, [KMAX][kKnnThreads]
+  int* pos;    // sorted positions, same layout
+  int size = 0, worst_s = 0, worst_i = -1;
+  float worst_d = 0.f;
+};
+
+__device__ __forceinline__ int data_index(const float4* __restrict__ sorted, int pos) {
+  return __float_as_int(sorted[pos].w);
+}
+
+// Slot of the largest key among the first `size` slots.
+__device__ __forceinline__ void knn_rescan(KnnTop& tp, const float4* __restrict__ sorted) {
+  float wd = tp.d[0];
+  int ws = 0, wi = -1;
+  for (int s = 1; s < tp.size; ++s) {
+    const float d = tp.d[s * kKnnThreads];
+    if (d > wd) {
+      wd = d;
+      ws = s;
+      wi = -1;
+    } else if (d == wd) {  // equal d^2: the larger index is the larger key
+      if (wi < 0) wi = data_index(sorted, tp.pos[ws * kKnnThreads]);
+      const int i2 = data_index(sorted, tp.pos[s * kKnnThreads]);
+      if (i2 > wi) {
+        ws = s;
+        wi = i2;
+      }
+    }
+  }
+  tp.worst_d = wd;
+  tp.worst_s = ws;
+  tp.worst_i = wi >= 0 ? wi : data_index(sorted, tp.pos[ws * kKnnThreads]);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kKnnThreads)
+    knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
+                     const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
+                     const float4* __restrict__ qrec, int64_t m, double p, int k,
+                     float* __restrict__ out, int32_t* __restrict__ nbr_out,
+                     float* __restrict__ kd2_out) {
+  extern __shared__ __align__(16) unsigned char knn_smem[];
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= m) return;  // no block-wide barrier in this kernel
+  KnnTop tp;
+  tp.d = reinterpret_cast<float*>(knn_smem) + threadIdx.x;
+  tp.pos = reinterpret_cast<int*>(knn_smem) + k * kKnnThreads + threadIdx.x;
+  const GridDev g = *grid;
+  const float4 rq = qrec[t];
+  const float qx = rq.x, qy = rq.y;
+  const int j = __float_as_int(rq.z);
+  int best_hit = INT_MAX;
+  float hit_z = 0.f;
+
+  auto consider_run = [&](int yy, int xa, int xb) {
+    const int a = cell_start(starts, base, yy * g.gx + xa);
+    const int b = cell_start(starts, base, yy * g.gx + xb + 1);
+    for (int q = a; q < b; ++q) {
+      const float4 v = sorted[q];
+      const float d2 = fp32_d2(qx, qy, v.x, v.y);
+      const int idx = __float_as_int(v.w);
+      if (d2 == 0.f && v.x == qx && v.y == qy && idx < best_hit) {
+        best_hit = idx;
+        hit_z = v.z;
+      }
+      if (tp.size < k) {
+        tp.d[tp.size * kKnnThreads] = d2;
+        tp.pos[tp.size * kKnnThreads] = q;
+        if (++tp.size == k) knn_rescan(tp, sorted);
+      } else if (d2 < tp.worst_d || (d2 == tp.worst_d && idx < tp.worst_i)) {
+        tp.d[tp.worst_s * kKnnThreads] = d2;
+        tp.pos[tp.worst_s * kKnnThreads] = q;
+        knn_rescan(tp, sorted);
+      }
+    }
+  };
+
+  if (finite2(qx, qy)) {
+    const float u = cell_pos(qx, g.hx0, g.inv2), v = cell_pos(qy, g.hy0, g.inv2);
+    const int cx = clamp_floor(u, 0, g.gx - 1), cy = clamp_floor(v, 0, g.gy - 1);
+    const int r_end = max(max(cx, g.gx - 1 - cx), max(cy, g.gy - 1 - cy));
+    const float mg = __fmaf_ru(fabsf(u) + fabsf(v), 0x1p-22f, 0x1p-9f);
+    const float ax = fmaxf(0.f, fmaxf(u - float(g.gx), -u) - mg);
+    const float ay = fmaxf(0.f, fmaxf(v - float(g.gy), -v) - mg);
+    const float hh = g.inv2 > 0.f ? 2.f / g.inv2 : 0.f;
+    const float h2 = __fmul_rd(hh, hh) * (1.f - 0x1p-18f);
+    for (int r = 0; r <= r_end; ++r) {
+      if (r == 0) {
+        consider_run(cy, cx, cx);
+      } else {
+        if (cy - r >= 0) consider_run(cy - r, max(0, cx - r), min(g.gx - 1, cx + r));
+        if (cy + r < g.gy) consider_run(cy + r, max(0, cx - r), min(g.gx - 1, cx + r));
+        const int y0 = max(0, cy - r + 1), y1 = min(g.gy - 1, cy + r - 1);
+        for (int yy = y0; yy <= y1; ++yy) {
+          if (cx - r >= 0) consider_run(yy, cx - r, cx - r);
+          if (cx + r < g.gx) consider_run(yy, cx + r, cx + r);
+        }
+      }
+      if (tp.size < k) continue;
+      float l2 = INFINITY;
+      if (cx - r > 0) {
+        const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
+        l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+      }
+      if (cx + r < g.gx - 1) {
+        const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
+        l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+      }
+      if (cy - r > 0) {
+        const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
+        l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+      }
+      if (cy + r < g.gy - 1) {
+        const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
+        l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+      }
+      // l2 = inf: no grid cell left unsearched (the loop ends anyway).
+      if (tp.worst_d < __fmul_rd(l2, h2) - 0x1p-126f) break;
+    }
+  }
+  const int size = tp.size;
+  if (size > 0 && size < k) knn_rescan(tp, sorted);
+  if (kd2_out) kd2_out[j] = size > 0 ? tp.worst_d : __int_as_float(0x7fc00000);
+  if (nbr_out) {
+    // Insertion sort of the slots by key, then the data indices in order.
+    for (int s = 1; s < size; ++s) {
+      const float d = tp.d[s * kKnnThreads];
+      const int ps = tp.pos[s * kKnnThreads];
+      int at = s;
+      while (at > 0) {
+        const float dp = tp.d[(at - 1) * kKnnThreads];
+        const int pp = tp.pos[(at - 1) * kKnnThreads];
+        const bool later = dp > d || (dp == d && data_index(sorted, pp) > data_index(sorted, ps));
+        if (!later) break;
+        tp.d[at * kKnnThreads] = dp;
+        tp.pos[at * kKnnThreads] = pp;
+        --at;
+      }
+      tp.d[at * kKnnThreads] = d;
+      tp.pos[at * kKnnThreads] = ps;
+    }
+    int32_t* row = nbr_out + int64_t(j) * k;
+    for (int s = 0; s < k; ++s) row[s] = s < size ? data_index(sorted, tp.pos[s * kKnnThreads]) : -1;
+  }
+  if (best_hit != INT_MAX || size == 0) {
+    out[j] = best_hit != INT_MAX ? hit_z : __int_as_float(0x7fc00000);
+    return;
+  }
+  const float hp = static_cast<float>(0.5 * p), nhp = -hp;
+  u64 hi = 0, lo = 0;
+  for (int s = 0; s < size; ++s) {
+    const float w = local_weight<MODE>(tp.d[s * kKnnThreads], hp, nhp);
+    two_sum_acc(hi, lo, pk(w, __fmul_rn(w, sorted[tp.pos[s * kKnnThreads]].z)));
+  }
+  float h0, h1, l0, l1;
+  upk(hi, h0, h1);
+  upk(lo, l0, l1);
+  if (h0 >= kTinyPerMember * float(size) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
+      fabsf(l1) <= FLT_MAX) {
+    const float z0 = __fdiv_rn(h1, h0);
+    const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
+    out[j] = __fmaf_rn(res, rcp_approx(h0), z0);
+    return;
+  }
+  // Outside FP32's range: FP64 over the selected points, scaled by d2_min^(p/2).
+  double dmin = INFINITY;
+  for (int s = 0; s < size; ++s) {
+    const float4 v = sorted[tp.pos[s * kKnnThreads]];
+    const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+    dmin = fmin(dmin, ex * ex + ey * ey);
+  }
+  double s0 = 0.0, s1 = 0.0;
+  for (int s = 0; s < size; ++s) {
+    const float4 v = sorted[tp.pos[s * kKnnThreads]];
+    const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+    const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+    s0 += w;
+    s1 += w * double(v.z);
+  }
+  out[j] = static_cast<float>(s1 / s0);
+}
+
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int scan_tiles_of(int64_t max_cells) {
@@ -532,9 +746,13 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells) {
   return L;
 }
 
-cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
-                         double radius, float* out, int32_t* count_out, void* workspace,
-                         const LocalLayout& L, int sm_count, cudaStream_t s) {
+namespace {
+
+// Enqueues the grid build shared by both local forms: bounding box and plan,
+// histograms, scans, scatter of data and queries into cell order.
+cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries, int64_t m,
+                             double radius, int knn_k, void* workspace, const LocalLayout& L,
+                             int sm_count, cudaStream_t s) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   GridDev* grid = reinterpret_cast<GridDev*>(ws + L.off_grid);
   int32_t* counts_d = reinterpret_cast<int32_t*>(ws + L.off_counts_d);
@@ -550,7 +768,7 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   if (e != cudaSuccess) return e;
   const unsigned bgrid = static_cast<unsigned>(
       std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count) * 4, (n + 255) / 256)));
-  box_plan_kernel<<<bgrid, 256, 0, s>>>(data, n, grid, radius, 1.0 / double(L.max_cells));
+  box_plan_kernel<<<bgrid, 256, 0, s>>>(data, n, grid, radius, 1.0 / double(L.max_cells), knn_k);
   const unsigned zgrid = static_cast<unsigned>(
       std::min<int64_t>(int64_t(sm_count) * 8, (L.max_cells + 4 + 255) / 256));
   zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts_d, counts_q);
@@ -560,6 +778,22 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
                                                         starts_q, sums, max_tiles);
   scatter_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, starts_d, starts_q, sums,
                                        max_tiles, counts_d, counts_q, sorted, qrec);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
+                         double radius, float* out, int32_t* count_out, void* workspace,
+                         const LocalLayout& L, int sm_count, cudaStream_t s) {
+  cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s);
+  if (e != cudaSuccess) return e;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const GridDev* grid = reinterpret_cast<const GridDev*>(ws + L.off_grid);
+  const int32_t* starts_d = reinterpret_cast<const int32_t*>(ws + L.off_starts_d);
+  const int32_t* sums = reinterpret_cast<const int32_t*>(ws + L.off_sums);
+  const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
+  const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
   const float r2f = static_cast<float>(radius * radius);
   const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
@@ -569,6 +803,36 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   else
     local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
+  return cudaGetLastError();
+}
+
+size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * 8; }
+
+cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
+                       int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
+                       const LocalLayout& L, int sm_count, cudaStream_t s) {
+  const size_t smem = knn_smem_bytes(k);
+  cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_query_kernel<kPowGeneral>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  e = launch_grid_sort(data, n, queries, m, 0.0, k, workspace, L, sm_count, s);
+  if (e != cudaSuccess) return e;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const GridDev* grid = reinterpret_cast<const GridDev*>(ws + L.off_grid);
+  const int32_t* starts_d = reinterpret_cast<const int32_t*>(ws + L.off_starts_d);
+  const int32_t* sums = reinterpret_cast<const int32_t*>(ws + L.off_sums);
+  const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
+  const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
+  const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
+  if (p == 2.0)
+    knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(grid, sorted, starts_d, sums, qrec,
+                                                              m, p, k, out, nbr_out, kd2_out);
+  else
+    knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
+        grid, sorted, starts_d, sums, qrec, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 

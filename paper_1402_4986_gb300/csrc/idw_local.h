@@ -1,5 +1,6 @@
-// Internal interface of the local (radius-limited) form: workspace layout
-// and the launch sequence (the grid of cells is planned on the device).
+// Internal interface of the local forms (radius-limited and k nearest
+// neighbours): workspace layout and the launch sequences (the grid of cells
+// is planned on the device).
 #pragma once
 
 #include <cstddef>
@@ -26,5 +27,12 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells);
 cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
                          double radius, float* out, int32_t* count_out, void* workspace,
                          const LocalLayout& L, int sm_count, cudaStream_t s);
+
+// The k-nearest-neighbour form (1 <= k <= kKnnMax): same grid build, then
+// a ring search per query.  nbr_out (m x k) and kd2_out (m) may be null.
+constexpr int kKnnMax = 64;
+cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
+                       int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
+                       const LocalLayout& L, int sm_count, cudaStream_t s);
 
 }  // namespace idw

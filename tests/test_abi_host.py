@@ -57,6 +57,7 @@ def test_null_handle_is_rejected(lib):
     assert lib.idw_destroy(None) == 1
     assert lib.idw_sync_status(None, None) == 1
     assert lib.idw_interpolate_local(None, None, 10, None, 10, 2.0, 0.1, None, None, None) == 1
+    assert lib.idw_interpolate_knn(None, None, 10, None, 10, 2.0, 4, None, None, None, None) == 1
     out = ctypes.c_void_p()
     assert lib.idw_create(None, 0) == 1
 
@@ -146,3 +147,5 @@ def test_binding_rejects_host_tensors_for_device_entry():
         idw.interpolate(torch.zeros(4, 2), q)
     with pytest.raises(ValueError):
         idw.interpolate_local(d, q, 2.0, 0.1)
+    with pytest.raises(ValueError):
+        idw.interpolate_knn(d, q, 2.0, 4)
