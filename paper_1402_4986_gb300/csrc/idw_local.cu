@@ -514,204 +514,221 @@ __global__ void __launch_bounds__(kLocalThreads)
 
 // ------------------------------------------------------------- k-NN form
 //
-// One thread per query, in cell order, searches square rings of cells around
-// the grid cell nearest to it and keeps the k smallest keys (FP32 d^2, data
-// index) in shared memory (slot s of thread t at [s * kKnnThreads + t]:
-// conflict-free), with the worst key tracked in registers.  After each ring
-// it stops once the k-th key is below a lower bound on the key of any point
-// not yet seen.  Such a point lies in the grid's box and outside the searched
-// square, on one of its sides that still has grid cells; with ax, ay the
-// query's distance to the box along each axis and D the distance to that
-// side (cell units, each minus a margin mg = (|u| + |v|) 2^-22 + 2^-9 for
-// the cell-position errors), its true distance is at least
-// h sqrt(max(ax, D)^2 + ay^2) (or the y analogue), and its FP32 key at
-// least that squared times (1 - 2^-18), minus 2^-126.  An exact tie with the
-// k-th key needs a strictly larger bound, so ties by index are never
-// decided by a point the search skipped.
+// One thread per query, in cell order, grows a square of cells around the
+// grid cell nearest to it (radius 0, 1, 2, 3, 4, 6, 9, ...: r += max(1, r/2),
+// the step halved while the added cells would hold more than 4k points; the
+// cells added at each step are walked as row runs) and keeps the k
+// smallest keys in a max-heap in shared memory.  A key is the FP32 d^2's
+// bits (non-negative, so they order as an unsigned integer) above the data
+// index: one 64-bit compare ranks by (d^2, index).  After each step the
+// search stops once the k-th key's d^2 is below a lower bound on the d^2 of
+// any point not yet seen.  Such a point lies in the grid's box and outside
+// the square, beyond one of its sides that still has grid cells; with ax, ay
+// the query's distance to the box along each axis and D the distance to
+// that side (cell units, each minus a margin mg = (|u| + |v|) 2^-22 + 2^-9
+// for the cell-position errors), its true distance is at least
+// h sqrt(max(ax, D)^2 + ay^2) (or the y analogue), and its FP32 d^2 at least
+// that squared times (1 - 2^-18), minus 2^-126.  The bound is strict, so an
+// unseen point can neither beat nor tie the k-th key.
 
 constexpr int kKnnThreads = 128;
 
-struct KnnTop {
-  float* d;    // keys' d^2, [KMAX][kKnnThreads]
-  int* pos;    // sorted positions, same layout
-  int size = 0, worst_s = 0, worst_i = -1;
-  float worst_d = 0.f;
-};
-
-__device__ __forceinline__ int data_index(const float4* __restrict__ sorted, int pos) {
-  return __float_as_int(sorted[pos].w);
+__device__ __forceinline__ u64 knn_key(float d2, int idx) {
+  return (u64(__float_as_uint(d2)) << 32) | u64(unsigned(idx));
 }
+__device__ __forceinline__ float key_d2(u64 key) { return __uint_as_float(unsigned(key >> 32)); }
+__device__ __forceinline__ int key_index(u64 key) { return int(unsigned(key)); }
 
-// Slot of the largest key among the first `size` slots.
-__device__ __forceinline__ void knn_rescan(KnnTop& tp, const float4* __restrict__ sorted) {
-  float wd = tp.d[0];
-  int ws = 0, wi = -1;
-  for (int s = 1; s < tp.size; ++s) {
-    const float d = tp.d[s * kKnnThreads];
-    if (d > wd) {
-      wd = d;
-      ws = s;
-      wi = -1;
-    } else if (d == wd) {  // equal d^2: the larger index is the larger key
-      if (wi < 0) wi = data_index(sorted, tp.pos[ws * kKnnThreads]);
-      const int i2 = data_index(sorted, tp.pos[s * kKnnThreads]);
-      if (i2 > wi) {
-        ws = s;
-        wi = i2;
-      }
+// Max-heap of this thread's keys: slot s at h[s * kKnnThreads] (conflict-free).
+struct KnnHeap {
+  u64* h;
+  int size = 0;
+
+  __device__ __forceinline__ u64 top() const { return h[0]; }
+  __device__ __forceinline__ void push(u64 key) {
+    int at = size++;
+    while (at > 0) {
+      const int parent = (at - 1) >> 1;
+      const u64 pk = h[parent * kKnnThreads];
+      if (pk >= key) break;
+      h[at * kKnnThreads] = pk;
+      at = parent;
     }
+    h[at * kKnnThreads] = key;
   }
-  tp.worst_d = wd;
-  tp.worst_s = ws;
-  tp.worst_i = wi >= 0 ? wi : data_index(sorted, tp.pos[ws * kKnnThreads]);
-}
+  // Replaces the largest key by a smaller one (keys are distinct).
+  __device__ __forceinline__ void replace_top(u64 key, int n) {
+    int at = 0;
+    for (;;) {
+      const int l = 2 * at + 1;
+      if (l >= n) break;
+      u64 bk = h[l * kKnnThreads];
+      int big = l;
+      if (l + 1 < n) {
+        const u64 rk = h[(l + 1) * kKnnThreads];
+        if (rk > bk) {
+          bk = rk;
+          big = l + 1;
+        }
+      }
+      if (bk <= key) break;
+      h[at * kKnnThreads] = bk;
+      at = big;
+    }
+    h[at * kKnnThreads] = key;
+  }
+};
 
 template <int MODE>
 __global__ void __launch_bounds__(kKnnThreads)
     knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                      const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
-                     const float4* __restrict__ qrec, int64_t m, double p, int k,
-                     float* __restrict__ out, int32_t* __restrict__ nbr_out,
+                     const float4* __restrict__ qrec, const float* __restrict__ data, int64_t m,
+                     double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
                      float* __restrict__ kd2_out) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= m) return;  // no block-wide barrier in this kernel
-  KnnTop tp;
-  tp.d = reinterpret_cast<float*>(knn_smem) + threadIdx.x;
-  tp.pos = reinterpret_cast<int*>(knn_smem) + k * kKnnThreads + threadIdx.x;
+  KnnHeap hp;
+  hp.h = reinterpret_cast<u64*>(knn_smem) + threadIdx.x;
   const GridDev g = *grid;
   const float4 rq = qrec[t];
   const float qx = rq.x, qy = rq.y;
   const int j = __float_as_int(rq.z);
   int best_hit = INT_MAX;
-  float hit_z = 0.f;
 
-  auto consider_run = [&](int yy, int xa, int xb) {
+  auto run = [&](int yy, int xa, int xb) {
     const int a = cell_start(starts, base, yy * g.gx + xa);
     const int b = cell_start(starts, base, yy * g.gx + xb + 1);
     for (int q = a; q < b; ++q) {
       const float4 v = sorted[q];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       const int idx = __float_as_int(v.w);
-      if (d2 == 0.f && v.x == qx && v.y == qy && idx < best_hit) {
-        best_hit = idx;
-        hit_z = v.z;
-      }
-      if (tp.size < k) {
-        tp.d[tp.size * kKnnThreads] = d2;
-        tp.pos[tp.size * kKnnThreads] = q;
-        if (++tp.size == k) knn_rescan(tp, sorted);
-      } else if (d2 < tp.worst_d || (d2 == tp.worst_d && idx < tp.worst_i)) {
-        tp.d[tp.worst_s * kKnnThreads] = d2;
-        tp.pos[tp.worst_s * kKnnThreads] = q;
-        knn_rescan(tp, sorted);
-      }
+      if (d2 == 0.f && v.x == qx && v.y == qy) best_hit = min(best_hit, idx);
+      const u64 key = knn_key(d2, idx);
+      if (hp.size < k)
+        hp.push(key);
+      else if (key < hp.top())
+        hp.replace_top(key, k);
     }
   };
 
   if (finite2(qx, qy)) {
     const float u = cell_pos(qx, g.hx0, g.inv2), v = cell_pos(qy, g.hy0, g.inv2);
     const int cx = clamp_floor(u, 0, g.gx - 1), cy = clamp_floor(v, 0, g.gy - 1);
-    const int r_end = max(max(cx, g.gx - 1 - cx), max(cy, g.gy - 1 - cy));
     const float mg = __fmaf_ru(fabsf(u) + fabsf(v), 0x1p-22f, 0x1p-9f);
     const float ax = fmaxf(0.f, fmaxf(u - float(g.gx), -u) - mg);
     const float ay = fmaxf(0.f, fmaxf(v - float(g.gy), -v) - mg);
     const float hh = g.inv2 > 0.f ? 2.f / g.inv2 : 0.f;
     const float h2 = __fmul_rd(hh, hh) * (1.f - 0x1p-18f);
-    for (int r = 0; r <= r_end; ++r) {
-      if (r == 0) {
-        consider_run(cy, cx, cx);
-      } else {
-        if (cy - r >= 0) consider_run(cy - r, max(0, cx - r), min(g.gx - 1, cx + r));
-        if (cy + r < g.gy) consider_run(cy + r, max(0, cx - r), min(g.gx - 1, cx + r));
-        const int y0 = max(0, cy - r + 1), y1 = min(g.gy - 1, cy + r - 1);
-        for (int yy = y0; yy <= y1; ++yy) {
-          if (cx - r >= 0) consider_run(yy, cx - r, cx - r);
-          if (cx + r < g.gx) consider_run(yy, cx + r, cx + r);
+    run(cy, cx, cx);
+    for (int r = 0;;) {
+      const bool open_l = cx - r > 0, open_r = cx + r < g.gx - 1;
+      const bool open_b = cy - r > 0, open_t = cy + r < g.gy - 1;
+      if (!(open_l || open_r || open_b || open_t)) break;  // the square covers the grid
+      if (hp.size == k) {
+        float l2 = INFINITY;
+        if (open_l) {
+          const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
+          l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
         }
+        if (open_r) {
+          const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
+          l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+        }
+        if (open_b) {
+          const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
+          l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+        }
+        if (open_t) {
+          const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
+          l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+        }
+        if (key_d2(hp.top()) < __fmul_rd(l2, h2) - 0x1p-126f) break;
       }
-      if (tp.size < k) continue;
-      float l2 = INFINITY;
-      if (cx - r > 0) {
-        const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
-        l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+      // The cells between squares r and r2 as row runs: side strips of the
+      // rows already in the square, then new rows below and above.
+      auto band = [&](int r2, auto&& fn) {
+        const int y0 = max(0, cy - r), y1 = min(g.gy - 1, cy + r);
+        const int la = max(0, cx - r2), lb = cx - r - 1;
+        const int ra = cx + r + 1, rb = min(g.gx - 1, cx + r2);
+        for (int yy = y0; yy <= y1; ++yy) {
+          if (la <= lb) fn(yy, la, lb);
+          if (ra <= rb) fn(yy, ra, rb);
+        }
+        const int xa = max(0, cx - r2), xb = min(g.gx - 1, cx + r2);
+        for (int yy = max(0, cy - r2); yy <= min(g.gy - 1, cy - r - 1); ++yy) fn(yy, xa, xb);
+        for (int yy = max(0, cy + r + 1); yy <= min(g.gy - 1, cy + r2); ++yy) fn(yy, xa, xb);
+      };
+      // Grow by max(1, r/2), halved while the band would hold more than 4k
+      // points (a step from empty space into a dense cluster stays short).
+      int r2 = r + max(1, r >> 1);
+      while (r2 > r + 1) {
+        int count = 0;
+        band(r2, [&](int yy, int xa, int xb) {
+          count += cell_start(starts, base, yy * g.gx + xb + 1) -
+                   cell_start(starts, base, yy * g.gx + xa);
+        });
+        if (count <= 4 * k) break;
+        r2 = r + max(1, (r2 - r) >> 1);
       }
-      if (cx + r < g.gx - 1) {
-        const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
-        l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
-      }
-      if (cy - r > 0) {
-        const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
-        l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
-      }
-      if (cy + r < g.gy - 1) {
-        const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
-        l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
-      }
-      // l2 = inf: no grid cell left unsearched (the loop ends anyway).
-      if (tp.worst_d < __fmul_rd(l2, h2) - 0x1p-126f) break;
+      band(r2, run);
+      r = r2;
     }
   }
-  const int size = tp.size;
-  if (size > 0 && size < k) knn_rescan(tp, sorted);
-  if (kd2_out) kd2_out[j] = size > 0 ? tp.worst_d : __int_as_float(0x7fc00000);
+  const int size = hp.size;
+  if (kd2_out) kd2_out[j] = size > 0 ? key_d2(hp.top()) : __int_as_float(0x7fc00000);
+  float zv = __int_as_float(0x7fc00000);  // NaN: nothing selected
+  if (best_hit != INT_MAX) {
+    zv = data[3 * int64_t(best_hit) + 2];
+  } else if (size > 0) {
+    const float hpw = static_cast<float>(0.5 * p), nhp = -hpw;
+    u64 hi = 0, lo = 0;
+    for (int s = 0; s < size; ++s) {
+      const u64 key = hp.h[s * kKnnThreads];
+      const float w = local_weight<MODE>(key_d2(key), hpw, nhp);
+      two_sum_acc(hi, lo, pk(w, __fmul_rn(w, data[3 * int64_t(key_index(key)) + 2])));
+    }
+    float h0, h1, l0, l1;
+    upk(hi, h0, h1);
+    upk(lo, l0, l1);
+    if (h0 >= kTinyPerMember * float(size) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
+        fabsf(l1) <= FLT_MAX) {
+      const float z0 = __fdiv_rn(h1, h0);
+      const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
+      zv = __fmaf_rn(res, rcp_approx(h0), z0);
+    } else {
+      // Outside FP32's range: FP64 over the selected points, scaled by
+      // d2_min^(p/2).
+      double dmin = INFINITY;
+      for (int s = 0; s < size; ++s) {
+        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
+        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+        dmin = fmin(dmin, ex * ex + ey * ey);
+      }
+      double s0 = 0.0, s1 = 0.0;
+      for (int s = 0; s < size; ++s) {
+        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
+        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+        const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+        s0 += w;
+        s1 += w * double(x[2]);
+      }
+      zv = static_cast<float>(s1 / s0);
+    }
+  }
+  out[j] = zv;
   if (nbr_out) {
-    // Insertion sort of the slots by key, then the data indices in order.
-    for (int s = 1; s < size; ++s) {
-      const float d = tp.d[s * kKnnThreads];
-      const int ps = tp.pos[s * kKnnThreads];
-      int at = s;
-      while (at > 0) {
-        const float dp = tp.d[(at - 1) * kKnnThreads];
-        const int pp = tp.pos[(at - 1) * kKnnThreads];
-        const bool later = dp > d || (dp == d && data_index(sorted, pp) > data_index(sorted, ps));
-        if (!later) break;
-        tp.d[at * kKnnThreads] = dp;
-        tp.pos[at * kKnnThreads] = pp;
-        --at;
-      }
-      tp.d[at * kKnnThreads] = d;
-      tp.pos[at * kKnnThreads] = ps;
-    }
+    // Heap sort: the largest remaining key goes to the end of the row.
     int32_t* row = nbr_out + int64_t(j) * k;
-    for (int s = 0; s < k; ++s) row[s] = s < size ? data_index(sorted, tp.pos[s * kKnnThreads]) : -1;
+    for (int s = size; s < k; ++s) row[s] = -1;
+    for (int n = size; n > 0; --n) {
+      const u64 top = hp.top();
+      row[n - 1] = key_index(top);
+      const u64 last = hp.h[(n - 1) * kKnnThreads];
+      if (n > 1) hp.replace_top(last, n - 1);
+    }
   }
-  if (best_hit != INT_MAX || size == 0) {
-    out[j] = best_hit != INT_MAX ? hit_z : __int_as_float(0x7fc00000);
-    return;
-  }
-  const float hp = static_cast<float>(0.5 * p), nhp = -hp;
-  u64 hi = 0, lo = 0;
-  for (int s = 0; s < size; ++s) {
-    const float w = local_weight<MODE>(tp.d[s * kKnnThreads], hp, nhp);
-    two_sum_acc(hi, lo, pk(w, __fmul_rn(w, sorted[tp.pos[s * kKnnThreads]].z)));
-  }
-  float h0, h1, l0, l1;
-  upk(hi, h0, h1);
-  upk(lo, l0, l1);
-  if (h0 >= kTinyPerMember * float(size) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
-      fabsf(l1) <= FLT_MAX) {
-    const float z0 = __fdiv_rn(h1, h0);
-    const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
-    out[j] = __fmaf_rn(res, rcp_approx(h0), z0);
-    return;
-  }
-  // Outside FP32's range: FP64 over the selected points, scaled by d2_min^(p/2).
-  double dmin = INFINITY;
-  for (int s = 0; s < size; ++s) {
-    const float4 v = sorted[tp.pos[s * kKnnThreads]];
-    const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-    dmin = fmin(dmin, ex * ex + ey * ey);
-  }
-  double s0 = 0.0, s1 = 0.0;
-  for (int s = 0; s < size; ++s) {
-    const float4 v = sorted[tp.pos[s * kKnnThreads]];
-    const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-    const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
-    s0 += w;
-    s1 += w * double(v.z);
-  }
-  out[j] = static_cast<float>(s1 / s0);
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -806,7 +823,7 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   return cudaGetLastError();
 }
 
-size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * 8; }
+size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
 
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
@@ -828,11 +845,11 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
-    knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(grid, sorted, starts_d, sums, qrec,
-                                                              m, p, k, out, nbr_out, kd2_out);
+    knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
+        grid, sorted, starts_d, sums, qrec, data, m, p, k, out, nbr_out, kd2_out);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, qrec, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, qrec, data, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 
