@@ -539,7 +539,9 @@ __device__ __forceinline__ u64 knn_key(float d2, int idx) {
 __device__ __forceinline__ float key_d2(u64 key) { return __uint_as_float(unsigned(key >> 32)); }
 __device__ __forceinline__ int key_index(u64 key) { return int(unsigned(key)); }
 
-// Max-heap of this thread's keys: slot s at h[s * kKnnThreads] (conflict-free).
+// 4-ary max-heap of this thread's keys: slot s at h[s * kKnnThreads]
+// (conflict-free); the children of slot a are 4a + 1 .. 4a + 4, so a sift
+// is at most 3 levels deep for k <= 64 and each level's loads issue together.
 struct KnnHeap {
   u64* h;
   int size = 0;
@@ -548,7 +550,7 @@ struct KnnHeap {
   __device__ __forceinline__ void push(u64 key) {
     int at = size++;
     while (at > 0) {
-      const int parent = (at - 1) >> 1;
+      const int parent = (at - 1) >> 2;
       const u64 pk = h[parent * kKnnThreads];
       if (pk >= key) break;
       h[at * kKnnThreads] = pk;
@@ -560,15 +562,18 @@ struct KnnHeap {
   __device__ __forceinline__ void replace_top(u64 key, int n) {
     int at = 0;
     for (;;) {
-      const int l = 2 * at + 1;
-      if (l >= n) break;
-      u64 bk = h[l * kKnnThreads];
-      int big = l;
-      if (l + 1 < n) {
-        const u64 rk = h[(l + 1) * kKnnThreads];
-        if (rk > bk) {
-          bk = rk;
-          big = l + 1;
+      const int c0 = 4 * at + 1;
+      if (c0 >= n) break;
+      u64 bk = h[c0 * kKnnThreads];
+      int big = c0;
+#pragma unroll
+      for (int c = 1; c < 4; ++c) {
+        if (c0 + c < n) {
+          const u64 ck = h[(c0 + c) * kKnnThreads];
+          if (ck > bk) {
+            bk = ck;
+            big = c0 + c;
+          }
         }
       }
       if (bk <= key) break;
@@ -596,6 +601,7 @@ __global__ void __launch_bounds__(kKnnThreads)
   const float qx = rq.x, qy = rq.y;
   const int j = __float_as_int(rq.z);
   int best_hit = INT_MAX;
+  u64 worst = ~u64(0);  // the heap's largest key once it holds k, else above every key
 
   auto run = [&](int yy, int xa, int xb) {
     const int a = cell_start(starts, base, yy * g.gx + xa);
@@ -606,10 +612,15 @@ __global__ void __launch_bounds__(kKnnThreads)
       const int idx = __float_as_int(v.w);
       if (d2 == 0.f && v.x == qx && v.y == qy) best_hit = min(best_hit, idx);
       const u64 key = knn_key(d2, idx);
-      if (hp.size < k)
-        hp.push(key);
-      else if (key < hp.top())
-        hp.replace_top(key, k);
+      if (key < worst) {  // worst stays ~0 (all ones) until the heap is full
+        if (hp.size < k) {
+          hp.push(key);
+          if (hp.size == k) worst = hp.top();
+        } else {
+          hp.replace_top(key, k);
+          worst = hp.top();
+        }
+      }
     }
   };
 
@@ -644,7 +655,7 @@ __global__ void __launch_bounds__(kKnnThreads)
           const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
           l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
         }
-        if (key_d2(hp.top()) < __fmul_rd(l2, h2) - 0x1p-126f) break;
+        if (key_d2(worst) < __fmul_rd(l2, h2) - 0x1p-126f) break;
       }
       // The cells between squares r and r2 as row runs: side strips of the
       // rows already in the square, then new rows below and above.
