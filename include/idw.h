@@ -50,7 +50,7 @@ typedef enum {
     IDW_ERR_INVALID_ARG = 1,   /* null pointer, bad size, p <= 0 or non-finite p */
     IDW_ERR_ALIGNMENT = 2,     /* a pointer lacks the element alignment */
     IDW_ERR_CUDA = 3,          /* a CUDA runtime call failed (see idw_last_cuda_error) */
-    IDW_ERR_NOT_FINITE_INPUT = 4,
+    IDW_ERR_NOT_FINITE_INPUT = 4, /* NaN / inf input found (only with IDW_OPT_VALIDATE_INPUTS) */
     IDW_ERR_WORKSPACE = 5,     /* device workspace could not be allocated */
     IDW_ERR_UNSUPPORTED = 6,   /* device is not sm_103 or option not supported */
     IDW_ERR_DEVICE_TIMEOUT = 7 /* a bounded wait inside a kernel gave up */
@@ -73,6 +73,14 @@ const char *idw_status_string(idw_status s);
  * call).  Fails with IDW_ERR_UNSUPPORTED if the device is not compute
  * capability 10.3. */
 idw_status idw_create(idw_handle_t *handle, int device);
+
+/*
+ * As idw_create, with the autotuner's JSON cache file given directly
+ * (NULL: as idw_create, i.e. the IDW_AUTOTUNE_CACHE environment variable or
+ * memory only).  The file is read now if it exists and rewritten after each
+ * tuning; a missing or unreadable file starts an empty table.
+ */
+idw_status idw_create_ex(idw_handle_t *handle, int device, const char *autotune_cache);
 
 /* Frees the handle and its workspace after synchronising the device. */
 idw_status idw_destroy(idw_handle_t handle);
@@ -211,6 +219,17 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *       Layouts 1 and 2 build the register pairs with moves.  A forced
  *       layout applies to single FP32 problems with sweep variant 0 (the
  *       layout ablation) and is ignored otherwise.
+ *   IDW_OPT_VALIDATE_INPUTS     0/1 (default 0).  When 1, every call that
+ *                               takes this handle first scans its data,
+ *                               queries (and, for idw_backward, grad_out) for
+ *                               NaN or infinite values and returns
+ *                               IDW_ERR_NOT_FINITE_INPUT, computing nothing,
+ *                               if it finds any.  The scan's verdict is read
+ *                               back, so a validating call synchronises its
+ *                               stream and returns IDW_ERR_UNSUPPORTED while
+ *                               the stream is being captured.  Off, inputs are
+ *                               not scanned and NaN propagates (Eq. 1 is
+ *                               evaluated as given).
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -221,7 +240,8 @@ typedef enum {
     IDW_OPT_FORCE_GENERAL_POWER = 3,
     IDW_OPT_LAST_VARIANT = 4,
     IDW_OPT_TUNED_CLASSES = 5,
-    IDW_OPT_STAGING_LAYOUT = 6
+    IDW_OPT_STAGING_LAYOUT = 6,
+    IDW_OPT_VALIDATE_INPUTS = 7
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

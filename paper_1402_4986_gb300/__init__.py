@@ -11,6 +11,7 @@ and autograd plumbing.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import torch
@@ -33,11 +34,15 @@ _DTYPE = {PREC_F32_COMP: torch.float32, PREC_F64_PLAIN: torch.float64}
 class Handle:
     """Owns one ``idw_handle_t`` (and its device workspace) on one device."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, autotune_cache: str | None = None):
         self.lib = _lib.load()
         self.device = int(device)
         h = ctypes.c_void_p()
-        _lib.check(self.lib.idw_create(ctypes.byref(h), self.device), "idw_create")
+        if autotune_cache is None:
+            _lib.check(self.lib.idw_create(ctypes.byref(h), self.device), "idw_create")
+        else:
+            _lib.check(self.lib.idw_create_ex(ctypes.byref(h), self.device,
+                                              os.fsencode(autotune_cache)), "idw_create_ex")
         self.ptr = h
 
     def close(self):

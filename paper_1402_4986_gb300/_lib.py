@@ -34,7 +34,7 @@ PREC_F64_PLAIN = 1
 PAPER_KERNELS = {"naive": 0, "tiled": 1}
 PAPER_LAYOUTS = {"soa": 0, "aos": 1, "aoas": 2, "hybrid": 3}
 OPTIONS = {"autotune": 1, "sweep_variant": 2, "force_general_power": 3, "last_variant": 4,
-           "tuned_classes": 5, "staging_layout": 6}
+           "tuned_classes": 5, "staging_layout": 6, "validate_inputs": 7}
 
 
 class PlanInfo(ctypes.Structure):
@@ -87,6 +87,7 @@ SIGNATURES = {
                                         c_void_p]),
     "idw_interpolate_local": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                       c_double, c_void_p, c_void_p, c_void_p]),
+    "idw_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.c_char_p]),
     "idw_interpolate_knn": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
 }

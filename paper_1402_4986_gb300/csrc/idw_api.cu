@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <fstream>
+#include <initializer_list>
 #include <map>
 #include <sstream>
 #include <string>
@@ -31,6 +32,8 @@ struct idw_handle_s {
   int occ_f32[2][idw::kNumSweepVariants] = {};  // [general p][variant]
   // Options (idw_set_option).
   int opt_autotune = 0, opt_variant = -1, opt_force_general = 0, opt_layout = -1;
+  int opt_validate = 0;         // scan inputs for NaN / inf before computing
+  unsigned* vflag = nullptr;    // device word the scan sets
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
   std::string tune_path;             // JSON cache file ("" = memory only)
@@ -275,6 +278,57 @@ int choose_variant_unresolved(idw_handle_t h, const idw::F32Problem* probs, int 
   return best;
 }
 
+// Sets *flag when any of the count values is NaN or infinite.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    nonfinite_scan_kernel(const T* __restrict__ a, int64_t count, unsigned* __restrict__ flag) {
+  bool bad = false;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+       i += int64_t(gridDim.x) * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+struct Span {
+  const void* ptr;
+  int64_t count;  // values
+  bool fp64;
+};
+
+// With IDW_OPT_VALIDATE_INPUTS set: scans every span and returns
+// IDW_ERR_NOT_FINITE_INPUT if any value is NaN or infinite.  Reads the
+// verdict back, so it synchronises the stream and refuses a capture.
+idw_status validate_inputs(idw_handle_t h, std::initializer_list<Span> spans, cudaStream_t s) {
+  if (!h->opt_validate) return IDW_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  if (cap != cudaStreamCaptureStatusNone) return IDW_ERR_UNSUPPORTED;
+  if (!h->vflag && (e = cudaMalloc(&h->vflag, sizeof(unsigned))) != cudaSuccess) {
+    h->vflag = nullptr;
+    return cuda_fail(h, e);
+  }
+  if ((e = cudaMemsetAsync(h->vflag, 0, sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_fail(h, e);
+  for (const Span& sp : spans) {
+    if (!sp.ptr || sp.count <= 0) continue;
+    const unsigned grid = static_cast<unsigned>(
+        std::max<int64_t>(1, std::min<int64_t>(int64_t(h->sm_count) * 4, (sp.count + 255) / 256)));
+    if (sp.fp64)
+      nonfinite_scan_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double*>(sp.ptr),
+                                                          sp.count, h->vflag);
+    else
+      nonfinite_scan_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(sp.ptr),
+                                                         sp.count, h->vflag);
+  }
+  unsigned flag = 0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, h->vflag, sizeof(flag), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return flag ? IDW_ERR_NOT_FINITE_INPUT : IDW_OK;
+}
+
 idw_status check_common(idw_handle_t h, const void* data, int64_t n, const void* queries,
                         int64_t m, double p, idw_precision prec, const void* out) {
   if (!h) return IDW_ERR_INVALID_ARG;
@@ -335,6 +389,15 @@ idw_status idw_create(idw_handle_t* out, int device) {
   return IDW_OK;
 }
 
+idw_status idw_create_ex(idw_handle_t* out, int device, const char* autotune_cache) {
+  idw_status st = idw_create(out, device);
+  if (st != IDW_OK || !autotune_cache) return st;
+  (*out)->tune_path = autotune_cache;  // overrides IDW_AUTOTUNE_CACHE
+  (*out)->tuned.clear();
+  load_tuning(*out);
+  return IDW_OK;
+}
+
 idw_status idw_destroy(idw_handle_t h) {
   if (!h) return IDW_ERR_INVALID_ARG;
   DeviceGuard guard(h->device);
@@ -342,6 +405,7 @@ idw_status idw_destroy(idw_handle_t h) {
   if (h->ws) cudaFree(h->ws);
   if (h->io) cudaFree(h->io);
   if (h->ctrl) cudaFree(h->ctrl);
+  if (h->vflag) cudaFree(h->vflag);
   destroy_events(h);
   delete h;
   return IDW_OK;
@@ -358,6 +422,9 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool f64 = prec == IDW_PREC_F64_PLAIN;
+  st = validate_inputs(h, {{data, 3 * n, f64}, {queries, 2 * m, f64}}, s);
+  if (st != IDW_OK) return st;
   cudaError_t e;
   if (prec == IDW_PREC_F32_COMP) {
     idw::F32Problem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m,
@@ -438,6 +505,10 @@ idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* co
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (const idw::F32Problem& pb : probs) {
+    const idw_status vs = validate_inputs(h, {{pb.data, 3 * pb.n, false}, {pb.queries, 2 * pb.m, false}}, s);
+    if (vs != IDW_OK) return vs;
+  }
   std::vector<idw::BatchPlan> plans;
   size_t need = 0;
   for (size_t b = 0; b < probs.size(); b += idw::kBatchCap) {
@@ -482,6 +553,9 @@ idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const floa
     return IDW_ERR_ALIGNMENT;
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
+  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}, {grad_out, m, false}},
+                       static_cast<cudaStream_t>(stream));
+  if (st != IDW_OK) return st;
   if (!h->occ_bwd) h->occ_bwd = idw::occupancy_backward_f32();
   idw::BwdPlan bp;
   idw::plan_backward_f32(n, m, h->sm_count, h->occ_bwd, &bp);
@@ -504,6 +578,9 @@ idw_status idw_paper_interpolate(idw_handle_t h, idw_paper_kernel kernel, idw_pa
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
   const bool fp64 = prec == IDW_PREC_F64_PLAIN;
+  st = validate_inputs(h, {{data, 3 * n, fp64}, {queries, 2 * m, fp64}},
+                       static_cast<cudaStream_t>(stream));
+  if (st != IDW_OK) return st;
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, idw::paper_layout_bytes(n, fp64));
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_paper_kernel(kernel, layout, fp64, data, n, queries, m, p, out,
@@ -521,6 +598,9 @@ idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
   if (count_out && !aligned(count_out, 4)) return IDW_ERR_ALIGNMENT;
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
+  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}},
+                       static_cast<cudaStream_t>(stream));
+  if (st != IDW_OK) return st;
   const int64_t max_cells = idw::local_max_cells(n);
   const idw::LocalLayout L = idw::local_layout(n, m, max_cells);
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
@@ -541,6 +621,9 @@ idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, con
     return IDW_ERR_ALIGNMENT;
   DeviceGuard guard(h->device);
   if (!guard.ok) return IDW_ERR_CUDA;
+  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}},
+                       static_cast<cudaStream_t>(stream));
+  if (st != IDW_OK) return st;
   const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
   if (st != IDW_OK) return st;
@@ -583,6 +666,9 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
       if (value < -1 || value > 2) return IDW_ERR_INVALID_ARG;
       h->opt_layout = static_cast<int>(value);
       return IDW_OK;
+    case IDW_OPT_VALIDATE_INPUTS:
+      h->opt_validate = value != 0;
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -597,6 +683,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_LAST_VARIANT: *value = h->last_variant; return IDW_OK;
     case IDW_OPT_TUNED_CLASSES: *value = static_cast<int64_t>(h->tuned.size()); return IDW_OK;
     case IDW_OPT_STAGING_LAYOUT: *value = h->opt_layout; return IDW_OK;
+    case IDW_OPT_VALIDATE_INPUTS: *value = h->opt_validate; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

@@ -1,0 +1,111 @@
+"""Input validation (IDW_OPT_VALIDATE_INPUTS) and the autotune cache given
+at handle creation (idw_create_ex).
+
+With validation on, every entry point scans its inputs first and refuses
+NaN or infinite values with IDW_ERR_NOT_FINITE_INPUT, computing nothing;
+clean inputs give the same results as without validation.
+"""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def idw():
+    from paper_1402_4986_gb300 import build
+    build.build()
+    import paper_1402_4986_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+@pytest.fixture()
+def vh(idw):
+    h = idw.Handle(torch.cuda.current_device())
+    idw.set_option("validate_inputs", 1, handle=h)
+    yield h
+    h.close()
+
+
+def _prob(seed=71, n=3000, m=700):
+    p = synthetic.uniform_problem(n, m, seed=seed)
+    return torch.from_numpy(p["data"]).cuda(), torch.from_numpy(p["queries"]).cuda()
+
+
+def _expect_not_finite(idw, fn):
+    with pytest.raises(idw.IDWError) as e:
+        fn()
+    assert e.value.name == "IDW_ERR_NOT_FINITE_INPUT"
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), float("-inf")])
+def test_every_entry_point_refuses_non_finite_inputs(idw, vh, bad):
+    d, q = _prob()
+    dbad = d.clone()
+    dbad[1234, 2] = bad          # a value
+    qbad = q.clone()
+    qbad[321, 0] = bad           # a query coordinate
+    assert idw.get_option("validate_inputs", handle=vh) == 1
+    for dd, qq in ((dbad, q), (d, qbad)):
+        _expect_not_finite(idw, lambda: idw.interpolate(dd, qq, 2.0, handle=vh))
+        _expect_not_finite(idw, lambda: idw.interpolate(dd.double(), qq.double(), 2.0, "f64",
+                                                        handle=vh))
+        _expect_not_finite(idw, lambda: idw.interpolate_local(dd, qq, 2.0, 0.05, handle=vh))
+        _expect_not_finite(idw, lambda: idw.interpolate_knn(dd, qq, 2.0, 8, handle=vh))
+        _expect_not_finite(idw, lambda: idw.paper_interpolate(dd, qq, 2.0, handle=vh))
+        _expect_not_finite(idw, lambda: idw.interpolate_batched([d, dd], [q, qq], 2.0, handle=vh))
+    Z, s0, hit = idw.interpolate_saved(d, q, 2.0, handle=vh)
+    g = torch.ones(q.shape[0], device="cuda")
+    g[7] = bad
+    _expect_not_finite(idw, lambda: idw.backward(d, q, 2.0, Z, s0, hit, g, handle=vh))
+
+
+def test_clean_inputs_give_the_same_results(idw, vh):
+    d, q = _prob(seed=72)
+    plain = idw.Handle(torch.cuda.current_device())
+    for fn in (lambda h: idw.interpolate(d, q, 2.0, handle=h),
+               lambda h: idw.interpolate_local(d, q, 2.0, 0.05, handle=h),
+               lambda h: idw.interpolate_knn(d, q, 2.0, 8, handle=h)):
+        a = fn(vh).cpu().numpy()
+        b = fn(plain).cpu().numpy()
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        ok = ~np.isnan(a)
+        assert np.all(np.abs(a[ok] - b[ok]) <= np.spacing(np.abs(b[ok])))
+    plain.close()
+
+
+def test_validation_refuses_stream_capture(idw, vh):
+    d, q = _prob(seed=73)
+    out = torch.empty(q.shape[0], device="cuda")
+    idw.interpolate(d, q, 2.0, out=out, handle=vh)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(idw.IDWError, match="UNSUPPORTED"):
+        with torch.cuda.graph(g):
+            idw.interpolate(d, q, 2.0, out=out, handle=vh)
+    torch.cuda.synchronize()
+    idw.set_option("validate_inputs", 0, handle=vh)
+    assert idw.get_option("validate_inputs", handle=vh) == 0
+
+
+def test_autotune_cache_given_at_creation(idw, tmp_path):
+    path = str(tmp_path / "tune.json")
+    d, q = _prob(seed=74, n=20000, m=20000)
+    h = idw.Handle(torch.cuda.current_device(), autotune_cache=path)
+    idw.set_option("autotune", 1, handle=h)
+    idw.interpolate(d, q, 2.0, handle=h)
+    torch.cuda.synchronize()
+    assert idw.get_option("tuned_classes", handle=h) >= 1
+    h.close()
+    with open(path) as f:
+        table = json.load(f)
+    assert len(table) >= 1
+    h2 = idw.Handle(torch.cuda.current_device(), autotune_cache=path)
+    assert idw.get_option("tuned_classes", handle=h2) == len(table)
+    h2.close()
