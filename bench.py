@@ -596,8 +596,27 @@ def run_layout(args):
                 rows.append({"n": n, "m": n, "p": p, "layout": layout, "layout_name": names[layout],
                              "pairs_s": float(n) * n / (ms / 1e3), "call_ms": ms,
                              "sweep_ms": sweep_ms})
+    # The plain FP64 form in the paper's FP64 layouts (Sec. 3.5, 4.1.2).
+    f64_names = {-1: "Hybrid (x,y) pairs + z[], 24 B/point", 1: "AoaS (x,y,z,pad), 32 B/point",
+                 2: "SoA x[],y[],z[], 24 B/point"}
+    for n in (100_000, 1 << 20):
+        prob = synthetic.config_scale(n)
+        d = torch.from_numpy(prob["data"]).cuda().double()
+        m = min(n, 65536)
+        q = torch.from_numpy(prob["queries"][:m]).cuda().double()
+        out = torch.empty(m, device="cuda", dtype=torch.float64)
+        for p in (2.0, 3.5):
+            for layout in (-1, 1, 2):
+                h = idw.Handle(torch.cuda.current_device())
+                idw.set_option("staging_layout", layout, handle=h)
+                ms = _events_ms(lambda: idw.interpolate(d, q, p, "f64", out=out, handle=h), 2)
+                h.close()
+                rows.append({"n": n, "m": m, "p": p, "precision": "f64", "layout": layout,
+                             "layout_name": f64_names[layout],
+                             "pairs_s": float(n) * m / (ms / 1e3), "call_ms": ms})
     _emit("staging-layout ablation: same sweep (variant 0) on data tiles staged as duplicated "
-          "pairs, aligned AoS or SoA; N=M, uniform [0,1)^2, wave field", rows)
+          "pairs, aligned AoS or SoA; N=M, uniform [0,1)^2, wave field; then the plain FP64 "
+          "form staged as Hybrid, AoaS or SoA (M = min(N, 65536))", rows)
 
 
 def run_paper(args):

@@ -218,7 +218,11 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *       16 B/point (Sec. 3.3); 2 SoA arrays x, y, z, 12 B/point (Sec. 2.2).
  *       Layouts 1 and 2 build the register pairs with moves.  A forced
  *       layout applies to single FP32 problems with sweep variant 0 (the
- *       layout ablation) and is ignored otherwise.
+ *       layout ablation) and is ignored otherwise.  For IDW_PREC_F64_PLAIN
+ *       it selects that form's staging: -1 or 0 the paper's Hybrid layout
+ *       ((x,y) pairs beside z, 24 B/point, Sec. 3.5; the default), 1 aligned
+ *       (x,y,z,pad) records (32 B/point), 2 SoA (24 B/point); the results
+ *       are bit-identical in every layout.
  *   IDW_OPT_VALIDATE_INPUTS     0/1 (default 0).  When 1, every call that
  *                               takes this handle first scans its data,
  *                               queries (and, for idw_backward, grad_out) for

@@ -18,6 +18,7 @@
 #include "idw.h"
 #include "idw_device.cuh"
 #include "idw_internal.h"
+#include "idw_f64_layout.h"
 #include "idw_local.h"
 
 struct idw_handle_s {
@@ -29,6 +30,7 @@ struct idw_handle_s {
   size_t io_bytes = 0;
   idw::Control* ctrl = nullptr;  // device control words
   int occ_f64 = 0, occ_bwd = 0;
+  int occ_f64_layout[3] = {};  // plain FP64 form per staging layout
   int occ_f32[2][idw::kNumSweepVariants] = {};  // [general p][variant]
   // Options (idw_set_option).
   int opt_autotune = 0, opt_variant = -1, opt_force_general = 0, opt_layout = -1;
@@ -439,13 +441,22 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
     h->last_variant = v;
     e = idw::launch_batch_f32(&pb, bp, p, h->ws, h->ctrl, h->sm_count, next_events(h), s);
   } else {
+    // Staging layout of the FP64 form: 1 = AoaS, 2 = SoA, otherwise Hybrid.
+    const int layout = h->opt_layout >= 1 ? h->opt_layout : idw::kF64Hybrid;
+    int& occ = h->occ_f64_layout[layout];
+    if (!occ) occ = idw::occupancy_forward_f64_layout(layout);
     Plan plan;
-    make_plan(h->sm_count, ctas_per_sm(h, prec, p), n, m, prec, &plan);
+    make_plan(h->sm_count, occ, n, m, prec, &plan);
+    // make_plan sizes Hybrid tiles; the AoaS records are wider.
+    plan.workspace_bytes -= plan.staged_bytes;
+    plan.staged_bytes = round_up(size_t(plan.data_tiles) * idw::f64_tile_bytes(layout), 256);
+    plan.workspace_bytes += plan.staged_bytes;
     st = ensure_buffer(h, &h->ws, &h->ws_bytes, plan.workspace_bytes);
     if (st != IDW_OK) return st;
     idw::F64Problem pb{static_cast<const double*>(data), n, static_cast<const double*>(queries), m,
                        p, static_cast<double*>(out), s0_out, hit_out};
-    e = idw::launch_forward_f64(pb, plan, h->ws, h->ctrl, h->sm_count, next_events(h), s);
+    e = idw::launch_forward_f64_layout(pb, plan, layout, h->ws, h->ctrl, h->sm_count,
+                                       next_events(h), s);
   }
   if (e != cudaSuccess) return cuda_fail(h, e);
   return IDW_OK;

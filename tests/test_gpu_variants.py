@@ -94,6 +94,27 @@ def test_option_errors(idw):
     h.close()
 
 
+@pytest.mark.parametrize("p", [2.0, 3.5])
+def test_fp64_staging_layouts_are_bit_identical(idw, p):
+    """The plain FP64 form staged as Hybrid (default), AoaS double4 records
+    or SoA: the same arithmetic in the same order, so bit-identical results,
+    each within 1e-13 of the oracle (the paper's FP64 layout question,
+    Sec. 4.1.2, asked of this library's sweep)."""
+    prob = synthetic.config_exact_hits(seed=77, n=5003, m=2051, hits=5)
+    d = torch.from_numpy(prob["data"]).cuda().double()
+    q = torch.from_numpy(prob["queries"]).cuda().double()
+    Z64, _ = oracle.idw(prob["data"], prob["queries"], p)
+    outs = []
+    for layout in (-1, 1, 2):
+        h = idw.Handle(0)
+        idw.set_option("staging_layout", layout, handle=h)
+        Z = idw.interpolate(d, q, p, "f64", handle=h).cpu().numpy()
+        h.close()
+        assert np.max(np.abs(Z - Z64)) / np.max(np.abs(prob["data"][:, 2])) <= 1e-13, layout
+        outs.append(Z)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
 @pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("p", [2.0, 3.5])
 def test_each_staging_layout_matches_oracle(idw, layout, p):
