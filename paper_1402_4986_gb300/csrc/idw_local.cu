@@ -57,6 +57,8 @@ constexpr int kScanBlock = 1024;            // threads of a scan block
 constexpr int kScanTile = 4 * kScanBlock;  // entries of a scan tile (an int4 per thread)
 constexpr int kLocalThreads = 256;
 constexpr int kMaxCellsPerAxis = 2048;
+constexpr int kBlockShift = 3;  // occupancy blocks of 8 x 8 cells (k-NN search)
+constexpr int kMaxBlocksPerAxis = kMaxCellsPerAxis >> kBlockShift;
 // A compensated weight sum below this per member may have lost flushed
 // (FTZ) weights: such queries are redone in FP64.
 constexpr float kTinyPerMember = 0x1p-100f;
@@ -332,6 +334,43 @@ __device__ __forceinline__ int cell_start(const int32_t* __restrict__ starts,
   return starts[i] + base[i / kScanTile];
 }
 
+// Occupancy of 8 x 8-cell blocks for the k-NN search: for block row by,
+// bpre[by * (kMaxBlocksPerAxis + 1) + bx] is the number of data points in
+// blocks 0 .. bx - 1 of that row.  One CTA per block row, one thread per
+// block; runs after the scan (cell starts are final).
+__global__ void __launch_bounds__(kMaxBlocksPerAxis)
+    block_prefix_kernel(const GridDev* __restrict__ grid, const int32_t* __restrict__ starts,
+                        const int32_t* __restrict__ base, int32_t* __restrict__ bpre) {
+  __shared__ int32_t warp_tot[kMaxBlocksPerAxis / 32];
+  const GridDev g = *grid;
+  const int bgx = (g.gx + 7) >> kBlockShift, bgy = (g.gy + 7) >> kBlockShift;
+  const int by = blockIdx.x;
+  if (by >= bgy) return;
+  const int bx = threadIdx.x;
+  int32_t c = 0;
+  if (bx < bgx) {
+    const int x0 = bx << kBlockShift, x1 = min(g.gx - 1, x0 + 7);
+    const int y0 = by << kBlockShift, y1 = min(g.gy - 1, y0 + 7);
+    for (int yy = y0; yy <= y1; ++yy)
+      c += cell_start(starts, base, yy * g.gx + x1 + 1) - cell_start(starts, base, yy * g.gx + x0);
+  }
+  // Exclusive scan over the row's blocks (kMaxBlocksPerAxis threads).
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_tot[wid] = incl;
+  __syncthreads();
+  int32_t before = incl - c;
+  for (int w = 0; w < wid; ++w) before += warp_tot[w];
+  int32_t* row = bpre + by * (kMaxBlocksPerAxis + 1);
+  if (bx < bgx) row[bx] = before;
+  if (bx == bgx - 1) row[bgx] = before + c;  // the row total
+}
+
 // Threads [0, n) place data points as (x, y, z, index), [n, n + m) place
 // queries as (x, y, index, 0).
 __global__ void __launch_bounds__(256)
@@ -588,7 +627,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kKnnThreads)
     knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                      const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
-                     const float4* __restrict__ qrec, const float* __restrict__ data, int64_t m,
+                     const int32_t* __restrict__ bpre, const float4* __restrict__ qrec,
+                     const float* __restrict__ data, int64_t m,
                      double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
                      float* __restrict__ kd2_out) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
@@ -657,19 +697,31 @@ __global__ void __launch_bounds__(kKnnThreads)
         }
         if (key_d2(worst) < __fmul_rd(l2, h2) - 0x1p-126f) break;
       }
-      // The cells between squares r and r2 as row runs: side strips of the
-      // rows already in the square, then new rows below and above.
+      // Rows ya..yb over columns xa..xb as row runs; once the square is 8
+      // cells out, each stretch of 8 rows whose occupancy blocks over those
+      // columns hold no point is skipped.
+      auto rows = [&](int ya, int yb, int xa, int xb, auto&& fn) {
+        if (xa > xb || ya > yb) return;  // then 0 <= ya <= yb < gy, 0 <= xa <= xb < gx
+        if (r < 8) {  // near the query the blocks are rarely empty: skip no checks
+          for (int yy = ya; yy <= yb; ++yy) fn(yy, xa, xb);
+          return;
+        }
+        for (int by = ya >> kBlockShift; by <= (yb >> kBlockShift); ++by) {
+          const int32_t* bp = bpre + by * (kMaxBlocksPerAxis + 1);
+          if (bp[(xb >> kBlockShift) + 1] == bp[xa >> kBlockShift]) continue;
+          const int y1 = min(yb, (by << kBlockShift) + 7);
+          for (int yy = max(ya, by << kBlockShift); yy <= y1; ++yy) fn(yy, xa, xb);
+        }
+      };
+      // The cells between squares r and r2: side strips of the rows already
+      // in the square, then new rows below and above.
       auto band = [&](int r2, auto&& fn) {
         const int y0 = max(0, cy - r), y1 = min(g.gy - 1, cy + r);
-        const int la = max(0, cx - r2), lb = cx - r - 1;
-        const int ra = cx + r + 1, rb = min(g.gx - 1, cx + r2);
-        for (int yy = y0; yy <= y1; ++yy) {
-          if (la <= lb) fn(yy, la, lb);
-          if (ra <= rb) fn(yy, ra, rb);
-        }
+        rows(y0, y1, max(0, cx - r2), cx - r - 1, fn);
+        rows(y0, y1, cx + r + 1, min(g.gx - 1, cx + r2), fn);
         const int xa = max(0, cx - r2), xb = min(g.gx - 1, cx + r2);
-        for (int yy = max(0, cy - r2); yy <= min(g.gy - 1, cy - r - 1); ++yy) fn(yy, xa, xb);
-        for (int yy = max(0, cy + r + 1); yy <= min(g.gy - 1, cy + r2); ++yy) fn(yy, xa, xb);
+        rows(max(0, cy - r2), min(g.gy - 1, cy - r - 1), xa, xb, fn);
+        rows(max(0, cy + r + 1), min(g.gy - 1, cy + r2), xa, xb, fn);
       };
       // Grow by max(1, r/2), halved while the band would hold more than 4k
       // points (a step from empty space into a dense cluster stays short).
@@ -770,6 +822,8 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells) {
   L.off_sums = off;       off += round_up(size_t(2 * scan_tiles_of(max_cells)) * 4, 256);
   L.off_sorted = off;     off += round_up(size_t(n) * 16, 256);
   L.off_qrec = off;       off += round_up(size_t(m) * 16, 256);
+  L.off_bpre = off;
+  off += round_up(size_t(kMaxBlocksPerAxis) * (kMaxBlocksPerAxis + 1) * 4, 256);
   L.bytes = off;
   return L;
 }
@@ -854,13 +908,15 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   const int32_t* sums = reinterpret_cast<const int32_t*>(ws + L.off_sums);
   const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
   const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
+  int32_t* bpre = reinterpret_cast<int32_t*>(ws + L.off_bpre);
+  block_prefix_kernel<<<kMaxBlocksPerAxis, kMaxBlocksPerAxis, 0, s>>>(grid, starts_d, sums, bpre);
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, qrec, data, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, qrec, data, m, p, k, out, nbr_out, kd2_out);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, qrec, data, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, qrec, data, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 
