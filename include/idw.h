@@ -280,6 +280,19 @@ idw_status idw_selftest_bounded_wait(idw_handle_t handle, void *stream);
 idw_status idw_measure_pipe_rates(int device, double rates[6]);
 
 /*
+ * Diagnostic of a debug build (the library compiled with -DIDW_DEBUG_CHECKS,
+ * e.g. paper_1402_4986_gb300.build.build(debug=True)): the kernels of the
+ * local and k-nearest-neighbour forms check every gather, scatter, cell,
+ * heap and output index; a failed check sets its site's bit in a device word
+ * and skips the access (nothing traps).  This call writes that word for
+ * `device` to *sites and clears it.  Bits: 0 cell index, 1 sorted-data
+ * gather, 2 scatter position, 3 output row, 4 heap slot or data index,
+ * 5 occupancy-block index, 6 hit index.  A release build returns
+ * IDW_ERR_UNSUPPORTED (and *sites = 0).  Synchronous.
+ */
+idw_status idw_debug_check_failures(int device, uint32_t *sites);
+
+/*
  * The paper's own GPU designs, as measured baselines (not the fast path):
  *   IDW_PAPER_NAIVE : one thread per prediction point reading every data
  *                     point from global memory (Sec. 3; data read m times);

@@ -76,6 +76,7 @@ SIGNATURES = {
     "idw_plan_forward": (c_int, [c_int32, c_int32, c_int64, c_int64, c_double, c_int,
                                  ctypes.POINTER(PlanInfo)]),
     "idw_measure_pipe_rates": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "idw_debug_check_failures": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint32)]),
     "idw_set_option": (c_int, [c_void_p, c_int, c_int64]),
     "idw_get_option": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),
     "idw_profile_enable": (c_int, [c_void_p, c_int]),
@@ -97,7 +98,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library to load: the debug build (index checks, see
+    idw_debug_check_failures) when IDW_DEBUG_CHECKS=1, else the release one."""
+    return _build.LIB_DEBUG if os.environ.get("IDW_DEBUG_CHECKS") == "1" else _build.LIB
 
 
 def load():

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "idw.h"
 #include "idw_device.cuh"
 #include "idw_internal.h"
@@ -52,6 +54,13 @@ using idw::Plan;
 constexpr int64_t kMaxCount = int64_t(1) << 31;
 
 inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// An NVTX range around one entry point (visible in Nsight timelines; a
+// no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Makes the handle's device current for the lifetime of the guard.
 struct DeviceGuard {
@@ -418,6 +427,7 @@ const char* idw_last_cuda_error(idw_handle_t h) { return h ? h->last_cuda : "nul
 idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, const void* queries,
                                  int64_t m, double p, idw_precision prec, void* out,
                                  double* s0_out, int32_t* hit_out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_saved");
   idw_status st = check_common(h, data, n, queries, m, p, prec, out);
   if (st != IDW_OK || m == 0) return st;
   if (!aligned(s0_out, 8) || !aligned(hit_out, 4)) return IDW_ERR_ALIGNMENT;
@@ -469,6 +479,7 @@ idw_status idw_interpolate(idw_handle_t h, const void* data, int64_t n, const vo
 
 idw_status idw_interpolate_host(idw_handle_t h, const void* data, int64_t n, const void* queries,
                                 int64_t m, double p, idw_precision prec, void* out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_host");
   idw_status st = check_common(h, data, n, queries, m, p, prec, out);
   if (st != IDW_OK || m == 0) return st;
   DeviceGuard guard(h->device);
@@ -495,6 +506,7 @@ idw_status idw_interpolate_host(idw_handle_t h, const void* data, int64_t n, con
 idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* const* data,
                                    const int64_t* n, const void* const* queries, const int64_t* m,
                                    double p, idw_precision prec, void* const* out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_batched");
   if (!h || count < 0 || (count > 0 && (!data || !n || !queries || !m || !out)))
     return IDW_ERR_INVALID_ARG;
   if (prec != IDW_PREC_F32_COMP) return IDW_ERR_UNSUPPORTED;
@@ -545,6 +557,7 @@ idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const floa
                         int64_t m, double p, const float* Z, const double* s0, const int32_t* hit,
                         const float* grad_out, float* grad_z, float* grad_data_xy,
                         float* grad_query_xy, double* grad_p, void* stream) {
+  NvtxRange nvtx("idw_backward");
   idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, Z);
   if (st != IDW_OK) return st;
   if (m == 0) {
@@ -582,6 +595,7 @@ idw_status idw_backward(idw_handle_t h, const float* data, int64_t n, const floa
 idw_status idw_paper_interpolate(idw_handle_t h, idw_paper_kernel kernel, idw_paper_layout layout,
                                  const void* data, int64_t n, const void* queries, int64_t m,
                                  double p, idw_precision prec, void* out, void* stream) {
+  NvtxRange nvtx("idw_paper_interpolate");
   idw_status st = check_common(h, data, n, queries, m, p, prec, out);
   if (st != IDW_OK || m == 0) return st;
   if (kernel != IDW_PAPER_NAIVE && kernel != IDW_PAPER_TILED) return IDW_ERR_INVALID_ARG;
@@ -602,6 +616,7 @@ idw_status idw_paper_interpolate(idw_handle_t h, idw_paper_kernel kernel, idw_pa
 idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
                                  const float* queries, int64_t m, double p, double radius,
                                  float* out, int32_t* count_out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_local");
   idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, out);
   if (st != IDW_OK) return st;
   if (!(radius > 0.0)) return IDW_ERR_INVALID_ARG;
@@ -624,6 +639,7 @@ idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
 idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, const float* queries,
                                int64_t m, double p, int32_t k, float* out, int32_t* nbr_out,
                                float* kd2_out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_knn");
   idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, out);
   if (st != IDW_OK) return st;
   if (k < 1 || k > idw::kKnnMax) return IDW_ERR_INVALID_ARG;
@@ -766,6 +782,20 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas, int64_t n, int64_t m
   out->partial_slots = pl.partial_slots;
   out->workspace_bytes = pl.workspace_bytes;
   return IDW_OK;
+}
+
+idw_status idw_debug_check_failures(int device, uint32_t* sites) {
+  if (!sites) return IDW_ERR_INVALID_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  bool enabled = false;
+  unsigned v = 0;
+  if (idw::debug_check_failures(&v, &enabled) != cudaSuccess) return IDW_ERR_CUDA;
+  *sites = v;
+  return enabled ? IDW_OK : IDW_ERR_UNSUPPORTED;
 }
 
 idw_status idw_measure_pipe_rates(int device, double rates[6]) {

@@ -63,6 +63,28 @@ constexpr int kMaxBlocksPerAxis = kMaxCellsPerAxis >> kBlockShift;
 // (FTZ) weights: such queries are redone in FP64.
 constexpr float kTinyPerMember = 0x1p-100f;
 
+// Index checks of a debug build (-DIDW_DEBUG_CHECKS): a failed check sets
+// its site's bit in a device word and the access it guards is skipped; no
+// trap.  Release builds compile every check to `true`.
+enum DebugSite : unsigned {
+  kSiteCell = 0,      // a cell index outside [0, cells]
+  kSiteGather = 1,    // a sorted-data position outside [0, n)
+  kSiteScatter = 2,   // a scatter position outside its array
+  kSiteOutput = 3,    // an output row outside [0, m)
+  kSiteHeap = 4,      // a heap slot outside [0, k)
+  kSiteBlock = 5,     // an occupancy-block index outside the prefix table
+  kSiteData = 6,      // a data index outside [0, n)
+};
+#ifdef IDW_DEBUG_CHECKS
+__device__ unsigned g_debug_failures;
+__device__ __forceinline__ bool dcheck(bool ok, DebugSite site) {
+  if (!ok) atomicOr(&g_debug_failures, 1u << site);
+  return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dcheck(bool, DebugSite) { return true; }
+#endif
+
 // Grid of cells, planned on the device.  Each call starts by setting every
 // byte of it to 0xff (keys at their identity, tickets at -1).
 struct GridDev {
@@ -330,7 +352,8 @@ __global__ void __launch_bounds__(kScanBlock)
 }
 
 __device__ __forceinline__ int cell_start(const int32_t* __restrict__ starts,
-                                          const int32_t* __restrict__ base, int i) {
+                                          const int32_t* __restrict__ base, int i, int cells) {
+  if (!dcheck(i >= 0 && i <= cells, kSiteCell)) return 0;
   return starts[i] + base[i / kScanTile];
 }
 
@@ -352,7 +375,8 @@ __global__ void __launch_bounds__(kMaxBlocksPerAxis)
     const int x0 = bx << kBlockShift, x1 = min(g.gx - 1, x0 + 7);
     const int y0 = by << kBlockShift, y1 = min(g.gy - 1, y0 + 7);
     for (int yy = y0; yy <= y1; ++yy)
-      c += cell_start(starts, base, yy * g.gx + x1 + 1) - cell_start(starts, base, yy * g.gx + x0);
+      c += cell_start(starts, base, yy * g.gx + x1 + 1, g.cells) -
+           cell_start(starts, base, yy * g.gx + x0, g.cells);
   }
   // Exclusive scan over the row's blocks (kMaxBlocksPerAxis threads).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -386,13 +410,15 @@ __global__ void __launch_bounds__(256)
     const float x = data[3 * i], y = data[3 * i + 1];
     const int c = data_cell(g, x, y);
     if (c < 0) return;
-    const int pos = cell_start(starts_d, sums, c) + atomicAdd(&cursor_d[c], 1);
+    const int pos = cell_start(starts_d, sums, c, g.cells) + atomicAdd(&cursor_d[c], 1);
+    if (!dcheck(pos >= 0 && pos < n, kSiteScatter)) return;
     sorted[pos] = make_float4(x, y, data[3 * i + 2], __int_as_float(static_cast<int>(i)));
   } else if (i < n + m) {
     const int64_t j = i - n;
     const float x = queries[2 * j], y = queries[2 * j + 1];
     const int b = query_bucket(g, x, y);
-    const int pos = cell_start(starts_q, sums + max_tiles, b) + atomicAdd(&cursor_q[b], 1);
+    const int pos = cell_start(starts_q, sums + max_tiles, b, g.cells) + atomicAdd(&cursor_q[b], 1);
+    if (!dcheck(pos >= 0 && pos < m, kSiteScatter)) return;
     qrec[pos] = make_float4(x, y, __int_as_float(static_cast<int>(j)), 0.f);
   }
 }
@@ -448,8 +474,8 @@ struct Runs {
       const int xa = clamp_floor(u - e, 0, g.gx), xb = clamp_floor(u + e, -1, g.gx - 1);
       a[r] = b[r] = 0;
       if (yy >= 0 && yy <= y1 && dy < g.rho && xa <= xb) {
-        a[r] = cell_start(starts, base, yy * g.gx + xa);
-        b[r] = cell_start(starts, base, yy * g.gx + xb + 1);
+        a[r] = cell_start(starts, base, yy * g.gx + xa, g.cells);
+        b[r] = cell_start(starts, base, yy * g.gx + xb + 1, g.cells);
       }
     }
   }
@@ -465,14 +491,16 @@ struct Runs {
 template <int MODE>
 __global__ void __launch_bounds__(kLocalThreads)
     local_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
-                       const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
-                       const float4* __restrict__ qrec, int64_t m, double p, float r2f,
-                       float r2t, float* __restrict__ out, int32_t* __restrict__ count_out) {
+                       int64_t n, const int32_t* __restrict__ starts,
+                       const int32_t* __restrict__ base, const float4* __restrict__ qrec,
+                       int64_t m, double p, float r2f, float r2t, float* __restrict__ out,
+                       int32_t* __restrict__ count_out) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= m) return;
   const float4 r = qrec[t];
   const float qx = r.x, qy = r.y;
   const int j = __float_as_int(r.z);
+  if (!dcheck(j >= 0 && j < m, kSiteOutput)) return;
   const Runs runs(*grid, qx, qy, starts, base);
   const float hp = static_cast<float>(0.5 * p), nhp = -hp;
 
@@ -484,6 +512,7 @@ __global__ void __launch_bounds__(kLocalThreads)
   for (int r = 0; r < 5; ++r) {
 #pragma unroll 2
     for (int k = runs.a[r]; k < runs.b[r]; ++k) {
+      if (!dcheck(k >= 0 && k < n, kSiteGather)) break;
       const float4 v = sorted[k];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       if (d2 < r2t) {
@@ -628,7 +657,7 @@ __global__ void __launch_bounds__(kKnnThreads)
     knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                      const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
                      const int32_t* __restrict__ bpre, const float4* __restrict__ qrec,
-                     const float* __restrict__ data, int64_t m,
+                     const float* __restrict__ data, int64_t n, int64_t m,
                      double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
                      float* __restrict__ kd2_out) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
@@ -640,19 +669,22 @@ __global__ void __launch_bounds__(kKnnThreads)
   const float4 rq = qrec[t];
   const float qx = rq.x, qy = rq.y;
   const int j = __float_as_int(rq.z);
+  if (!dcheck(j >= 0 && j < m, kSiteOutput)) return;
   int best_hit = INT_MAX;
   u64 worst = ~u64(0);  // the heap's largest key once it holds k, else above every key
 
   auto run = [&](int yy, int xa, int xb) {
-    const int a = cell_start(starts, base, yy * g.gx + xa);
-    const int b = cell_start(starts, base, yy * g.gx + xb + 1);
+    const int a = cell_start(starts, base, yy * g.gx + xa, g.cells);
+    const int b = cell_start(starts, base, yy * g.gx + xb + 1, g.cells);
     for (int q = a; q < b; ++q) {
+      if (!dcheck(q >= 0 && q < n, kSiteGather)) break;
       const float4 v = sorted[q];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       const int idx = __float_as_int(v.w);
       if (d2 == 0.f && v.x == qx && v.y == qy) best_hit = min(best_hit, idx);
       const u64 key = knn_key(d2, idx);
       if (key < worst) {  // worst stays ~0 (all ones) until the heap is full
+        if (!dcheck(hp.size <= k && idx >= 0 && idx < n, kSiteHeap)) continue;
         if (hp.size < k) {
           hp.push(key);
           if (hp.size == k) worst = hp.top();
@@ -708,6 +740,9 @@ __global__ void __launch_bounds__(kKnnThreads)
         }
         for (int by = ya >> kBlockShift; by <= (yb >> kBlockShift); ++by) {
           const int32_t* bp = bpre + by * (kMaxBlocksPerAxis + 1);
+          if (!dcheck(by < kMaxBlocksPerAxis && (xb >> kBlockShift) < kMaxBlocksPerAxis,
+                      kSiteBlock))
+            continue;
           if (bp[(xb >> kBlockShift) + 1] == bp[xa >> kBlockShift]) continue;
           const int y1 = min(yb, (by << kBlockShift) + 7);
           for (int yy = max(ya, by << kBlockShift); yy <= y1; ++yy) fn(yy, xa, xb);
@@ -729,8 +764,8 @@ __global__ void __launch_bounds__(kKnnThreads)
       while (r2 > r + 1) {
         int count = 0;
         band(r2, [&](int yy, int xa, int xb) {
-          count += cell_start(starts, base, yy * g.gx + xb + 1) -
-                   cell_start(starts, base, yy * g.gx + xa);
+          count += cell_start(starts, base, yy * g.gx + xb + 1, g.cells) -
+                   cell_start(starts, base, yy * g.gx + xa, g.cells);
         });
         if (count <= 4 * k) break;
         r2 = r + max(1, (r2 - r) >> 1);
@@ -743,7 +778,7 @@ __global__ void __launch_bounds__(kKnnThreads)
   if (kd2_out) kd2_out[j] = size > 0 ? key_d2(hp.top()) : __int_as_float(0x7fc00000);
   float zv = __int_as_float(0x7fc00000);  // NaN: nothing selected
   if (best_hit != INT_MAX) {
-    zv = data[3 * int64_t(best_hit) + 2];
+    if (dcheck(best_hit >= 0 && best_hit < n, kSiteData)) zv = data[3 * int64_t(best_hit) + 2];
   } else if (size > 0) {
     const float hpw = static_cast<float>(0.5 * p), nhp = -hpw;
     u64 hi = 0, lo = 0;
@@ -880,12 +915,26 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
   if (p == 2.0)
-    local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(grid, sorted, starts_d, sums, qrec,
-                                                               m, p, r2f, r2t, out, count_out);
+    local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
   else
     local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
-        grid, sorted, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
   return cudaGetLastError();
+}
+
+cudaError_t debug_check_failures(unsigned* sites, bool* enabled) {
+#ifdef IDW_DEBUG_CHECKS
+  *enabled = true;
+  cudaError_t e = cudaMemcpyFromSymbol(sites, g_debug_failures, sizeof(unsigned));
+  const unsigned zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_debug_failures, &zero, sizeof(unsigned));
+  return e;
+#else
+  *enabled = false;
+  *sites = 0;
+  return cudaSuccess;
+#endif
 }
 
 size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
@@ -913,10 +962,10 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, qrec, data, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, qrec, data, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 

@@ -28,6 +28,11 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
                          double radius, float* out, int32_t* count_out, void* workspace,
                          const LocalLayout& L, int sm_count, cudaStream_t s);
 
+// Index-check failures of a debug build (bit s = check site s failed since
+// the last call; cleared by the call), on the current device.  *enabled is
+// false in a release build.
+cudaError_t debug_check_failures(unsigned* sites, bool* enabled);
+
 // The k-nearest-neighbour form (1 <= k <= kKnnMax): same grid build, then
 // a ring search per query.  nbr_out (m x k) and kd2_out (m) may be null.
 constexpr int kKnnMax = 64;

@@ -109,3 +109,34 @@ def test_autotune_cache_given_at_creation(idw, tmp_path):
     h2 = idw.Handle(torch.cuda.current_device(), autotune_cache=path)
     assert idw.get_option("tuned_classes", handle=h2) == len(table)
     h2.close()
+
+
+def test_misaligned_pointers_are_refused(idw):
+    """Every device pointer is checked for its element alignment on the host,
+    before any launch (IDW_ERR_ALIGNMENT)."""
+    import ctypes
+    h = idw.get_handle()
+    lib = h.lib
+    buf = torch.zeros(4096, dtype=torch.float64, device="cuda")
+    base = buf.data_ptr()
+    ok32, bad32 = base, base + 2          # float32 needs 4-byte alignment
+    ok64, bad64 = base, base + 4          # float64 needs 8-byte alignment
+    s = torch.cuda.current_stream().cuda_stream
+    P = ctypes.c_void_p
+
+    def fwd(prec, d, q, o):
+        return lib.idw_interpolate(h.ptr, P(d), 16, P(q), 16, 2.0, prec, P(o), P(s))
+
+    assert fwd(0, bad32, ok32, ok32) == 2
+    assert fwd(0, ok32, bad32, ok32) == 2
+    assert fwd(0, ok32, ok32, bad32) == 2
+    assert fwd(1, bad64, ok64, ok64) == 2
+    assert fwd(1, ok64, ok64, bad64) == 2
+    assert lib.idw_interpolate_saved(h.ptr, P(ok32), 16, P(ok32), 16, 2.0, 0, P(ok32), P(bad64),
+                                     P(ok32), P(s)) == 2
+    assert lib.idw_interpolate_local(h.ptr, P(ok32), 16, P(ok32), 16, 2.0, 0.1, P(ok32),
+                                     P(bad32), P(s)) == 2
+    assert lib.idw_interpolate_knn(h.ptr, P(ok32), 16, P(ok32), 16, 2.0, 4, P(ok32), P(bad32),
+                                   P(ok32), P(s)) == 2
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(buf) == 0  # nothing was launched
