@@ -85,6 +85,20 @@ def test_general_power(idw, p):
     assert _rel_err(Zd, Z64, data[:, 2]) <= TOL_F64, p
 
 
+@pytest.mark.parametrize("p", [0.01, 40.0, 64.0])
+def test_extreme_powers(idw, p):
+    """p near 0 (weights nearly equal: the sums' compensation carries the
+    result) and p = 40, 64 (FP32 weights overflow or flush for most pairs, so
+    most queries take the FP64 recompute; Z tends to the nearest value)."""
+    prob = synthetic.uniform_problem(2000, 600, seed=95, exact_hits=3)
+    data, q = prob["data"], prob["queries"]
+    Z64, _ = oracle.idw(data, q, p)
+    Z, s0, hit = _run(idw, data, q, p)
+    assert _rel_err(Z, Z64, data[:, 2]) <= TOL_F32C, p
+    Zd, _, _ = _run(idw, data, q, p, "f64")
+    assert _rel_err(Zd, Z64, data[:, 2]) <= TOL_F64, p
+
+
 def test_clustered_config_sampled(idw):
     prob = synthetic.config_clustered(n=65536, grid=256)
     data, q = prob["data"], prob["queries"]
