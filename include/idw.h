@@ -120,10 +120,12 @@ idw_status idw_interpolate_host(idw_handle_t handle, const void *data_xyz, int64
                                 idw_precision prec, void *out, void *stream);
 
 /*
- * `count` independent problems (Eq. 1 for each) in one persistent launch.
- * The arrays of pointers and sizes are HOST arrays of length `count`; the
- * pointers they hold are device pointers laid out as in idw_interpolate.
- * Only IDW_PREC_F32_COMP is supported.  Instances with m_k = 0 are skipped.
+ * `count` independent problems (Eq. 1 for each).  The arrays of pointers
+ * and sizes are HOST arrays of length `count`; the pointers they hold are
+ * device pointers laid out as in idw_interpolate.  IDW_PREC_F32_COMP runs
+ * the batch as one persistent launch (chunks of 256 problems);
+ * IDW_PREC_F64_PLAIN, the comparison form, runs one stream-ordered
+ * single-problem call per instance.  Instances with m_k = 0 are skipped.
  */
 idw_status idw_interpolate_batched(idw_handle_t handle, int32_t count,
                                    const void *const *data_xyz, const int64_t *n,

@@ -166,24 +166,26 @@ def interpolate_host(data, queries, p: float = 2.0, precision="f32c", out=None,
 
 
 def interpolate_batched(datas, queries_list, p: float = 2.0, outs=None,
-                        handle: Handle | None = None):
-    """Eq. 1 for many independent problems in one call (FP32-compensated)."""
+                        handle: Handle | None = None, precision="f32c"):
+    """Eq. 1 for many independent problems in one call (FP32-compensated in
+    one persistent launch; "f64": the plain FP64 form, one launch each)."""
+    prec = _prec(precision)
     k = len(datas)
     if len(queries_list) != k:
         raise ValueError("datas and queries_list differ in length")
     if k == 0:
         return []
     for d, q in zip(datas, queries_list):
-        _check_inputs(d, q, PREC_F32_COMP)
+        _check_inputs(d, q, prec)
     if outs is None:
-        outs = [torch.empty(q.shape[0], dtype=torch.float32, device=q.device) for q in queries_list]
+        outs = [torch.empty(q.shape[0], dtype=_DTYPE[prec], device=q.device) for q in queries_list]
     h = handle or get_handle(datas[0].device)
     P = ctypes.c_void_p * k
     I = ctypes.c_int64 * k
     st = h.lib.idw_interpolate_batched(
         h.ptr, k, P(*[d.data_ptr() for d in datas]), I(*[d.shape[0] for d in datas]),
         P(*[q.data_ptr() for q in queries_list]), I(*[q.shape[0] for q in queries_list]),
-        float(p), PREC_F32_COMP, P(*[o.data_ptr() for o in outs]), _stream(datas[0]))
+        float(p), prec, P(*[o.data_ptr() for o in outs]), _stream(datas[0]))
     _lib.check(st, "idw_interpolate_batched", h.ptr)
     return outs
 

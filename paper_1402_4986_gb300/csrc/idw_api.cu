@@ -509,10 +509,19 @@ idw_status idw_interpolate_batched(idw_handle_t h, int32_t count, const void* co
   NvtxRange nvtx("idw_interpolate_batched");
   if (!h || count < 0 || (count > 0 && (!data || !n || !queries || !m || !out)))
     return IDW_ERR_INVALID_ARG;
-  if (prec != IDW_PREC_F32_COMP) return IDW_ERR_UNSUPPORTED;
   for (int32_t k = 0; k < count; ++k) {
     idw_status st = check_common(h, data[k], n[k], queries[k], m[k], p, prec, out[k]);
     if (st != IDW_OK) return st;
+  }
+  if (prec == IDW_PREC_F64_PLAIN) {
+    // The comparison form: one stream-ordered single-problem call each
+    // (consecutive problems reuse the workspace in stream order).
+    for (int32_t k = 0; k < count; ++k) {
+      const idw_status st = idw_interpolate_saved(h, data[k], n[k], queries[k], m[k], p, prec,
+                                                  out[k], nullptr, nullptr, stream);
+      if (st != IDW_OK) return st;
+    }
+    return IDW_OK;
   }
   // Problems with m = 0 have nothing to compute; the rest go in chunks of
   // up to kBatchCap problems, one persistent launch per chunk.

@@ -111,3 +111,18 @@ def test_batched_call_is_graph_capturable(idw):
     torch.cuda.synchronize()
     for a, b in zip(eager, outs):
         assert torch.equal(a, b)
+
+
+def test_fp64_batch_matches_oracle(idw):
+    """The plain FP64 form through the batched entry (one call per instance)."""
+    probs = _problems([(300, 200), (1, 5), (2049, 257), (50, 0), (4000, 3000)], 300)
+    d = [torch.from_numpy(pr["data"]).cuda().double() for pr in probs]
+    q = [torch.from_numpy(pr["queries"]).cuda().double() for pr in probs]
+    outs = idw.interpolate_batched(d, q, 2.5, precision="f64")
+    idw.sync_status()
+    for pr, o in zip(probs, outs):
+        if pr["queries"].shape[0] == 0:
+            continue
+        Z64, _ = oracle.idw(pr["data"], pr["queries"], 2.5)
+        err = np.max(np.abs(o.cpu().numpy() - Z64)) / np.max(np.abs(pr["data"][:, 2]))
+        assert err <= 1e-13, err
