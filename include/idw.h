@@ -9,7 +9,10 @@
  *     Z(q) = sum_i w_i z_i / sum_i w_i,   w_i = d(q, x_i)^(-p),
  *
  * over ALL n data points (standard, global IDW; Sec. 1 and Sec. 2.1), with p
- * an arbitrary positive real (Sec. 2.1; typically 2).
+ * an arbitrary positive real (Sec. 2.1; typically 2).  The two local forms
+ * the paper names among its related work (Sec. 1) are here too: Eq. 1 over
+ * the data points within a radius R (idw_interpolate_local) and over the k
+ * nearest data points (idw_interpolate_knn).
  *
  * Conventions shared by every entry point:
  *   - A data point is a row (x, y, z): d is the 2-D Euclidean distance in
@@ -20,7 +23,8 @@
  *   - A query whose (x, y) equals a data point's (x, y) numerically (so
  *     d = 0, where Eq. 1 is undefined) gets the z of the LOWEST such index.
  *   - NaN in a query's inputs gives NaN in its result unless an exact hit
- *     is found first; inputs are not scanned for NaN.
+ *     is found first; inputs are not scanned for NaN unless the handle's
+ *     IDW_OPT_VALIDATE_INPUTS option is set.
  *   - Pointers named "device" are CUDA device (or managed) memory owned by
  *     the caller; they must stay valid until the work on `stream` is done.
  *     Every float array needs 4-byte alignment, every double array 8-byte.
@@ -103,7 +107,9 @@ idw_status idw_interpolate(idw_handle_t handle, const void *data_xyz, int64_t n,
  * As idw_interpolate, and also saves what the adjoint needs:
  *   s0_out  : device, m doubles, nullable: the weight sum S0 = sum_i w_i
  *             (+inf at an exact hit).
- *   hit_out : device, m int32, nullable: the exact-hit index, or -1.
+ *   hit_out : device, m int32, nullable: the exact-hit index, -1 for an
+ *             ordinary query, or -2 where the sums left FP32's range and the
+ *             query was recomputed in FP64 (F32_COMP only).
  */
 idw_status idw_interpolate_saved(idw_handle_t handle, const void *data_xyz, int64_t n,
                                  const void *queries_xy, int64_t m, double p,
