@@ -1,0 +1,61 @@
+"""Data sets whose 16-byte staged records pass 2^32 bytes (n > 2^28): every
+byte offset and record index on the device must be 64-bit clean.  The
+global, radius-limited and k-NN forms are checked on sampled queries
+against the oracle.  About 12 GB of device memory and 3.3 GB of host memory.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+N = (1 << 28) + 12345
+TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def problem():
+    from paper_1402_4986_gb300 import build
+    build.build()
+    import paper_1402_4986_gb300 as idw
+    rng = np.random.default_rng(2025)
+    data = np.empty((N, 3), np.float32)
+    data[:, :2] = rng.random((N, 2), dtype=np.float32)
+    data[:, 2] = np.sin(6.283185307 * data[:, 0]) * np.cos(6.283185307 * data[:, 1])
+    q = rng.random((300, 2), dtype=np.float32)
+    q[7] = data[N - 3, :2]  # an exact hit near the end of the data
+    d = torch.from_numpy(data).cuda()
+    qq = torch.from_numpy(q).cuda()
+    idx = np.sort(np.random.default_rng(3).choice(300, 24, replace=False))
+    idx = np.union1d(idx, [7])
+    yield idw, data, q, d, qq, idx
+    del d, qq
+    torch.cuda.empty_cache()
+
+
+def test_global_form_past_4gb_of_staged_records(problem):
+    idw, data, q, d, qq, idx = problem
+    Z = idw.interpolate(d, qq, 2.0).cpu().numpy()
+    Z64, hit = oracle.idw(data, q[idx], 2.0)
+    assert hit[list(idx).index(7)] == N - 3
+    err = np.max(np.abs(Z[idx].astype(np.float64) - Z64)) / np.max(np.abs(data[:, 2]))
+    assert err <= TOL, err
+
+
+def test_local_forms_past_4gb_of_sorted_records(problem):
+    idw, data, q, d, qq, idx = problem
+    R = 2e-4  # ~34 members per query at this density
+    Z, cnt = idw.interpolate_local(d, qq, 2.0, R, counts=True)
+    Zl, _, cl = oracle.idw_local(data, q[idx], 2.0, R)
+    assert np.array_equal(cnt.cpu().numpy()[idx], cl)
+    ok = ~np.isnan(Zl)
+    err = np.max(np.abs(Z.cpu().numpy()[idx][ok] - Zl[ok])) / np.max(np.abs(data[:, 2]))
+    assert err <= TOL, err
+    Zk, nbr = idw.interpolate_knn(d, qq, 2.0, 16, neighbours=True)
+    rk = oracle.idw_knn(data, q[idx], 2.0, 16)
+    assert np.array_equal(nbr.cpu().numpy()[idx], rk["nbr"])
+    assert rk["nbr"][list(idx).index(7), 0] == N - 3
+    err = np.max(np.abs(Zk.cpu().numpy()[idx] - rk["Z"])) / np.max(np.abs(data[:, 2]))
+    assert err <= TOL, err
