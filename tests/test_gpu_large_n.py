@@ -59,3 +59,25 @@ def test_local_forms_past_4gb_of_sorted_records(problem):
     assert rk["nbr"][list(idx).index(7), 0] == N - 3
     err = np.max(np.abs(Zk.cpu().numpy()[idx] - rk["Z"])) / np.max(np.abs(data[:, 2]))
     assert err <= TOL, err
+
+
+def test_adjoint_past_4gb_of_staged_records(problem):
+    """Query gradients on sampled queries against the oracle; the data-side
+    gradients through partition of unity and translation invariance."""
+    idw, data, q, d, qq, idx = problem
+    p = 2.5
+    keep = np.setdiff1d(np.arange(q.shape[0]), [7])  # no exact hit here
+    qk = qq[torch.from_numpy(keep).cuda()].contiguous()
+    g = torch.from_numpy(np.random.default_rng(4).standard_normal(keep.size).astype(np.float32))
+    Z, s0, hit = idw.interpolate_saved(d, qk, p)
+    gz, gxy, gq, _ = idw.backward(d, qk, p, Z, s0, hit, g.cuda(), need_p=False)
+    idw.sync_status()
+    sel = np.arange(0, keep.size, 25)
+    G = oracle.idw_grad(data, q[keep][sel], p, g.numpy()[sel].astype(np.float64))
+    gq = gq.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(gq[sel] - G["grad_q"])) <= 1e-4 * np.max(np.abs(G["grad_q"]))
+    g64 = g.numpy().astype(np.float64)
+    assert abs(float(gz.double().sum()) - g64.sum()) <= 1e-4 * np.abs(g64).sum()
+    gxy = gxy.cpu().numpy().astype(np.float64)
+    total = gxy.sum(0) + gq.sum(0)
+    assert np.all(np.abs(total) <= 1e-4 * (np.abs(gxy).sum(0) + np.abs(gq).sum(0)))
