@@ -81,3 +81,37 @@ def test_adjoint_past_4gb_of_staged_records(problem):
     gxy = gxy.cpu().numpy().astype(np.float64)
     total = gxy.sum(0) + gq.sum(0)
     assert np.all(np.abs(total) <= 1e-4 * (np.abs(gxy).sum(0) + np.abs(gq).sum(0)))
+
+
+def test_large_m_past_4gb_of_partials_and_query_records():
+    """m = 2^28 + 123 queries against 64 points: the 16-byte partial-sum
+    slots and sorted query records pass 2^32 bytes."""
+    from paper_1402_4986_gb300 import build
+    build.build()
+    import paper_1402_4986_gb300 as idw
+    M = (1 << 28) + 123
+    rng = np.random.default_rng(2026)
+    data = np.empty((64, 3), np.float32)
+    data[:, :2] = rng.random((64, 2), dtype=np.float32)
+    data[:, 2] = rng.standard_normal(64).astype(np.float32)
+    qd = torch.rand(M, 2, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    d = torch.from_numpy(data).cuda()
+    sel = torch.tensor([0, 1, 12345, M // 2, M - 2, M - 1], device="cuda")
+    qs = qd[sel].cpu().numpy()
+    zmax = np.max(np.abs(data[:, 2]))
+    Z = idw.interpolate(d, qd, 2.0)
+    Z64, _ = oracle.idw(data, qs, 2.0)
+    assert np.max(np.abs(Z[sel].cpu().numpy() - Z64)) / zmax <= TOL
+    del Z
+    Zl = idw.interpolate_local(d, qd, 2.0, 0.2)
+    Zl64, _, _ = oracle.idw_local(data, qs, 2.0, 0.2)
+    a = Zl[sel].cpu().numpy()
+    assert np.array_equal(np.isnan(a), np.isnan(Zl64))
+    ok = ~np.isnan(Zl64)
+    assert np.max(np.abs(a[ok] - Zl64[ok]), initial=0.0) / zmax <= TOL
+    del Zl
+    Zk = idw.interpolate_knn(d, qd, 2.0, 8)
+    rk = oracle.idw_knn(data, qs, 2.0, 8)
+    assert np.max(np.abs(Zk[sel].cpu().numpy() - rk["Z"])) / zmax <= TOL
+    del Zk, qd
+    torch.cuda.empty_cache()
