@@ -13,8 +13,9 @@ namespace idw {
 namespace {
 
 constexpr int kProbeThreads = 512;
-constexpr int kProbeIters = 2048;
+constexpr int kProbeIters = 8192;  // long enough that launch skew is noise
 constexpr int kChains = 8;
+constexpr int kRounds = 16;        // rounds per loop trip: loop overhead ~2%
 
 enum ProbeOp : int { kOpFfma = 0, kOpFfma2, kOpRcp, kOpLg2, kOpEx2, kOpDfma, kNumOps };
 
@@ -46,10 +47,10 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(float seed, ProbeO
   __syncthreads();
   const unsigned long long t0 = clock64();
 #pragma unroll 1
-  for (int it = 0; it < kProbeIters; it += 4) {
+  for (int it = 0; it < kProbeIters; it += kRounds) {
 #pragma unroll
-    for (int c = 0; c < 4 * kChains; ++c) {
-      const int k = c % kChains;  // four rounds per loop trip: little loop overhead
+    for (int c = 0; c < kRounds * kChains; ++c) {
+      const int k = c % kChains;
       if (OP == kOpFfma) v[k] = fmaf(v[k], 0.999f, 0.001f);
       if (OP == kOpFfma2) pv[k] = fma2(pv[k], a2, b2);
       if (OP == kOpRcp) v[k] = rcp_approx(v[k]) + 0.5f;  // fixed point 1.28
