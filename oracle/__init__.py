@@ -1,4 +1,6 @@
-"""FP64 CPU oracle for global Shepard IDW (Sec. 2.1, Eq. 1).
+"""FP64 CPU oracle for Shepard IDW (Sec. 2.1, Eq. 1): the global form, its
+gradients, and the radius-limited and k-nearest-neighbour local forms of
+the related work (Sec. 1).
 
 TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
@@ -11,7 +13,10 @@ numpy arrays.  Inputs given as float32 are promoted to float64 exactly, so the
 oracle sees the same bit patterns as the GPU path.
 
 Parity: pinned by ``tests/test_oracle_pins.py`` (exact rationals, mpmath,
-closed forms, invariants, finite differences).
+closed forms, invariants, finite differences, FP32-decision searches), and
+``tests/test_oracle_mutations.py`` checks that planted mistakes fail a pin.
+The ``bench.py`` CPU legs (``cpu_baseline`` and ``--impl reference``) time it
+as it stands.
 """
 from __future__ import annotations
 
