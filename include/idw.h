@@ -295,7 +295,8 @@ idw_status idw_measure_pipe_rates(int device, double rates[6]);
  * and skips the access (nothing traps).  This call writes that word for
  * `device` to *sites and clears it.  Bits: 0 cell index, 1 sorted-data
  * gather, 2 scatter position, 3 output row, 4 heap slot or data index,
- * 5 occupancy-block index, 6 hit index.  A release build returns
+ * 5 occupancy-block index, 6 hit index, 7 summed-area-table entry.  A
+ * release build returns
  * IDW_ERR_UNSUPPORTED (and *sites = 0).  Synchronous.
  */
 idw_status idw_debug_check_failures(int device, uint32_t *sites);

@@ -74,6 +74,7 @@ enum DebugSite : unsigned {
   kSiteHeap = 4,      // a heap slot outside [0, k)
   kSiteBlock = 5,     // an occupancy-block index outside the prefix table
   kSiteData = 6,      // a data index outside [0, n)
+  kSiteTable = 7,     // a summed-area-table entry outside (gx + 1)(gy + 1)
 };
 #ifdef IDW_DEBUG_CHECKS
 __device__ unsigned g_debug_failures;
@@ -395,6 +396,46 @@ __global__ void __launch_bounds__(kMaxBlocksPerAxis)
   if (bx == bgx - 1) row[bgx] = before + c;  // the row total
 }
 
+// Summed-area table of the data cells for the k-NN search: with W = gx + 1,
+// sat[y * W + x] is the number of data points in rows 0 .. y - 1 and columns
+// 0 .. x - 1, so any rectangle of cells is counted from four entries.  A
+// CTA takes 32 columns; its warp w sums rows w C .. (w + 1) C - 1 of each
+// column (C = ceil(gy / 32)), the warps' totals are scanned through shared
+// memory, and each warp writes its rows.  Launched with enough CTAs for
+// 2049 columns; those past gx + 1 return at once (the plan is on the
+// device).
+constexpr int kSatCols = 32, kSatWarps = 32;
+__global__ void __launch_bounds__(kSatCols * kSatWarps)
+    sat_kernel(const GridDev* __restrict__ grid, const int32_t* __restrict__ starts,
+               const int32_t* __restrict__ base, int32_t* __restrict__ sat) {
+  __shared__ int32_t part[kSatWarps][kSatCols];
+  const GridDev g = *grid;
+  if (int(blockIdx.x) * kSatCols > g.gx) return;  // the whole CTA: no barrier is reached
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int W = g.gx + 1, x = blockIdx.x * kSatCols + lane;
+  const int chunk = (g.gy + kSatWarps - 1) / kSatWarps;
+  const int y0 = min(g.gy, w * chunk), y1 = min(g.gy, y0 + chunk);
+  // Points of row y in columns 0 .. x - 1 (x = gx: the whole row).
+  auto row_prefix = [&](int y) {
+    return cell_start(starts, base, y * g.gx + x, g.cells) -
+           cell_start(starts, base, y * g.gx, g.cells);
+  };
+  int32_t s = 0;
+  if (x < W)
+    for (int y = y0; y < y1; ++y) s += row_prefix(y);
+  part[w][lane] = s;
+  __syncthreads();
+  int32_t acc = 0;
+  for (int i = 0; i < w; ++i) acc += part[i][lane];
+  if (x < W) {
+    if (w == 0) sat[x] = 0;
+    for (int y = y0; y < y1; ++y) {
+      acc += row_prefix(y);
+      if (dcheck(y + 1 <= g.gy, kSiteTable)) sat[(y + 1) * W + x] = acc;
+    }
+  }
+}
+
 // Threads [0, n) place data points as (x, y, z, index), [n, n + m) place
 // queries as (x, y, index, 0).
 __global__ void __launch_bounds__(256)
@@ -656,8 +697,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kKnnThreads)
     knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                      const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
-                     const int32_t* __restrict__ bpre, const float4* __restrict__ qrec,
-                     const float* __restrict__ data, int64_t n, int64_t m,
+                     const int32_t* __restrict__ bpre, const int32_t* __restrict__ sat,
+                     const float4* __restrict__ qrec, const float* __restrict__ data, int64_t n,
+                     int64_t m,
                      double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
                      float* __restrict__ kd2_out) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
@@ -704,7 +746,38 @@ __global__ void __launch_bounds__(kKnnThreads)
     const float ay = fmaxf(0.f, fmaxf(v - float(g.gy), -v) - mg);
     const float hh = g.inv2 > 0.f ? 2.f / g.inv2 : 0.f;
     const float h2 = __fmul_rd(hh, hh) * (1.f - 0x1p-18f);
+    const float ih2 = __frcp_ru(h2);  // +inf for the one-cell grid: nothing is clipped
+    // Once the heap holds k keys, a cell can only matter if the stop test's
+    // lower bound for its points, (gap_x^2 + gap_y^2) h2 - 2^-126 with each
+    // gap reduced by mg, is at most the k-th key's d^2: gap_x^2 + gap_y^2 <=
+    // reach2() (rounded up; +inf or NaN clips nothing).
+    auto reach2 = [&]() {
+      return __fmul_ru(__fadd_ru(key_d2(worst), 0x1p-126f), ih2);
+    };
+    // Narrows a range [lo, hi] to the cells t whose gap from c (reduced by
+    // mg) is at most e: t <= c + mg + e and t + 1 >= c - mg - e, rounded
+    // outwards.  An empty range is left as it is; otherwise the result lies
+    // in [lo, hi] or is empty (lo > hi).  NaN bounds clip nothing.
+    auto clip = [&](float c, float e, int& lo, int& hi) {
+      if (lo > hi) return;
+      const float a = ceilf(__fsub_rd(__fsub_rd(__fsub_rd(c, mg), e), 1.f));
+      const float b = floorf(__fadd_ru(__fadd_ru(c, mg), e));
+      const int nlo = int(fminf(fmaxf(float(lo), a), float(hi) + 1.f));
+      const int nhi = int(fmaxf(fminf(float(hi), b), float(lo) - 1.f));
+      lo = nlo;
+      hi = nhi;
+    };
+    // Points in the square of radius rr around (cx, cy), from the table.
+    auto square_count = [&](int rr) {
+      const int ya = max(0, cy - rr), yb = min(g.gy - 1, cy + rr);
+      const int xa = max(0, cx - rr), xb = min(g.gx - 1, cx + rr);
+      const int W = g.gx + 1;
+      if (!dcheck(ya >= 0 && xa >= 0 && yb < g.gy && xb < g.gx, kSiteTable)) return 0;
+      return sat[(yb + 1) * W + xb + 1] - sat[ya * W + xb + 1] - sat[(yb + 1) * W + xa] +
+             sat[ya * W + xa];
+    };
     run(cy, cx, cx);
+    int in_square = -1;  // points in the square of radius r, once counted
     for (int r = 0;;) {
       const bool open_l = cx - r > 0, open_r = cx + r < g.gx - 1;
       const bool open_b = cy - r > 0, open_t = cy + r < g.gy - 1;
@@ -732,10 +805,28 @@ __global__ void __launch_bounds__(kKnnThreads)
       // Rows ya..yb over columns xa..xb as row runs; once the square is 8
       // cells out, each stretch of 8 rows whose occupancy blocks over those
       // columns hold no point is skipped.
+      // With a full heap, rows and columns beyond the k-th key's reach are
+      // dropped first, and each row keeps only the columns its chord reaches.
+      auto row = [&](int yy, int xa, int xb, auto&& fn) {
+        if (hp.size == k) {
+          const float gap = fmaxf(0.f, fmaxf(float(yy) - v, v - float(yy + 1)) - mg);
+          const float w2 = reach2(), g2 = __fmul_rd(gap, gap);
+          if (g2 > w2) return;
+          clip(u, __fsqrt_ru(__fsub_ru(w2, g2)), xa, xb);
+          if (xa > xb) return;
+        }
+        fn(yy, xa, xb);
+      };
       auto rows = [&](int ya, int yb, int xa, int xb, auto&& fn) {
         if (xa > xb || ya > yb) return;  // then 0 <= ya <= yb < gy, 0 <= xa <= xb < gx
+        if (hp.size == k) {  // narrows the ranges (or empties them)
+          const float e = __fsqrt_ru(reach2());
+          clip(v, e, ya, yb);
+          clip(u, e, xa, xb);
+          if (xa > xb || ya > yb) return;
+        }
         if (r < 8) {  // near the query the blocks are rarely empty: skip no checks
-          for (int yy = ya; yy <= yb; ++yy) fn(yy, xa, xb);
+          for (int yy = ya; yy <= yb; ++yy) row(yy, xa, xb, fn);
           return;
         }
         for (int by = ya >> kBlockShift; by <= (yb >> kBlockShift); ++by) {
@@ -745,7 +836,7 @@ __global__ void __launch_bounds__(kKnnThreads)
             continue;
           if (bp[(xb >> kBlockShift) + 1] == bp[xa >> kBlockShift]) continue;
           const int y1 = min(yb, (by << kBlockShift) + 7);
-          for (int yy = max(ya, by << kBlockShift); yy <= y1; ++yy) fn(yy, xa, xb);
+          for (int yy = max(ya, by << kBlockShift); yy <= y1; ++yy) row(yy, xa, xb, fn);
         }
       };
       // The cells between squares r and r2: side strips of the rows already
@@ -760,17 +851,21 @@ __global__ void __launch_bounds__(kKnnThreads)
       };
       // Grow by max(1, r/2), halved while the band would hold more than 4k
       // points (a step from empty space into a dense cluster stays short).
+      // From r = 4 on (steps of 2 or more), the band's count comes from the
+      // summed-area table and an empty band is not walked.
       int r2 = r + max(1, r >> 1);
-      while (r2 > r + 1) {
-        int count = 0;
-        band(r2, [&](int yy, int xa, int xb) {
-          count += cell_start(starts, base, yy * g.gx + xb + 1, g.cells) -
-                   cell_start(starts, base, yy * g.gx + xa, g.cells);
-        });
-        if (count <= 4 * k) break;
-        r2 = r + max(1, (r2 - r) >> 1);
+      if (r >= 4) {
+        if (in_square < 0) in_square = square_count(r);
+        int c2 = square_count(r2);
+        while (c2 - in_square > 4 * k && r2 > r + 1) {
+          r2 = r + max(1, (r2 - r) >> 1);
+          c2 = square_count(r2);
+        }
+        if (c2 != in_square) band(r2, run);
+        in_square = c2;
+      } else {
+        band(r2, run);
       }
-      band(r2, run);
       r = r2;
     }
   }
@@ -859,6 +954,9 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells) {
   L.off_qrec = off;       off += round_up(size_t(m) * 16, 256);
   L.off_bpre = off;
   off += round_up(size_t(kMaxBlocksPerAxis) * (kMaxBlocksPerAxis + 1) * 4, 256);
+  // (gx + 1)(gy + 1) = cells + gx + gy + 1 entries, cells <= max_cells.
+  L.off_sat = off;
+  off += round_up(size_t(max_cells + 2 * kMaxCellsPerAxis + 1) * 4, 256);
   L.bytes = off;
   return L;
 }
@@ -958,14 +1056,17 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
   const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
   int32_t* bpre = reinterpret_cast<int32_t*>(ws + L.off_bpre);
+  int32_t* sat = reinterpret_cast<int32_t*>(ws + L.off_sat);
   block_prefix_kernel<<<kMaxBlocksPerAxis, kMaxBlocksPerAxis, 0, s>>>(grid, starts_d, sums, bpre);
+  sat_kernel<<<(kMaxCellsPerAxis + 1 + kSatCols - 1) / kSatCols, kSatCols * kSatWarps, 0, s>>>(
+      grid, starts_d, sums, sat);
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 

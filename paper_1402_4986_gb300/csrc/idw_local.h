@@ -14,7 +14,7 @@ namespace idw {
 struct LocalLayout {
   int64_t max_cells = 0;
   size_t off_grid = 0, off_counts_d = 0, off_counts_q = 0, off_starts_d = 0, off_starts_q = 0;
-  size_t off_sums = 0, off_sorted = 0, off_qrec = 0, off_bpre = 0;
+  size_t off_sums = 0, off_sorted = 0, off_qrec = 0, off_bpre = 0, off_sat = 0;
   size_t bytes = 0;
 };
 
