@@ -106,8 +106,10 @@ def parse():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--members", type=float, nargs="*", default=None,
-                    help="local / knn workloads only: uniform data with these neighbour "
-                         "counts (K, or k) instead of the default sweep")
+                    help="local / knn workloads only: these neighbour counts (K, or k) "
+                         "instead of the default sweep")
+    ap.add_argument("--data", choices=["uniform", "clustered"], default="uniform",
+                    help="local / knn workloads with --members: the data distribution")
     ap.add_argument("--config", default="headline",
                     choices=["headline", "scale", "clustered", "adjoint", "batched", "layout",
                              "paper", "local", "knn", "all"],
@@ -667,7 +669,7 @@ def run_local(args):
     rows = []
     cases = ((False, 32.0), (False, 8.0), (False, 128.0), (True, 32.0))
     if args.members:
-        cases = tuple((False, float(k)) for k in args.members)
+        cases = tuple((args.data == "clustered", float(k)) for k in args.members)
     for clustered, members in cases:
         prob = synthetic.config_local(members=members, clustered=clustered)
         d = torch.from_numpy(prob["data"]).cuda()
@@ -705,7 +707,8 @@ def run_knn(args):
     import paper_1402_4986_gb300 as idw
     rows = []
     ks = tuple(int(k) for k in args.members) if args.members else (8, 32, 64)
-    cases = [(False, k) for k in ks] + ([] if args.members else [(True, 32)])
+    cases = ([(args.data == "clustered", k) for k in ks] if args.members
+             else [(False, k) for k in ks] + [(True, 32)])
     for clustered, k in cases:
         prob = synthetic.config_local(clustered=clustered)
         d = torch.from_numpy(prob["data"]).cuda()

@@ -640,7 +640,9 @@ __global__ void __launch_bounds__(kLocalThreads)
 // that squared times (1 - 2^-18), minus 2^-126.  The bound is strict, so an
 // unseen point can neither beat nor tie the k-th key.
 
-constexpr int kKnnThreads = 128;
+// One warp per block: a block whose slowest query is still searching holds
+// only its own warp's heaps in shared memory.
+constexpr int kKnnThreads = 32;
 
 __device__ __forceinline__ u64 knn_key(float d2, int idx) {
   return (u64(__float_as_uint(d2)) << 32) | u64(unsigned(idx));
@@ -693,8 +695,10 @@ struct KnnHeap {
   }
 };
 
+// At most 64 registers (32 one-warp blocks per SM); left to itself the
+// compiler settles on fewer and spills.
 template <int MODE>
-__global__ void __launch_bounds__(kKnnThreads)
+__global__ void __maxnreg__(64)
     knn_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                      const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
                      const int32_t* __restrict__ bpre, const int32_t* __restrict__ sat,
@@ -776,84 +780,40 @@ __global__ void __launch_bounds__(kKnnThreads)
       return sat[(yb + 1) * W + xb + 1] - sat[ya * W + xb + 1] - sat[(yb + 1) * W + xa] +
              sat[ya * W + xa];
     };
-    run(cy, cx, cx);
     int in_square = -1;  // points in the square of radius r, once counted
-    for (int r = 0;;) {
-      const bool open_l = cx - r > 0, open_r = cx + r < g.gx - 1;
-      const bool open_b = cy - r > 0, open_t = cy + r < g.gy - 1;
-      if (!(open_l || open_r || open_b || open_t)) break;  // the square covers the grid
-      if (hp.size == k) {
-        float l2 = INFINITY;
-        if (open_l) {
-          const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
-          l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
-        }
-        if (open_r) {
-          const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
-          l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
-        }
-        if (open_b) {
-          const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
-          l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
-        }
-        if (open_t) {
-          const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
-          l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
-        }
-        if (key_d2(worst) < __fmul_rd(l2, h2) - 0x1p-126f) break;
-      }
-      // Rows ya..yb over columns xa..xb as row runs; once the square is 8
-      // cells out, each stretch of 8 rows whose occupancy blocks over those
-      // columns hold no point is skipped.
-      // With a full heap, rows and columns beyond the k-th key's reach are
-      // dropped first, and each row keeps only the columns its chord reaches.
-      auto row = [&](int yy, int xa, int xb, auto&& fn) {
+    // r = -1 stands for the query's own cell; then square r grows to r2.
+    for (int r = -1;;) {
+      if (r >= 0) {
+        const bool open_l = cx - r > 0, open_r = cx + r < g.gx - 1;
+        const bool open_b = cy - r > 0, open_t = cy + r < g.gy - 1;
+        if (!(open_l || open_r || open_b || open_t)) break;  // the square covers the grid
         if (hp.size == k) {
-          const float gap = fmaxf(0.f, fmaxf(float(yy) - v, v - float(yy + 1)) - mg);
-          const float w2 = reach2(), g2 = __fmul_rd(gap, gap);
-          if (g2 > w2) return;
-          clip(u, __fsqrt_ru(__fsub_ru(w2, g2)), xa, xb);
-          if (xa > xb) return;
+          float l2 = INFINITY;
+          if (open_l) {
+            const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
+            l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+          }
+          if (open_r) {
+            const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
+            l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+          }
+          if (open_b) {
+            const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
+            l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+          }
+          if (open_t) {
+            const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
+            l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+          }
+          if (key_d2(worst) < __fmul_rd(l2, h2) - 0x1p-126f) break;
         }
-        fn(yy, xa, xb);
-      };
-      auto rows = [&](int ya, int yb, int xa, int xb, auto&& fn) {
-        if (xa > xb || ya > yb) return;  // then 0 <= ya <= yb < gy, 0 <= xa <= xb < gx
-        if (hp.size == k) {  // narrows the ranges (or empties them)
-          const float e = __fsqrt_ru(reach2());
-          clip(v, e, ya, yb);
-          clip(u, e, xa, xb);
-          if (xa > xb || ya > yb) return;
-        }
-        if (r < 8) {  // near the query the blocks are rarely empty: skip no checks
-          for (int yy = ya; yy <= yb; ++yy) row(yy, xa, xb, fn);
-          return;
-        }
-        for (int by = ya >> kBlockShift; by <= (yb >> kBlockShift); ++by) {
-          const int32_t* bp = bpre + by * (kMaxBlocksPerAxis + 1);
-          if (!dcheck(by < kMaxBlocksPerAxis && (xb >> kBlockShift) < kMaxBlocksPerAxis,
-                      kSiteBlock))
-            continue;
-          if (bp[(xb >> kBlockShift) + 1] == bp[xa >> kBlockShift]) continue;
-          const int y1 = min(yb, (by << kBlockShift) + 7);
-          for (int yy = max(ya, by << kBlockShift); yy <= y1; ++yy) row(yy, xa, xb, fn);
-        }
-      };
-      // The cells between squares r and r2: side strips of the rows already
-      // in the square, then new rows below and above.
-      auto band = [&](int r2, auto&& fn) {
-        const int y0 = max(0, cy - r), y1 = min(g.gy - 1, cy + r);
-        rows(y0, y1, max(0, cx - r2), cx - r - 1, fn);
-        rows(y0, y1, cx + r + 1, min(g.gx - 1, cx + r2), fn);
-        const int xa = max(0, cx - r2), xb = min(g.gx - 1, cx + r2);
-        rows(max(0, cy - r2), min(g.gy - 1, cy - r - 1), xa, xb, fn);
-        rows(max(0, cy + r + 1), min(g.gy - 1, cy + r2), xa, xb, fn);
-      };
+      }
       // Grow by max(1, r/2), halved while the band would hold more than 4k
       // points (a step from empty space into a dense cluster stays short).
       // From r = 4 on (steps of 2 or more), the band's count comes from the
       // summed-area table and an empty band is not walked.
       int r2 = r + max(1, r >> 1);
+      bool walk = true;
       if (r >= 4) {
         if (in_square < 0) in_square = square_count(r);
         int c2 = square_count(r2);
@@ -861,10 +821,65 @@ __global__ void __launch_bounds__(kKnnThreads)
           r2 = r + max(1, (r2 - r) >> 1);
           c2 = square_count(r2);
         }
-        if (c2 != in_square) band(r2, run);
+        walk = c2 != in_square;
         in_square = c2;
-      } else {
-        band(r2, run);
+      }
+      // The cells between squares r and r2 in four parts: the side strips of
+      // the rows already in the square, then the new rows below and above.
+      // One loop walks every part, so the candidate code exists once.
+#pragma unroll 1
+      for (int part = 0; walk && part < 4; ++part) {
+        int ya, yb, xa, xb;
+        if (r < 0) {
+          if (part > 0) break;
+          ya = yb = cy;
+          xa = xb = cx;
+        } else if (part < 2) {
+          ya = max(0, cy - r);
+          yb = min(g.gy - 1, cy + r);
+          xa = part == 0 ? max(0, cx - r2) : cx + r + 1;
+          xb = part == 0 ? cx - r - 1 : min(g.gx - 1, cx + r2);
+        } else {
+          xa = max(0, cx - r2);
+          xb = min(g.gx - 1, cx + r2);
+          ya = part == 2 ? max(0, cy - r2) : cy + r + 1;
+          yb = part == 2 ? cy - r - 1 : min(g.gy - 1, cy + r2);
+        }
+        if (xa > xb || ya > yb) continue;  // then 0 <= ya <= yb < gy, 0 <= xa <= xb < gx
+        // With a full heap, rows and columns beyond the k-th key's reach are
+        // dropped first (the ranges only narrow, or empty).
+        if (hp.size == k) {
+          const float e = __fsqrt_ru(reach2());
+          clip(v, e, ya, yb);
+          clip(u, e, xa, xb);
+          if (xa > xb || ya > yb) continue;
+        }
+        // Once the square is 8 cells out, each stretch of 8 rows whose
+        // occupancy blocks over xa..xb hold no point is skipped.
+        const bool check_blocks = r >= 8;
+        for (int y8 = ya; y8 <= yb;) {
+          const int y1 = check_blocks ? min(yb, y8 | 7) : yb;
+          bool occupied = true;
+          if (check_blocks) {
+            const int by = y8 >> kBlockShift;
+            const int32_t* bp = bpre + by * (kMaxBlocksPerAxis + 1);
+            occupied = dcheck(by < kMaxBlocksPerAxis && (xb >> kBlockShift) < kMaxBlocksPerAxis,
+                              kSiteBlock) &&
+                       bp[(xb >> kBlockShift) + 1] != bp[xa >> kBlockShift];
+          }
+          for (int yy = y8; occupied && yy <= y1; ++yy) {
+            int ra = xa, rb = xb;
+            if (hp.size == k) {  // the columns this row's chord reaches
+              const float gap = fmaxf(0.f, fmaxf(float(yy) - v, v - float(yy + 1)) - mg);
+              const float w2 = reach2(), g2 = __fmul_rd(gap, gap);
+              if (g2 > w2) continue;
+              clip(u, __fsqrt_ru(__fsub_ru(w2, g2)), ra, rb);
+              if (ra > rb) continue;
+            }
+            run(yy, ra, rb);
+          }
+          y8 = y1 + 1;
+        }
       }
       r = r2;
     }
