@@ -433,9 +433,11 @@ idw_status idw_interpolate_local(idw_handle_t handle, const float *data_xyz, int
  *
  * Method, on `stream` without host synchronisation (graph-capturable): the
  * grid build of idw_interpolate_local with cells sized for k points at the
- * data's mean density, then one thread per query (in cell order) searches
- * square rings of cells around the grid cell nearest to it, keeping the k
- * best keys in shared memory, and stops once the k-th key is below a
+ * data's mean density, then one thread per query (in cell order) grows a
+ * square of cells around the grid cell nearest to it, keeping the k best
+ * keys in shared memory.  Band sizes come from a summed-area table of the
+ * cells; once k keys are held, cells whose points provably lie beyond the
+ * k-th key are skipped; the search stops once the k-th key is below a
  * conservative FP32 lower bound on the key of any point not yet seen.
  * Workspace as idw_interpolate_local.  Errors as in idw_interpolate, plus
  * IDW_ERR_INVALID_ARG for k outside [1, 64].
@@ -443,6 +445,60 @@ idw_status idw_interpolate_local(idw_handle_t handle, const float *data_xyz, int
 idw_status idw_interpolate_knn(idw_handle_t handle, const float *data_xyz, int64_t n,
                                const float *queries_xy, int64_t m, double p, int32_t k,
                                float *out, int32_t *nbr_out, float *kd2_out, void *stream);
+
+/*
+ * Prepared index of the local forms: the data side of idw_interpolate_local
+ * or idw_interpolate_knn (bounding box, grid plan, counting sort of the
+ * data, and for k-NN the cell-count tables) built once, then queried by any
+ * number of calls that each sort only their own queries.  Results are those
+ * of the one-shot calls on the same data: the same members and neighbour
+ * lists, values within the last bits (candidate order within a cell may
+ * differ).
+ *
+ * idw_local_index_create builds an index over `data_xyz` (device float
+ * n x 3, as in idw_interpolate) for exactly one form:
+ *   radius > 0 and k == 0      : a radius index (cells for radius R; R may
+ *                                be +inf, which gives the global form);
+ *   radius == 0, 1 <= k <= 64  : a k-NN index (cells for k neighbours).
+ * The index copies what it needs (sorted records; for k-NN also the data),
+ * so `data_xyz` may be freed or changed once the build has run.  It owns
+ * device memory on the handle's device (about 16 bytes per data point and
+ * 8 per cell; k-NN adds 12 per data point, 4 per cell and 264 KB), allocated
+ * here (cudaMalloc, so the call cannot be captured).  The build is enqueued
+ * on `stream`: order later queries on other streams after it.  With
+ * IDW_OPT_VALIDATE_INPUTS set the data are scanned first.  Errors:
+ * IDW_ERR_INVALID_ARG (null handle, index or data, n outside [1, 2^31),
+ * a bad radius / k combination), IDW_ERR_ALIGNMENT, IDW_ERR_WORKSPACE (the
+ * allocation failed), IDW_ERR_NOT_FINITE_INPUT, IDW_ERR_CUDA.
+ *
+ * idw_local_index_interpolate is idw_interpolate_local on a radius index,
+ * for any 0 < radius <= the build radius (a smaller radius still uses the
+ * build's cells).  idw_local_index_knn is idw_interpolate_knn on a k-NN
+ * index, for any 1 <= k <= 64.  Outputs, NaN and hit rules are those of
+ * the one-shot calls.  Both run on `stream` without host synchronisation
+ * (graph-capturable once the handle's workspace has grown) and take the
+ * handle's workspace: 16 bytes per query and 8 per cell.  The handle must be
+ * on the index's device; calling the wrong form's query on an index, a
+ * radius above the build radius or k outside [1, 64] gives
+ * IDW_ERR_INVALID_ARG.  Several handles (one per stream) may query one
+ * index at the same time: queries only read it.
+ *
+ * idw_local_index_destroy frees the index (cudaFree: the device is
+ * synchronised first).  Destroying NULL returns IDW_ERR_INVALID_ARG.
+ */
+typedef struct idw_local_index_s *idw_local_index_t;
+
+idw_status idw_local_index_create(idw_handle_t handle, const float *data_xyz, int64_t n,
+                                  double radius, int32_t k, idw_local_index_t *index,
+                                  void *stream);
+idw_status idw_local_index_interpolate(idw_handle_t handle, idw_local_index_t index,
+                                       const float *queries_xy, int64_t m, double p,
+                                       double radius, float *out, int32_t *count_out,
+                                       void *stream);
+idw_status idw_local_index_knn(idw_handle_t handle, idw_local_index_t index,
+                               const float *queries_xy, int64_t m, double p, int32_t k,
+                               float *out, int32_t *nbr_out, float *kd2_out, void *stream);
+idw_status idw_local_index_destroy(idw_local_index_t index);
 
 #ifdef __cplusplus
 }

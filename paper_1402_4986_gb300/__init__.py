@@ -21,7 +21,8 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
-    "interpolate_batched", "interpolate_local", "interpolate_knn", "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
+    "interpolate_batched", "interpolate_local", "interpolate_knn", "LocalIndex",
+    "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
@@ -252,6 +253,93 @@ def interpolate_knn(data, queries, p: float = 2.0, k: int = 16, out=None,
     _lib.check(st, "idw_interpolate_knn", h.ptr)
     res = (out,) + ((nbr,) if neighbours else ()) + ((kd2,) if kth_d2 else ())
     return res if len(res) > 1 else out
+
+
+class LocalIndex:
+    """Prepared index of a local form (``idw_local_index_create``): the data
+    side is built once, then each call sorts only its own queries.
+
+    ``LocalIndex(data, radius=R)`` serves ``interpolate`` for any radius up
+    to R; ``LocalIndex(data, k=K)`` serves ``knn`` for any 1 <= k <= 64 (its
+    cells are sized for K).  Results equal the one-shot
+    ``interpolate_local`` / ``interpolate_knn`` on the same data.  The index
+    copies what it needs, so ``data`` may change after construction.
+    """
+
+    def __init__(self, data, radius: float | None = None, k: int | None = None,
+                 handle: Handle | None = None):
+        if (radius is None) == (k is None):
+            raise ValueError("give exactly one of radius or k")
+        if data.dim() != 2 or data.shape[1] != 3 or not data.is_cuda:
+            raise ValueError("data must be a CUDA (n, 3) tensor")
+        if data.dtype != torch.float32 or not data.is_contiguous():
+            raise ValueError("data must be contiguous float32")
+        self.handle = handle or get_handle(data.device)
+        self.device = data.device
+        self.radius = None if radius is None else float(radius)
+        self.k = None if k is None else int(k)
+        self.n = data.shape[0]
+        ix = ctypes.c_void_p()
+        st = self.handle.lib.idw_local_index_create(
+            self.handle.ptr, _ptr(data), self.n, 0.0 if radius is None else float(radius),
+            0 if k is None else int(k), ctypes.byref(ix), _stream(data))
+        _lib.check(st, "idw_local_index_create", self.handle.ptr)
+        self.ptr = ix
+
+    def _queries(self, queries):
+        if queries.dim() != 2 or queries.shape[1] != 2 or not queries.is_cuda:
+            raise ValueError("queries must be a CUDA (m, 2) tensor")
+        if queries.dtype != torch.float32 or not queries.is_contiguous():
+            raise ValueError("queries must be contiguous float32")
+        if queries.device != self.device:
+            raise ValueError("queries must be on the index's device")
+        return queries.shape[0]
+
+    def interpolate(self, queries, p: float = 2.0, radius: float | None = None, out=None,
+                    counts: bool = False, handle: Handle | None = None):
+        """``interpolate_local`` on the indexed data (radius defaults to the
+        build radius and may not exceed it).  ``handle`` (default: the
+        build's) supplies the workspace: one handle per concurrent stream."""
+        m = self._queries(queries)
+        h = handle or self.handle
+        r = self.radius if radius is None else float(radius)
+        if out is None:
+            out = torch.empty(m, dtype=torch.float32, device=self.device)
+        cnt = torch.empty(m, dtype=torch.int32, device=self.device) if counts else None
+        st = h.lib.idw_local_index_interpolate(
+            h.ptr, self.ptr, _ptr(queries), m, float(p), 0.0 if r is None else r,
+            _ptr(out), _ptr(cnt), _stream(queries))
+        _lib.check(st, "idw_local_index_interpolate", h.ptr)
+        return (out, cnt) if counts else out
+
+    def knn(self, queries, p: float = 2.0, k: int | None = None, out=None,
+            neighbours: bool = False, kth_d2: bool = False, handle: Handle | None = None):
+        """``interpolate_knn`` on the indexed data (k defaults to the build k;
+        ``handle`` as in ``interpolate``)."""
+        m = self._queries(queries)
+        h = handle or self.handle
+        kk = int(k) if k is not None else (self.k or 0)  # 0: refused by the library
+        if out is None:
+            out = torch.empty(m, dtype=torch.float32, device=self.device)
+        nbr = torch.empty(m, max(kk, 1), dtype=torch.int32, device=self.device) if neighbours else None
+        kd2 = torch.empty(m, dtype=torch.float32, device=self.device) if kth_d2 else None
+        st = h.lib.idw_local_index_knn(
+            h.ptr, self.ptr, _ptr(queries), m, float(p), kk, _ptr(out), _ptr(nbr),
+            _ptr(kd2), _stream(queries))
+        _lib.check(st, "idw_local_index_knn", h.ptr)
+        res = (out,) + ((nbr,) if neighbours else ()) + ((kd2,) if kth_d2 else ())
+        return res if len(res) > 1 else out
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self.handle.lib.idw_local_index_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=True,

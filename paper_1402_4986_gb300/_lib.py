@@ -91,6 +91,13 @@ SIGNATURES = {
     "idw_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.c_char_p]),
     "idw_interpolate_knn": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                     c_int32, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "idw_local_index_create": (c_int, [c_void_p, c_void_p, c_int64, c_double, c_int32,
+                                       ctypes.POINTER(c_void_p), c_void_p]),
+    "idw_local_index_interpolate": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double,
+                                            c_double, c_void_p, c_void_p, c_void_p]),
+    "idw_local_index_knn": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_int32,
+                                    c_void_p, c_void_p, c_void_p, c_void_p]),
+    "idw_local_index_destroy": (c_int, [c_void_p]),
 }
 
 _lock = threading.Lock()

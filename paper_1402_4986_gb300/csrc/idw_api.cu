@@ -47,6 +47,15 @@ struct idw_handle_s {
   size_t events_used = 0;
 };
 
+// A prepared index of the local forms (idw_local_index_create).
+struct idw_local_index_s {
+  int device = 0;
+  double radius = 0.0;  // > 0: a radius index built for this radius
+  int k = 0;            // > 0: a k-NN index built for k neighbours
+  idw::IndexLayout X;
+  void* mem = nullptr;  // device buffer laid out by X
+};
+
 namespace {
 
 using idw::Plan;
@@ -666,6 +675,100 @@ idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, con
   const cudaError_t e = idw::launch_knn(data, n, queries, m, p, k, out, nbr_out, kd2_out, h->ws, L,
                                         h->sm_count, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+idw_status idw_local_index_create(idw_handle_t h, const float* data, int64_t n, double radius,
+                                  int32_t k, idw_local_index_t* index, void* stream) {
+  NvtxRange nvtx("idw_local_index_create");
+  if (!h || !index || !data) return IDW_ERR_INVALID_ARG;
+  *index = nullptr;
+  if (n < 1 || n >= kMaxCount) return IDW_ERR_INVALID_ARG;
+  const bool knn = radius == 0.0 && k >= 1 && k <= idw::kKnnMax;
+  const bool rad = radius > 0.0 && k == 0;  // NaN fails both
+  if (!knn && !rad) return IDW_ERR_INVALID_ARG;
+  if (!aligned(data, 4)) return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  idw_status st = validate_inputs(h, {{data, 3 * n, false}}, s);
+  if (st != IDW_OK) return st;
+  idw_local_index_t ix = new idw_local_index_s();
+  ix->device = h->device;
+  ix->radius = rad ? radius : 0.0;
+  ix->k = knn ? k : 0;
+  ix->X = idw::index_layout(n, knn);
+  cudaError_t e = cudaMalloc(&ix->mem, ix->X.bytes);
+  if (e != cudaSuccess) {
+    cuda_fail(h, e);
+    delete ix;
+    return IDW_ERR_WORKSPACE;
+  }
+  e = idw::launch_index_build(data, n, rad ? radius : 0.0, ix->k, ix->mem, ix->X, h->sm_count, s);
+  if (e != cudaSuccess) {
+    cudaFree(ix->mem);
+    delete ix;
+    return cuda_fail(h, e);
+  }
+  *index = ix;
+  return IDW_OK;
+}
+
+idw_status idw_local_index_interpolate(idw_handle_t h, idw_local_index_t ix,
+                                       const float* queries, int64_t m, double p, double radius,
+                                       float* out, int32_t* count_out, void* stream) {
+  NvtxRange nvtx("idw_local_index_interpolate");
+  if (!h || !ix || ix->radius <= 0.0 || h->device != ix->device) return IDW_ERR_INVALID_ARG;
+  if (m < 0 || m >= kMaxCount || !(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
+  if (!(radius > 0.0 && radius <= ix->radius)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (!queries || !out) return IDW_ERR_INVALID_ARG;
+  if (!aligned(queries, 4) || !aligned(out, 4) || (count_out && !aligned(count_out, 4)))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  idw_status st = validate_inputs(h, {{queries, 2 * m, false}}, s);
+  if (st != IDW_OK) return st;
+  const idw::QueryLayout Q = idw::query_layout(m, ix->X.max_cells);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_index_local(ix->mem, ix->X, queries, m, p, radius, out,
+                                                count_out, h->ws, Q, h->sm_count, s);
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+idw_status idw_local_index_knn(idw_handle_t h, idw_local_index_t ix, const float* queries,
+                               int64_t m, double p, int32_t k, float* out, int32_t* nbr_out,
+                               float* kd2_out, void* stream) {
+  NvtxRange nvtx("idw_local_index_knn");
+  if (!h || !ix || ix->k <= 0 || h->device != ix->device) return IDW_ERR_INVALID_ARG;
+  if (m < 0 || m >= kMaxCount || !(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
+  if (k < 1 || k > idw::kKnnMax) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (!queries || !out) return IDW_ERR_INVALID_ARG;
+  if (!aligned(queries, 4) || !aligned(out, 4) || (nbr_out && !aligned(nbr_out, 4)) ||
+      (kd2_out && !aligned(kd2_out, 4)))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  idw_status st = validate_inputs(h, {{queries, 2 * m, false}}, s);
+  if (st != IDW_OK) return st;
+  const idw::QueryLayout Q = idw::query_layout(m, ix->X.max_cells);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_index_knn(ix->mem, ix->X, queries, m, p, k, out, nbr_out,
+                                              kd2_out, h->ws, Q, h->sm_count, s);
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+idw_status idw_local_index_destroy(idw_local_index_t ix) {
+  if (!ix) return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(ix->device);
+  cudaDeviceSynchronize();
+  if (ix->mem) cudaFree(ix->mem);
+  delete ix;
+  return IDW_OK;
 }
 
 idw_status idw_sync_status(idw_handle_t h, void* stream) {

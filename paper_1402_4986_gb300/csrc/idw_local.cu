@@ -301,9 +301,10 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp
   return (wid > 0 ? warp_tot[wid - 1] : 0) + incl - v;
 }
 
-// Exclusive scan of both histograms (blockIdx.y: 0 data, 1 queries), one
-// tile of kScanTile entries per block (four consecutive entries per thread),
-// over cells + 1 entries.  Each tile writes its local prefix to starts[],
+// Exclusive scan of the histograms (half = first + blockIdx.y: 0 data,
+// 1 queries; launched with gridDim.y = 2 for both, 1 for one), one tile of
+// kScanTile entries per block (four consecutive entries per thread), over
+// cells + 1 entries.  Each tile writes its local prefix to starts[],
 // clears the counts (they become the scatter cursors) and records its total;
 // the block that finishes last turns the totals into tile bases (exclusive
 // scan in place), so that a cell starts at starts[i] + base[i / kScanTile].
@@ -311,14 +312,16 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* warp
 __global__ void __launch_bounds__(kScanBlock)
     scan_kernel(GridDev* __restrict__ grid, int32_t* __restrict__ counts_d,
                 int32_t* __restrict__ counts_q, int32_t* __restrict__ starts_d,
-                int32_t* __restrict__ starts_q, int32_t* __restrict__ sums, int max_tiles) {
+                int32_t* __restrict__ starts_q, int32_t* __restrict__ sums, int max_tiles,
+                int first) {
   __shared__ int32_t warp_tot[kScanBlock / 32];
   __shared__ bool last;
   const int len = grid->cells + 1;
   const int ntiles = (len + kScanTile - 1) / kScanTile;
   if (int(blockIdx.x) >= ntiles) return;  // tile beyond the grid
-  int4* in = reinterpret_cast<int4*>(blockIdx.y ? counts_q : counts_d);
-  int4* out = reinterpret_cast<int4*>(blockIdx.y ? starts_q : starts_d);
+  const int half = first + int(blockIdx.y);
+  int4* in = reinterpret_cast<int4*>(half ? counts_q : counts_d);
+  int4* out = reinterpret_cast<int4*>(half ? starts_q : starts_d);
   const int i4 = blockIdx.x * kScanBlock + threadIdx.x;  // int4 index
   int4 v = make_int4(0, 0, 0, 0);
   if (4 * i4 < len) {
@@ -331,13 +334,13 @@ __global__ void __launch_bounds__(kScanBlock)
   if (4 * i4 < len)
     out[i4] = make_int4(before, before + v.x, before + v.x + v.y, before + v.x + v.y + v.z);
   if (threadIdx.x == 0) {
-    sums[blockIdx.y * max_tiles + blockIdx.x] = total;  // published by the ticket
-    last = ticket_acq_rel(&grid->scan_ticket) + 1u == unsigned(2 * ntiles - 1);
+    sums[half * max_tiles + blockIdx.x] = total;  // published by the ticket
+    last = ticket_acq_rel(&grid->scan_ticket) + 1u == unsigned(int(gridDim.y) * ntiles - 1);
   }
   __syncthreads();  // the last block's threads read after thread 0's acquire
   if (!last) return;
   const int per = (ntiles + kScanBlock - 1) / kScanBlock;
-  for (int y = 0; y < 2; ++y) {
+  for (int y = first; y < first + int(gridDim.y); ++y) {
     int32_t* sb = sums + y * max_tiles;
     const int b0 = min(ntiles, int(threadIdx.x) * per), b1 = min(ntiles, b0 + per);
     int32_t acc = 0;
@@ -1005,7 +1008,7 @@ cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries,
   const unsigned pgrid = static_cast<unsigned>((n + m + 255) / 256);
   count_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, counts_d, counts_q);
   scan_kernel<<<dim3(max_tiles, 2), kScanBlock, 0, s>>>(grid, counts_d, counts_q, starts_d,
-                                                        starts_q, sums, max_tiles);
+                                                        starts_q, sums, max_tiles, 0);
   scatter_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, starts_d, starts_q, sums,
                                        max_tiles, counts_d, counts_q, sorted, qrec);
   return cudaGetLastError();
@@ -1082,6 +1085,179 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
         grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// Copies an index's plan into a query call's scratch with the tickets reset.
+// For the radius form (radius > 0) the reach is recomputed for the call's
+// radius, which the host has checked is at most the build radius, so rho
+// stays below 2 and the coverage argument of the plan still holds.
+__global__ void index_prep_kernel(const GridDev* __restrict__ src, GridDev* __restrict__ dst,
+                                  double radius) {
+  GridDev g = *src;
+  g.box_ticket = 0xffffffffu;
+  g.scan_ticket = 0xffffffffu;
+  if (radius > 0.0 && g.inv2 > 0.f)
+    g.rho = __fmaf_ru(__fmul_ru(__double2float_ru(radius), g.inv2), 0.5f + 0x1p-9f, 0x1p-8f);
+  *dst = g;
+}
+
+// Query side of a call on a prepared index: plan copy, then the counting
+// sort of the queries alone (the scan runs its query half only).
+cudaError_t launch_query_sort(const GridDev* xgrid, const float* queries, int64_t m, double radius,
+                              int64_t max_cells, void* workspace, const QueryLayout& Q,
+                              int sm_count, cudaStream_t s) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  GridDev* grid = reinterpret_cast<GridDev*>(ws + Q.off_grid);
+  int32_t* counts = reinterpret_cast<int32_t*>(ws + Q.off_counts);
+  int32_t* starts = reinterpret_cast<int32_t*>(ws + Q.off_starts);
+  int32_t* sums = reinterpret_cast<int32_t*>(ws + Q.off_sums);
+  float4* qrec = reinterpret_cast<float4*>(ws + Q.off_qrec);
+  const int max_tiles = scan_tiles_of(max_cells);
+  index_prep_kernel<<<1, 1, 0, s>>>(xgrid, grid, radius);
+  const unsigned zgrid = static_cast<unsigned>(
+      std::min<int64_t>(int64_t(sm_count) * 8, (max_cells + 4 + 255) / 256));
+  zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts, counts);
+  const unsigned qgrid = static_cast<unsigned>((m + 255) / 256);
+  count_kernel<<<qgrid, 256, 0, s>>>(grid, nullptr, 0, queries, m, counts, counts);
+  scan_kernel<<<dim3(max_tiles, 1), kScanBlock, 0, s>>>(grid, counts, counts, starts, starts, sums,
+                                                        max_tiles, 1);
+  scatter_kernel<<<qgrid, 256, 0, s>>>(grid, nullptr, 0, queries, m, starts, starts, sums,
+                                       max_tiles, counts, counts, nullptr, qrec);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+IndexLayout index_layout(int64_t n, bool knn) {
+  IndexLayout X;
+  X.n = n;
+  X.knn = knn;
+  X.max_cells = local_max_cells(n);
+  const size_t len = size_t(X.max_cells + 1 + 3) / 4 * 16;  // whole int4s
+  size_t off = 0;
+  X.off_grid = off;    off += round_up(sizeof(GridDev), 256);
+  X.off_counts = off;  off += round_up(len, 256);
+  X.off_starts = off;  off += round_up(len, 256);
+  X.off_sums = off;    off += round_up(size_t(scan_tiles_of(X.max_cells)) * 4, 256);
+  X.off_sorted = off;  off += round_up(size_t(n) * 16, 256);
+  if (knn) {
+    X.off_data = off;  off += round_up(size_t(n) * 12, 256);
+    X.off_bpre = off;  off += round_up(size_t(kMaxBlocksPerAxis) * (kMaxBlocksPerAxis + 1) * 4, 256);
+    X.off_sat = off;   off += round_up(size_t(X.max_cells + 2 * kMaxCellsPerAxis + 1) * 4, 256);
+  }
+  X.bytes = off;
+  return X;
+}
+
+QueryLayout query_layout(int64_t m, int64_t max_cells) {
+  QueryLayout Q;
+  const size_t len = size_t(max_cells + 1 + 3) / 4 * 16;
+  size_t off = 0;
+  Q.off_grid = off;    off += round_up(sizeof(GridDev), 256);
+  Q.off_counts = off;  off += round_up(len, 256);
+  Q.off_starts = off;  off += round_up(len, 256);
+  Q.off_sums = off;    off += round_up(size_t(2 * scan_tiles_of(max_cells)) * 4, 256);
+  Q.off_qrec = off;    off += round_up(size_t(m) * 16, 256);
+  Q.bytes = off;
+  return Q;
+}
+
+cudaError_t launch_index_build(const float* data, int64_t n, double radius, int knn_k,
+                               void* index_mem, const IndexLayout& X, int sm_count,
+                               cudaStream_t s) {
+  unsigned char* mem = static_cast<unsigned char*>(index_mem);
+  GridDev* grid = reinterpret_cast<GridDev*>(mem + X.off_grid);
+  int32_t* counts = reinterpret_cast<int32_t*>(mem + X.off_counts);
+  int32_t* starts = reinterpret_cast<int32_t*>(mem + X.off_starts);
+  int32_t* sums = reinterpret_cast<int32_t*>(mem + X.off_sums);
+  float4* sorted = reinterpret_cast<float4*>(mem + X.off_sorted);
+  const int max_tiles = scan_tiles_of(X.max_cells);
+  cudaError_t e = cudaMemsetAsync(grid, 0xff, sizeof(GridDev), s);
+  if (e != cudaSuccess) return e;
+  const unsigned bgrid = static_cast<unsigned>(
+      std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count) * 4, (n + 255) / 256)));
+  box_plan_kernel<<<bgrid, 256, 0, s>>>(data, n, grid, radius, 1.0 / double(X.max_cells), knn_k);
+  const unsigned zgrid = static_cast<unsigned>(
+      std::min<int64_t>(int64_t(sm_count) * 8, (X.max_cells + 4 + 255) / 256));
+  zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts, counts);
+  const unsigned dgrid = static_cast<unsigned>((n + 255) / 256);
+  count_kernel<<<dgrid, 256, 0, s>>>(grid, data, n, nullptr, 0, counts, counts);
+  scan_kernel<<<dim3(max_tiles, 1), kScanBlock, 0, s>>>(grid, counts, counts, starts, starts, sums,
+                                                        max_tiles, 0);
+  scatter_kernel<<<dgrid, 256, 0, s>>>(grid, data, n, nullptr, 0, starts, starts, sums, max_tiles,
+                                       counts, counts, sorted, nullptr);
+  if (X.knn) {
+    e = cudaMemcpyAsync(mem + X.off_data, data, size_t(n) * 12, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    int32_t* bpre = reinterpret_cast<int32_t*>(mem + X.off_bpre);
+    int32_t* sat = reinterpret_cast<int32_t*>(mem + X.off_sat);
+    block_prefix_kernel<<<kMaxBlocksPerAxis, kMaxBlocksPerAxis, 0, s>>>(grid, starts, sums, bpre);
+    sat_kernel<<<(kMaxCellsPerAxis + 1 + kSatCols - 1) / kSatCols, kSatCols * kSatWarps, 0, s>>>(
+        grid, starts, sums, sat);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
+                               int64_t m, double p, double radius, float* out, int32_t* count_out,
+                               void* workspace, const QueryLayout& Q, int sm_count,
+                               cudaStream_t s) {
+  const unsigned char* mem = static_cast<const unsigned char*>(index_mem);
+  const GridDev* xgrid = reinterpret_cast<const GridDev*>(mem + X.off_grid);
+  cudaError_t e = launch_query_sort(xgrid, queries, m, radius, X.max_cells, workspace, Q, sm_count, s);
+  if (e != cudaSuccess) return e;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const GridDev* grid = reinterpret_cast<const GridDev*>(ws + Q.off_grid);
+  const float4* qrec = reinterpret_cast<const float4*>(ws + Q.off_qrec);
+  const int32_t* starts = reinterpret_cast<const int32_t*>(mem + X.off_starts);
+  const int32_t* sums = reinterpret_cast<const int32_t*>(mem + X.off_sums);
+  const float4* sorted = reinterpret_cast<const float4*>(mem + X.off_sorted);
+  const float r2f = static_cast<float>(radius * radius);
+  const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
+  const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
+  if (p == 2.0)
+    local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out);
+  else
+    local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const float* queries,
+                             int64_t m, double p, int k, float* out, int32_t* nbr_out,
+                             float* kd2_out, void* workspace, const QueryLayout& Q, int sm_count,
+                             cudaStream_t s) {
+  const size_t smem = knn_smem_bytes(k);
+  cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(knn_query_kernel<kPowGeneral>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const unsigned char* mem = static_cast<const unsigned char*>(index_mem);
+  const GridDev* xgrid = reinterpret_cast<const GridDev*>(mem + X.off_grid);
+  e = launch_query_sort(xgrid, queries, m, 0.0, X.max_cells, workspace, Q, sm_count, s);
+  if (e != cudaSuccess) return e;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const GridDev* grid = reinterpret_cast<const GridDev*>(ws + Q.off_grid);
+  const float4* qrec = reinterpret_cast<const float4*>(ws + Q.off_qrec);
+  const int32_t* starts = reinterpret_cast<const int32_t*>(mem + X.off_starts);
+  const int32_t* sums = reinterpret_cast<const int32_t*>(mem + X.off_sums);
+  const float4* sorted = reinterpret_cast<const float4*>(mem + X.off_sorted);
+  const float* data = reinterpret_cast<const float*>(mem + X.off_data);
+  const int32_t* bpre = reinterpret_cast<const int32_t*>(mem + X.off_bpre);
+  const int32_t* sat = reinterpret_cast<const int32_t*>(mem + X.off_sat);
+  const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
+  if (p == 2.0)
+    knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
+        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out);
+  else
+    knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
+        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out);
   return cudaGetLastError();
 }
 

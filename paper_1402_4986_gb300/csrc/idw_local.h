@@ -40,4 +40,44 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s);
 
+// A prepared index: the data side of a local form built once and queried
+// by many calls.  The index's own buffer holds the plan, the data cell
+// starts and tile bases, the sorted records, and for k-NN a copy of the data
+// (read by original index), the occupancy-block prefix and the
+// summed-area table.
+struct IndexLayout {
+  int64_t n = 0, max_cells = 0;
+  bool knn = false;
+  size_t off_grid = 0, off_counts = 0, off_starts = 0, off_sums = 0, off_sorted = 0;
+  size_t off_data = 0, off_bpre = 0, off_sat = 0;
+  size_t bytes = 0;
+};
+IndexLayout index_layout(int64_t n, bool knn);
+
+// Scratch of one query call on a prepared index (in the handle's workspace).
+struct QueryLayout {
+  size_t off_grid = 0, off_counts = 0, off_starts = 0, off_sums = 0, off_qrec = 0;
+  size_t bytes = 0;
+};
+QueryLayout query_layout(int64_t m, int64_t max_cells);
+
+// Enqueues the data side: bounding box, plan (cells for `radius`, or for k
+// neighbours when knn_k > 0), counting sort of the data, and for k-NN the
+// data copy and both count tables.
+cudaError_t launch_index_build(const float* data, int64_t n, double radius, int knn_k,
+                               void* index_mem, const IndexLayout& X, int sm_count,
+                               cudaStream_t s);
+
+// One query call on a radius index (0 < radius <= the build radius).
+cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
+                               int64_t m, double p, double radius, float* out, int32_t* count_out,
+                               void* workspace, const QueryLayout& Q, int sm_count,
+                               cudaStream_t s);
+
+// One query call on a k-NN index (1 <= k <= kKnnMax).
+cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const float* queries,
+                             int64_t m, double p, int k, float* out, int32_t* nbr_out,
+                             float* kd2_out, void* workspace, const QueryLayout& Q, int sm_count,
+                             cudaStream_t s);
+
 }  // namespace idw

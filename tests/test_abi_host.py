@@ -58,6 +58,12 @@ def test_null_handle_is_rejected(lib):
     assert lib.idw_sync_status(None, None) == 1
     assert lib.idw_interpolate_local(None, None, 10, None, 10, 2.0, 0.1, None, None, None) == 1
     assert lib.idw_interpolate_knn(None, None, 10, None, 10, 2.0, 4, None, None, None, None) == 1
+    ix = ctypes.c_void_p()
+    assert lib.idw_local_index_create(None, None, 10, 0.1, 0, ctypes.byref(ix), None) == 1
+    assert not ix.value
+    assert lib.idw_local_index_interpolate(None, None, None, 10, 2.0, 0.1, None, None, None) == 1
+    assert lib.idw_local_index_knn(None, None, None, 10, 2.0, 4, None, None, None, None) == 1
+    assert lib.idw_local_index_destroy(None) == 1
     out = ctypes.c_void_p()
     assert lib.idw_create(None, 0) == 1
 
@@ -149,3 +155,7 @@ def test_binding_rejects_host_tensors_for_device_entry():
         idw.interpolate_local(d, q, 2.0, 0.1)
     with pytest.raises(ValueError):
         idw.interpolate_knn(d, q, 2.0, 4)
+    with pytest.raises(ValueError):
+        idw.LocalIndex(d, radius=0.1)
+    with pytest.raises(ValueError):
+        idw.LocalIndex(d, radius=0.1, k=4)

@@ -49,10 +49,15 @@ for name, data, q in cases:
     Z, cnt = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True)
     Zo, _, co = oracle.idw_local(data, q, 2.0, 0.03)
     assert np.array_equal(cnt.cpu().numpy(), co), name
+    _, cnt_ix = idw.LocalIndex(d, radius=0.03).interpolate(qq, 2.0, 0.02, counts=True)
+    assert np.array_equal(cnt_ix.cpu().numpy(), oracle.idw_local(data, q, 2.0, 0.02)[2]), name
+    kix = idw.LocalIndex(d, k=9)
     for k in (1, 9, 33):
         Zk, nbr = idw.interpolate_knn(d, qq, 2.0, k, neighbours=True)
         r = oracle.idw_knn(data, q, 2.0, k)
         assert np.array_equal(nbr.cpu().numpy(), r["nbr"]), (name, k)
+        _, nbr_ix = kix.knn(qq, 2.0, k, neighbours=True)
+        assert np.array_equal(nbr_ix.cpu().numpy(), r["nbr"]), (name, k, "index")
         ok = ~np.isnan(r["Z"])
         if ok.any():
             worst = max(worst, float(np.max(np.abs(Zk.cpu().numpy()[ok] - r["Z"][ok]))))
