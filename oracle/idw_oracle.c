@@ -41,7 +41,10 @@
  *   - an exact hit anywhere returns z of the lowest coincident index;
  *   - no member gives NaN;
  *   - data points with a non-finite coordinate are ignored (neither hits
- *     nor members).
+ *     nor members);
+ *   - its gradients hold each membership set fixed (the sets are piecewise
+ *     constant in every input), so they are the global form's derivatives
+ *     summed over the members; a query without members contributes none.
  *
  * k-nearest-neighbour variant (the other local form of the related work,
  * Sec. 1): Eq. 1 over the k data points nearest to the query.  Readings:
@@ -348,6 +351,181 @@ int oracle_idw_local(const double *data, int64_t n, const double *q, int64_t m, 
     if (m == 0)
         return 0;
     return parallel_for(m, nthreads, local_range, &c);
+}
+
+/* ------------------------------------------------ local-form gradients */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    int64_t m;
+    double p;
+    float r2f;            /* fl32(R^2) */
+    const double *g;      /* upstream gradient, m */
+    double *Z;            /* m out */
+    int64_t *hit;         /* m, pass A */
+    int32_t *count;       /* m, pass A: members (-1 at a hit) */
+    double *S0;           /* m, scaled by d2min^(p/2), pass A */
+    double *d2min;        /* m, pass A: smallest member d^2 */
+    double *grad_q;       /* m x 2 out */
+    double *grad_p_part;  /* m out */
+    double *grad_z;       /* n out */
+    double *grad_xy;      /* n x 2 out */
+} local_grad_ctx;
+
+/*
+ * Pass A of the local gradient, per query: the members, hit, Z and S0 exactly
+ * as oracle_idw_local finds them, then dZ/dq and the query's share of dZ/dp,
+ * the global formulas with every sum taken over the members only.
+ */
+static void local_grad_query_range(void *vctx, int64_t b, int64_t e)
+{
+    local_grad_ctx *c = (local_grad_ctx *)vctx;
+    for (int64_t j = b; j < e; j++) {
+        const double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+        const float qxf = (float)qx, qyf = (float)qy;
+        int64_t hit = -1;
+        int32_t members = 0;
+        double dmin = INFINITY;
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            if (!isfinite(x) || !isfinite(y))
+                continue;
+            if (x == qx && y == qy) {
+                hit = i;
+                break;
+            }
+            if (local_member(qxf, qyf, (float)x, (float)y, c->r2f)) {
+                const double d2 = sqdist(qx, qy, x, y);
+                if (d2 < dmin)
+                    dmin = d2;
+                members++;
+            }
+        }
+        c->hit[j] = hit;
+        c->count[j] = hit >= 0 ? -1 : members;
+        c->d2min[j] = dmin;
+        c->grad_q[2 * j] = 0.0;
+        c->grad_q[2 * j + 1] = 0.0;
+        c->grad_p_part[j] = 0.0;
+        if (hit >= 0) { /* exact hit: z of that point, no coordinate gradient */
+            c->Z[j] = c->data[3 * hit + 2];
+            continue;
+        }
+        if (members == 0) {
+            c->Z[j] = NAN; /* no neighbourhood: no value and no gradient */
+            continue;
+        }
+        nsum s0 = {0.0, 0.0}, s1 = {0.0, 0.0};
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            const int member = local_member(qxf, qyf, (float)x, (float)y, c->r2f);
+            if (!member)
+                continue;
+            const double w = scaled_weight(dmin, sqdist(qx, qy, x, y), c->p);
+            nsum_add(&s0, w);
+            nsum_add(&s1, w * c->data[3 * i + 2]);
+        }
+        const double S0 = nsum_value(&s0), Zj = nsum_value(&s1) / S0;
+        c->S0[j] = S0;
+        c->Z[j] = Zj;
+        nsum sx = {0, 0}, sy = {0, 0}, sp = {0, 0};
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            const int member = local_member(qxf, qyf, (float)x, (float)y, c->r2f);
+            if (!member)
+                continue; /* members only: the query-side sums */
+            const double dx = qx - x, dy = qy - y, d2 = dx * dx + dy * dy;
+            const double w = scaled_weight(dmin, d2, c->p);
+            const double a = (c->data[3 * i + 2] - Zj) * w;
+            nsum_add(&sx, a * dx / d2);
+            nsum_add(&sy, a * dy / d2);
+            nsum_add(&sp, a * log(d2));
+        }
+        const double gj = c->g[j];
+        c->grad_q[2 * j] = -gj * (c->p / S0) * nsum_value(&sx);
+        c->grad_q[2 * j + 1] = -gj * (c->p / S0) * nsum_value(&sy);
+        c->grad_p_part[j] = -0.5 * gj * nsum_value(&sp) / S0;
+    }
+}
+
+/* Pass B, per data point: the sums over the queries whose neighbourhood
+ * holds it of dZ/dz_i and dZ/dx_i (an exact hit passes g_j to its point). */
+static void local_grad_data_range(void *vctx, int64_t b, int64_t e)
+{
+    local_grad_ctx *c = (local_grad_ctx *)vctx;
+    for (int64_t i = b; i < e; i++) {
+        const double x = c->data[3 * i], y = c->data[3 * i + 1], z = c->data[3 * i + 2];
+        const float xf = (float)x, yf = (float)y;
+        nsum tz = {0, 0}, tx = {0, 0}, ty = {0, 0};
+        for (int64_t j = 0; j < c->m; j++) {
+            const double gj = c->g[j];
+            if (c->hit[j] >= 0) {
+                if (c->hit[j] == i)
+                    nsum_add(&tz, gj); /* dZ/dz at a hit */
+                continue;
+            }
+            if (c->count[j] == 0)
+                continue;
+            const double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+            if (!local_member((float)qx, (float)qy, xf, yf, c->r2f))
+                continue; /* i is outside query j's neighbourhood */
+            const double dx = qx - x, dy = qy - y, d2 = dx * dx + dy * dy;
+            const double w = scaled_weight(c->d2min[j], d2, c->p);
+            const double S0 = c->S0[j];
+            nsum_add(&tz, gj * w / S0);
+            const double a = gj * (c->p / S0) * (z - c->Z[j]) * w / d2;
+            nsum_add(&tx, a * dx);
+            nsum_add(&ty, a * dy);
+        }
+        c->grad_z[i] = nsum_value(&tz);
+        c->grad_xy[2 * i] = nsum_value(&tx);
+        c->grad_xy[2 * i + 1] = nsum_value(&ty);
+    }
+}
+
+/*
+ * Gradient of L = sum_j g_j Z(q_j) for the local form (oracle_idw_local):
+ * the membership sets are held fixed (they are piecewise constant in every
+ * input), so each derivative is the global one summed over the members.  A
+ * query with an exact hit passes g_j to dL/dz of the hit point and nothing
+ * else; a query with no member contributes nothing.
+ *   data, q, p, radius : as oracle_idw_local.   g : m doubles.
+ *   Outputs (host memory): Z[m], grad_z[n], grad_xy[n x 2], grad_q[m x 2],
+ *   grad_p[1].
+ * Returns the number of threads used, or -1 on bad arguments / no memory.
+ */
+int oracle_idw_local_grad(const double *data, int64_t n, const double *q, int64_t m, double p,
+                          double radius, const double *g, double *Z, double *grad_z,
+                          double *grad_xy, double *grad_q, double *grad_p, int nthreads)
+{
+    if (!data || !q || !g || !Z || !grad_z || !grad_xy || !grad_q || !grad_p || n < 1 ||
+        m < 1 || !(p > 0.0) || !isfinite(p) || !(radius > 0.0))
+        return -1;
+    int64_t *hit = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int32_t *count = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    double *S0 = (double *)malloc((size_t)m * sizeof(double));
+    double *d2min = (double *)malloc((size_t)m * sizeof(double));
+    double *gp = (double *)malloc((size_t)m * sizeof(double));
+    int t = -1;
+    if (hit && count && S0 && d2min && gp) {
+        local_grad_ctx c = {data, n, q, m, p, (float)(radius * radius), g, Z, hit, count,
+                            S0, d2min, grad_q, gp, grad_z, grad_xy};
+        t = parallel_for(m, nthreads, local_grad_query_range, &c);
+        if (t > 0)
+            t = parallel_for(n, nthreads, local_grad_data_range, &c);
+        nsum total = {0, 0};
+        for (int64_t j = 0; j < m; j++)
+            nsum_add(&total, gp[j]);
+        *grad_p = nsum_value(&total);
+    }
+    free(hit);
+    free(count);
+    free(S0);
+    free(d2min);
+    free(gp);
+    return t;
 }
 
 /* ------------------------------------------------------- k-NN variant */

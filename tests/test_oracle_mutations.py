@@ -54,6 +54,15 @@ MUTATIONS = [
      "                if (hit < 0"),
     ("exact-hit gradient dropped", "                if (c->hit[j] == i)\n                    nsum_add(&gz, gj);",
      "                if (c->hit[j] == i)\n                    nsum_add(&gz, 0.0);"),
+    ("local query gradient over all points", "                continue; /* members only: the query-side sums */",
+     "                ; /* members only: the query-side sums */"),
+    ("local data gradient outside the neighbourhood",
+     "                continue; /* i is outside query j's neighbourhood */",
+     "                ; /* i is outside query j's neighbourhood */"),
+    ("local p-gradient factor 1/2 dropped", "c->grad_p_part[j] = -0.5 * gj * nsum_value(&sp) / S0;",
+     "c->grad_p_part[j] = -gj * nsum_value(&sp) / S0;"),
+    ("local data-gradient sign", "const double a = gj * (c->p / S0) * (z - c->Z[j]) * w / d2;",
+     "const double a = gj * (c->p / S0) * (c->Z[j] - z) * w / d2;"),
 ]
 
 PINS = [
@@ -82,6 +91,10 @@ PINS = [
     pins.test_knn_selection_is_decided_in_fp32,
     pins.test_knn_non_finite_inputs,
     pins.test_local_ignores_non_finite_points,
+    lambda: pins.test_local_gradient_matches_central_differences(3.0),
+    pins.test_local_gradient_with_huge_radius_is_the_global_gradient,
+    pins.test_local_gradient_sums_and_translation,
+    pins.test_local_gradient_at_hits_and_empty_neighbourhoods,
 ]
 
 

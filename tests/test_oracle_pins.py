@@ -549,3 +549,97 @@ def test_local_ignores_non_finite_points():
     Z, hit, count = oracle.idw_local(data, q, 2.0, 0.5)
     assert np.isnan(Z[0]) and hit[0] == -1 and count[0] == 0
     assert Z[1] == 1.0 and count[1] == 1
+
+
+# ------------------------------------------------- local-form gradients
+
+def _local_loss(data, q, p, radius, g, ok):
+    Z, _, _ = oracle.idw_local(data, q, p, radius)
+    return float(np.dot(g[ok], Z[ok]))
+
+
+@pytest.mark.parametrize("p", [2.0, 3.0])
+def test_local_gradient_matches_central_differences(p):
+    """Central differences of the local oracle's loss, for coordinates whose
+    perturbation leaves every membership set unchanged (the sets are held
+    fixed by definition), against the analytic local gradient."""
+    rng = np.random.default_rng(41)
+    n = m = 96
+    data = np.empty((n, 3), np.float64)
+    data[:, :2] = synthetic.separated_xy(rng, n, 2e-3)
+    data[:, 2] = rng.standard_normal(n)
+    q = synthetic.separated_xy(rng, m, 2e-3).astype(np.float64) + 1e-3 * rng.random((m, 2))
+    data[:, :2] = data[:, :2].astype(np.float32)
+    q = q.astype(np.float32).astype(np.float64)
+    R = 0.2
+    g = rng.standard_normal(m)
+    _, _, c0 = oracle.idw_local(data, q, p, R)
+    ok = c0 > 0
+    assert 0 < ok.sum() < m or ok.all()
+    G = oracle.idw_local_grad(data, q, p, R, g)
+    eps = 1e-6
+
+    def fd(arr, idx):
+        a = arr.copy(); a[idx] += eps
+        b = arr.copy(); b[idx] -= eps
+        args = ((a, q), (b, q)) if arr is data else ((data, a), (data, b))
+        for d_, q_ in args:  # the membership sets must not move
+            if not np.array_equal(oracle.idw_local(d_, q_, p, R)[2], c0):
+                return None
+        return (_local_loss(*args[0], p, R, g, ok) - _local_loss(*args[1], p, R, g, ok)) / (2 * eps)
+
+    scale_d = max(np.abs(G["grad_xy"]).max(), np.abs(G["grad_z"]).max())
+    checked = 0
+    for i in rng.choice(n, 16, replace=False):
+        for col, ref in ((2, G["grad_z"][i]), (0, G["grad_xy"][i, 0]), (1, G["grad_xy"][i, 1])):
+            v = fd(data, (i, col))
+            if v is not None:
+                assert abs(v - ref) <= 1e-6 * scale_d, (i, col, v, ref)
+                checked += 1
+    scale_q = np.abs(G["grad_q"]).max()
+    for j in rng.choice(m, 16, replace=False):
+        for col in (0, 1):
+            v = fd(q, (j, col))
+            if v is not None:
+                assert abs(v - G["grad_q"][j, col]) <= 1e-6 * scale_q, (j, col)
+                checked += 1
+    assert checked >= 40
+    dp = (_local_loss(data, q, p + eps, R, g, ok) - _local_loss(data, q, p - eps, R, g, ok)) / (2 * eps)
+    assert abs(dp - G["grad_p"]) <= 1e-6 * max(1.0, abs(dp))
+    Zl, _, _ = oracle.idw_local(data, q, p, R)
+    assert np.array_equal(np.isnan(G["Z"]), np.isnan(Zl))
+    assert np.array_equal(G["Z"][ok], Zl[ok])
+
+
+def test_local_gradient_with_huge_radius_is_the_global_gradient():
+    prob = synthetic.uniform_problem(300, 120, seed=42)
+    g = np.random.default_rng(43).standard_normal(120)
+    L = oracle.idw_local_grad(prob["data"], prob["queries"], 2.5, 1e30, g)
+    G = oracle.idw_grad(prob["data"], prob["queries"], 2.5, g)
+    for k in ("grad_z", "grad_xy", "grad_q"):
+        assert np.abs(L[k] - G[k]).max() <= 1e-12 * np.abs(G[k]).max(), k
+    assert abs(L["grad_p"] - G["grad_p"]) <= 1e-12 * abs(G["grad_p"])
+
+
+def test_local_gradient_sums_and_translation():
+    """With g = 1 the z-gradient sums to the number of queries with a value
+    (each query's weights are normalised over its members), and moving every
+    point and query together changes nothing, so the coordinate gradients
+    cancel.  Clustered data leave some queries without members."""
+    prob = synthetic.config_local(seed=44, n=600, m=400, members=6.0, clustered=True)
+    data, q, R = prob["data"], prob["queries"], prob["radius"]
+    G = oracle.idw_local_grad(data, q, 2.0, R, np.ones(q.shape[0]))
+    Zl, _, cnt = oracle.idw_local(data, q, 2.0, R)
+    assert (cnt == 0).any() and (cnt > 0).any()
+    assert abs(G["grad_z"].sum() - np.isfinite(Zl).sum()) <= 1e-10
+    assert np.abs(G["grad_xy"].sum(0) + G["grad_q"].sum(0)).max() <= 1e-9 * np.abs(G["grad_q"]).max()
+
+
+def test_local_gradient_at_hits_and_empty_neighbourhoods():
+    data = np.array([[0.1, 0.2, 1.5], [0.7, 0.4, -1.0], [0.3, 0.9, 2.0], [0.75, 0.45, 4.0]],
+                    np.float64)
+    q = np.array([[0.7, 0.4], [5.0, 5.0]], np.float64)  # a hit, and no member at all
+    G = oracle.idw_local_grad(data, q, 2.0, 0.2, np.array([3.0, 7.0]))
+    assert np.array_equal(G["grad_z"], [0.0, 3.0, 0.0, 0.0])
+    assert np.all(G["grad_xy"] == 0) and np.all(G["grad_q"] == 0) and G["grad_p"] == 0
+    assert G["Z"][0] == -1.0 and np.isnan(G["Z"][1])
