@@ -694,6 +694,18 @@ def run_local(args):
                          "empty_queries": int((c == 0).sum()),
                          "counts_match_oracle": bool(np.array_equal(c[idx], c64)),
                          "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+        gout = torch.from_numpy(np.random.default_rng(7).standard_normal(m).astype(np.float32)).cuda()
+        bms = _events_ms(lambda: idw.local_backward(d, q, 2.0, R, gout), 10, warm=3)
+        _, _, gq, _ = idw.local_backward(d, q, 2.0, R, gout)
+        sub = np.sort(idx[:128])
+        Gs = oracle.idw_local_grad(prob["data"], prob["queries"][sub], 2.0, R,
+                                   gout.cpu().numpy()[sub])
+        gerr = float(np.max(np.abs(gq.cpu().numpy()[sub] - Gs["grad_q"])) /
+                     np.max(np.abs(Gs["grad_q"])))
+        rows.append({"data": "clustered" if clustered else "uniform", "call": "backward",
+                     "n": n, "m": m, "radius": R, "p": 2.0, "ms": bms,
+                     "queries_s": m / (bms / 1e3), "grad_q_error_vs_fp64_oracle": gerr,
+                     "error_sample_queries": len(sub)})
         build_ms = _events_ms(lambda: idw.LocalIndex(d, radius=R).close(), 3, warm=1)
         ix = idw.LocalIndex(d, radius=R)
         ms = _events_ms(lambda: ix.interpolate(q, 2.0, out=out), 10, warm=3)
@@ -706,7 +718,8 @@ def run_local(args):
     _emit("local (radius-limited) Eq. 1: N = M = 2^20, queries uniform on [0,1)^2, "
           "R = sqrt(K / (pi N)); data uniform (wave field) or 64 Gaussian blobs (bump field); "
           "a one-shot call's time includes the grid build, a prepared index's call sorts the "
-          "queries only (index_build_ms: building it, allocation included)", rows,
+          "queries only (index_build_ms: building it, allocation included); backward = every "
+          "gradient (z, data xy, query xy, p) including its grid build", rows,
           metric="local queries/s", unit="queries/s")
 
 

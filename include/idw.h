@@ -447,6 +447,37 @@ idw_status idw_interpolate_knn(idw_handle_t handle, const float *data_xyz, int64
                                float *out, int32_t *nbr_out, float *kd2_out, void *stream);
 
 /*
+ * Gradients of the local (radius) form: for L = sum_j grad_out[j] Z(q_j),
+ * with Z from idw_interpolate_local at the same radius, writes
+ *   grad_z[i]        = dL/dz_i                (n floats),
+ *   grad_data_xy[i]  = dL/d(x_i, y_i)         (n x 2 floats),
+ *   grad_query_xy[j] = dL/d(qx_j, qy_j)       (m x 2 floats),
+ *   grad_p[0]        = dL/dp                  (one double).
+ * Each may be NULL (not computed).  Each query's membership set (the FP32
+ * test of idw_interpolate_local) is held fixed: it is piecewise constant in
+ * every input, so each derivative is that of the global form (see
+ * idw_backward) summed over the members.  A query with an exact hit passes
+ * grad_out[j] to dL/dz of its point (the lowest coincident index) and
+ * nothing else; a query without members (Z = NaN) contributes nothing, and
+ * non-finite data points get zero gradients.
+ *
+ * Method, on `stream` without host synchronisation: the grid build of
+ * idw_interpolate_local, then one thread per query (cell order) finds its
+ * members and computes Z, S0, dL/dq and its share of dL/dp with weights
+ * scaled by the members' smallest d^2 (FP32; FP64 where the FP32 values
+ * leave their range), and one thread per data point walks the queries whose
+ * disc reaches it with the same FP32 membership test and sums dL/dz and
+ * dL/dx in registers (one write per point: deterministic, no atomics).
+ * dL/dp is a sum of per-warp FP64 atomics, so its last bits may vary.
+ * Workspace: that of idw_interpolate_local plus 32 bytes per query.
+ * Errors as in idw_interpolate_local; grad_p must be 8-byte aligned.
+ */
+idw_status idw_local_backward(idw_handle_t handle, const float *data_xyz, int64_t n,
+                              const float *queries_xy, int64_t m, double p, double radius,
+                              const float *grad_out, float *grad_z, float *grad_data_xy,
+                              float *grad_query_xy, double *grad_p, void *stream);
+
+/*
  * Prepared index of the local forms: the data side of idw_interpolate_local
  * or idw_interpolate_knn (bounding box, grid plan, counting sort of the
  * data, and for k-NN the cell-count tables) built once, then queried by any

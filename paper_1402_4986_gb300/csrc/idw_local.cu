@@ -624,6 +624,243 @@ __global__ void __launch_bounds__(kLocalThreads)
   if (count_out) count_out[j] = members;
 }
 
+// ------------------------------------------------- local-form gradients
+//
+// dL/d(inputs) of L = sum_j g_j Z(q_j) for the radius form.  Each query's
+// membership set is held fixed (it is piecewise constant in every input), so
+// every derivative is the global one (the chain rule on Eq. 1) summed over
+// the members:
+//   dZ/dz_i = w_i / S0,   dZ/dx_i = (p / S0)(z_i - Z) w_i (q - x_i) / d_i^2,
+//   dZ/dq = -sum_i dZ/dx_i,   dZ/dp = -(1 / (2 S0)) sum_i (z_i - Z) w_i ln d_i^2.
+// Weights are scaled by the members' smallest d^2 (w_i = (d2_min / d_i^2)^(p/2)
+// <= 1): every formula is a ratio in w / S0, so the factor cancels, and
+// nothing overflows.  Since sum_i (z_i - Z) w_i = 0, ln d_i^2 may be taken
+// relative to d2_min.  An exact hit passes g_j to dL/dz of its point only; a
+// query without members contributes nothing.
+//
+// Two kernels share one record per sorted query:
+//   1. per query (in cell order): hit and members, the sums, Z, dL/dq and
+//      the query's share of dL/dp (a warp sum, then one FP64 atomic);
+//   2. per data point (in cell order): walks the sorted queries whose disc
+//      can reach it (the grid's coverage argument is symmetric in the two
+//      points) with the same FP32 membership test, and sums dL/dz_i and
+//      dL/dx_i in registers: one write per point, no atomics.
+// FP32 throughout, except queries whose d2_min is below 2^-100 (or zero
+// without a coincident point) or whose FP32 sums are not finite: those use
+// FP64 on both sides.
+struct LocalGradRec {
+  double d2min;  // the members' smallest d^2 (an FP32 value on the FP32 path)
+  double c;      // g_j / S0 (scaled), or g_j at an exact hit
+  double z;      // Z_j
+  int code;      // >= 0: exact hit (data index); -1: nothing; -2: FP32; -3: FP64
+  int pad;
+};
+constexpr int kGradHitNone = -1, kGradF32 = -2, kGradF64 = -3;
+
+// Scaled FP32 weight (d2min / d2)^(p/2); lmin = log2(d2min) for general p.
+template <int MODE>
+__device__ __forceinline__ float grad_weight(float d2, float d2min, float lmin, float hp) {
+  if (MODE == kPow2) return __fmul_rn(d2min, rcp_approx(d2));
+  return ex2_approx(-hp * (lg2_approx(d2) - lmin));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLocalThreads)
+    local_grad_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
+                            int64_t n, const int32_t* __restrict__ starts,
+                            const int32_t* __restrict__ base, const float4* __restrict__ qrec,
+                            int64_t m, double p, float r2f, float r2t,
+                            const float* __restrict__ grad_out, float* __restrict__ grad_q,
+                            double* __restrict__ grad_p, LocalGradRec* __restrict__ rec) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double gp = 0.0;  // this query's share of dL/dp (every lane joins the warp sum)
+  if (t < m) {
+    const float4 r = qrec[t];
+    const float qx = r.x, qy = r.y;
+    const int j = __float_as_int(r.z);
+    if (dcheck(j >= 0 && j < m, kSiteOutput)) {
+      const float gj = grad_out[j];
+      const Runs runs(*grid, qx, qy, starts, base);
+      int best = INT_MAX, members = 0;
+      float d2min = INFINITY;
+#pragma unroll
+      for (int rr = 0; rr < 5; ++rr)
+        for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+          if (!dcheck(k >= 0 && k < n, kSiteGather)) break;
+          const float4 v = sorted[k];
+          const float d2 = fp32_d2(qx, qy, v.x, v.y);
+          if (!(d2 < r2t)) continue;
+          if (v.x == qx && v.y == qy) {
+            best = min(best, __float_as_int(v.w));
+          } else if (d2 < r2f) {
+            ++members;
+            d2min = fminf(d2min, d2);
+          }
+        }
+      LocalGradRec out{0.0, 0.0, 0.0, kGradHitNone, 0};
+      float gqx = 0.f, gqy = 0.f;
+      if (best != INT_MAX) {
+        out.code = best;
+        out.c = gj;
+      } else if (members > 0) {
+        const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+        bool f32 = d2min >= 0x1p-100f;
+        if (f32) {
+          const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+              const float4 v = sorted[k];
+              const float d2 = fp32_d2(qx, qy, v.x, v.y);
+              if (!(d2 < r2f)) continue;
+              const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+              s0 += w;
+              s1 = fmaf(w, v.z, s1);
+            }
+          const float Z = s1 / s0;
+          const float lmin2 = lg2_approx(d2min);
+          float ax = 0.f, ay = 0.f, al = 0.f;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+              const float4 v = sorted[k];
+              const float dx = __fsub_rn(qx, v.x), dy = __fsub_rn(qy, v.y);
+              const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+              if (!(d2 < r2f)) continue;
+              const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+              const float a = (v.z - Z) * w, ar = a * rcp_approx(d2);
+              ax = fmaf(ar, dx, ax);
+              ay = fmaf(ar, dy, ay);
+              al = fmaf(a, lg2_approx(d2) - lmin2, al);
+            }
+          const float k1 = gj * pf / s0;
+          gqx = -k1 * ax;
+          gqy = -k1 * ay;
+          gp = -0.5 * double(gj) * double(al) * 0.6931471805599453 / double(s0);
+          out.code = kGradF32;
+          out.c = double(gj / s0);
+          out.z = Z;
+          out.d2min = d2min;
+          f32 = isfinite(Z) && isfinite(gqx) && isfinite(gqy) && isfinite(gp) && isfinite(gj / s0);
+        }
+        if (!f32) {  // FP64: weights scaled by the exact d2_min^(p/2)
+          double dmin = INFINITY;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+              const float4 v = sorted[k];
+              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+              dmin = fmin(dmin, ex * ex + ey * ey);
+            }
+          double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+              const float4 v = sorted[k];
+              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+              const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+              s0 += w;
+              s1 += w * double(v.z);
+            }
+          const double Z = s1 / s0;
+          double ax = 0.0, ay = 0.0, al = 0.0;
+#pragma unroll
+          for (int rr = 0; rr < 5; ++rr)
+            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+              const float4 v = sorted[k];
+              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+              const double d2 = ex * ex + ey * ey;
+              const double w = pow(dmin / d2, 0.5 * p);
+              const double a = (double(v.z) - Z) * w;
+              ax += a * ex / d2;
+              ay += a * ey / d2;
+              al += a * log(d2 / dmin);
+            }
+          gqx = static_cast<float>(-double(gj) * p / s0 * ax);
+          gqy = static_cast<float>(-double(gj) * p / s0 * ay);
+          gp = -0.5 * double(gj) * al / s0;
+          out.code = kGradF64;
+          out.c = double(gj) / s0;
+          out.z = Z;
+          out.d2min = dmin;
+        }
+      }
+      rec[t] = out;
+      if (grad_q) {
+        grad_q[2 * int64_t(j)] = gqx;
+        grad_q[2 * int64_t(j) + 1] = gqy;
+      }
+    }
+  }
+  if (grad_p) {
+    gp = warp_sum(gp);
+    if ((threadIdx.x & 31) == 0 && gp != 0.0) atomicAdd(grad_p, gp);
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLocalThreads)
+    local_grad_data_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
+                           int64_t n, const int32_t* __restrict__ starts_d,
+                           const int32_t* __restrict__ base_d,
+                           const int32_t* __restrict__ starts_q,
+                           const int32_t* __restrict__ base_q, const float4* __restrict__ qrec,
+                           int64_t m, const LocalGradRec* __restrict__ rec, double p, float r2f,
+                           float* __restrict__ grad_z, float* __restrict__ grad_xy) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const GridDev g = *grid;
+  if (k >= cell_start(starts_d, base_d, g.cells, g.cells)) return;  // placed (finite) points
+  if (!dcheck(k < n, kSiteGather)) return;
+  const float4 v = sorted[k];
+  const int idx = __float_as_int(v.w);
+  if (!dcheck(idx >= 0 && idx < n, kSiteData)) return;
+  const Runs runs(g, v.x, v.y, starts_q, base_q);
+  const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+  float gz = 0.f, gx = 0.f, gy = 0.f;
+#pragma unroll
+  for (int rr = 0; rr < 5; ++rr)
+    for (int t = runs.a[rr]; t < runs.b[rr]; ++t) {
+      if (!dcheck(t >= 0 && t < m, kSiteGather)) break;
+      const LocalGradRec R = rec[t];
+      if (R.code == kGradHitNone) continue;
+      if (R.code >= 0) {
+        if (R.code == idx) gz += static_cast<float>(R.c);
+        continue;
+      }
+      const float4 q = qrec[t];
+      const float dx = __fsub_rn(q.x, v.x), dy = __fsub_rn(q.y, v.y);
+      const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+      if (!(d2 < r2f)) continue;  // the query's membership test, bit for bit
+      if (R.code == kGradF32) {
+        const float d2min = static_cast<float>(R.d2min);
+        const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
+        const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+        const float c = static_cast<float>(R.c);
+        gz = fmaf(c, w, gz);
+        const float a = c * pf * (v.z - static_cast<float>(R.z)) * w * rcp_approx(d2);
+        gx = fmaf(a, dx, gx);
+        gy = fmaf(a, dy, gy);
+      } else {
+        const double ex = double(q.x) - v.x, ey = double(q.y) - v.y;
+        const double e2 = ex * ex + ey * ey;
+        const double w = pow(R.d2min / e2, 0.5 * p);
+        gz += static_cast<float>(R.c * w);
+        const double a = R.c * p * (double(v.z) - R.z) * w / e2;
+        gx += static_cast<float>(a * ex);
+        gy += static_cast<float>(a * ey);
+      }
+    }
+  if (grad_z) grad_z[idx] = gz;
+  if (grad_xy) {
+    grad_xy[2 * int64_t(idx)] = gx;
+    grad_xy[2 * int64_t(idx) + 1] = gy;
+  }
+}
+
 // ------------------------------------------------------------- k-NN form
 //
 // One thread per query, in cell order, grows a square of cells around the
@@ -1036,6 +1273,47 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   else
     local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
+  return cudaGetLastError();
+}
+
+size_t local_grad_record_bytes(int64_t m) { return round_up(size_t(m) * sizeof(LocalGradRec), 256); }
+
+cudaError_t launch_local_backward(const float* data, int64_t n, const float* queries, int64_t m,
+                                  double p, double radius, const float* grad_out, float* grad_z,
+                                  float* grad_xy, float* grad_q, double* grad_p, void* workspace,
+                                  const LocalLayout& L, int sm_count, cudaStream_t s) {
+  cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s);
+  if (e != cudaSuccess) return e;
+  if (grad_z && (e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
+  if (grad_xy && (e = cudaMemsetAsync(grad_xy, 0, size_t(n) * 8, s)) != cudaSuccess) return e;
+  if (grad_p && (e = cudaMemsetAsync(grad_p, 0, sizeof(double), s)) != cudaSuccess) return e;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  const GridDev* grid = reinterpret_cast<const GridDev*>(ws + L.off_grid);
+  const int32_t* starts_d = reinterpret_cast<const int32_t*>(ws + L.off_starts_d);
+  const int32_t* starts_q = reinterpret_cast<const int32_t*>(ws + L.off_starts_q);
+  const int32_t* sums = reinterpret_cast<const int32_t*>(ws + L.off_sums);
+  const int32_t* sums_q = sums + scan_tiles_of(L.max_cells);
+  const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
+  const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
+  LocalGradRec* rec = reinterpret_cast<LocalGradRec*>(ws + L.bytes);
+  const float r2f = static_cast<float>(radius * radius);
+  const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
+  const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
+  const unsigned dgrid = static_cast<unsigned>((n + kLocalThreads - 1) / kLocalThreads);
+  const bool data_side = grad_z || grad_xy;
+  if (p == 2.0) {
+    local_grad_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec);
+    if (data_side)
+      local_grad_data_kernel<kPow2><<<dgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, p, r2f, grad_z, grad_xy);
+  } else {
+    local_grad_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec);
+    if (data_side)
+      local_grad_data_kernel<kPowGeneral><<<dgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, p, r2f, grad_z, grad_xy);
+  }
   return cudaGetLastError();
 }
 

@@ -49,6 +49,10 @@ for name, data, q in cases:
     Z, cnt = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True)
     Zo, _, co = oracle.idw_local(data, q, 2.0, 0.03)
     assert np.array_equal(cnt.cpu().numpy(), co), name
+    gl = torch.linspace(-1.0, 1.0, q.shape[0], device="cuda")
+    gzl = idw.local_backward(d, qq, 2.0, 0.03, gl)[0].cpu().numpy()
+    Gl = oracle.idw_local_grad(data, q, 2.0, 0.03, gl.cpu().numpy())["grad_z"]
+    assert np.max(np.abs(gzl - Gl)) <= 1e-4 * max(np.max(np.abs(Gl)), 1e-30), name
     _, cnt_ix = idw.LocalIndex(d, radius=0.03).interpolate(qq, 2.0, 0.02, counts=True)
     assert np.array_equal(cnt_ix.cpu().numpy(), oracle.idw_local(data, q, 2.0, 0.02)[2]), name
     kix = idw.LocalIndex(d, k=9)
