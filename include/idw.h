@@ -469,7 +469,7 @@ idw_status idw_interpolate_knn(idw_handle_t handle, const float *data_xyz, int64
  * disc reaches it with the same FP32 membership test and sums dL/dz and
  * dL/dx in registers (one write per point: deterministic, no atomics).
  * dL/dp is a sum of per-warp FP64 atomics, so its last bits may vary.
- * Workspace: that of idw_interpolate_local plus 32 bytes per query.
+ * Workspace: that of idw_interpolate_local plus 40 bytes per query.
  * Errors as in idw_interpolate_local; grad_p must be 8-byte aligned.
  */
 idw_status idw_local_backward(idw_handle_t handle, const float *data_xyz, int64_t n,

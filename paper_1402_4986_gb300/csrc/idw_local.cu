@@ -648,12 +648,17 @@ __global__ void __launch_bounds__(kLocalThreads)
 // FP32 throughout, except queries whose d2_min is below 2^-100 (or zero
 // without a coincident point) or whose FP32 sums are not finite: those use
 // FP64 on both sides.
+// The record read for every (point, query) candidate is 16 bytes of FP32
+// (FP64-to-FP32 conversions run at the FP64 rate on this part); queries on
+// the FP64 path keep their values in a second array read only for them.
 struct LocalGradRec {
-  double d2min;  // the members' smallest d^2 (an FP32 value on the FP32 path)
-  double c;      // g_j / S0 (scaled), or g_j at an exact hit
-  double z;      // Z_j
-  int code;      // >= 0: exact hit (data index); -1: nothing; -2: FP32; -3: FP64
-  int pad;
+  float d2min;  // the members' smallest d^2 (FP32 path)
+  float c;      // g_j / S0 (scaled), or g_j at an exact hit
+  float z;      // Z_j
+  int code;     // >= 0: exact hit (data index); -1: nothing; -2: FP32; -3: FP64
+};
+struct LocalGradRec64 {
+  double d2min, c, z;  // FP64 path only
 };
 constexpr int kGradHitNone = -1, kGradF32 = -2, kGradF64 = -3;
 
@@ -671,7 +676,8 @@ __global__ void __launch_bounds__(kLocalThreads)
                             const int32_t* __restrict__ base, const float4* __restrict__ qrec,
                             int64_t m, double p, float r2f, float r2t,
                             const float* __restrict__ grad_out, float* __restrict__ grad_q,
-                            double* __restrict__ grad_p, LocalGradRec* __restrict__ rec) {
+                            double* __restrict__ grad_p, LocalGradRec* __restrict__ rec,
+                            LocalGradRec64* __restrict__ rec64) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double gp = 0.0;  // this query's share of dL/dp (every lane joins the warp sum)
   if (t < m) {
@@ -681,8 +687,12 @@ __global__ void __launch_bounds__(kLocalThreads)
     if (dcheck(j >= 0 && j < m, kSiteOutput)) {
       const float gj = grad_out[j];
       const Runs runs(*grid, qx, qy, starts, base);
+      // One pass: hit, members, d2_min, and the sums with weights scaled by
+      // the smallest d^2 so far (rescaled, as in an online softmax, when a
+      // smaller one appears, so every scaled weight stays <= 1).
+      const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
       int best = INT_MAX, members = 0;
-      float d2min = INFINITY;
+      float d2min = INFINITY, lmin = 0.f, s0 = 0.f, s1 = 0.f;
 #pragma unroll
       for (int rr = 0; rr < 5; ++rr)
         for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
@@ -692,32 +702,32 @@ __global__ void __launch_bounds__(kLocalThreads)
           if (!(d2 < r2t)) continue;
           if (v.x == qx && v.y == qy) {
             best = min(best, __float_as_int(v.w));
-          } else if (d2 < r2f) {
-            ++members;
-            d2min = fminf(d2min, d2);
+            continue;
           }
+          if (!(d2 < r2f)) continue;
+          ++members;
+          if (d2 < d2min) {
+            const float l = MODE == kPow2 ? 0.f : lg2_approx(d2);
+            if (members > 1) {
+              const float f = grad_weight<MODE>(d2min, d2, l, hp);  // (d2 / d2min_old)^(p/2)
+              s0 *= f;
+              s1 *= f;
+            }
+            d2min = d2;
+            lmin = l;
+          }
+          const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+          s0 += w;
+          s1 = fmaf(w, v.z, s1);
         }
-      LocalGradRec out{0.0, 0.0, 0.0, kGradHitNone, 0};
+      LocalGradRec out{0.f, 0.f, 0.f, kGradHitNone};
       float gqx = 0.f, gqy = 0.f;
       if (best != INT_MAX) {
         out.code = best;
         out.c = gj;
       } else if (members > 0) {
-        const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
         bool f32 = d2min >= 0x1p-100f;
         if (f32) {
-          const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
-          float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-          for (int rr = 0; rr < 5; ++rr)
-            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
-              const float4 v = sorted[k];
-              const float d2 = fp32_d2(qx, qy, v.x, v.y);
-              if (!(d2 < r2f)) continue;
-              const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
-              s0 += w;
-              s1 = fmaf(w, v.z, s1);
-            }
           const float Z = s1 / s0;
           const float lmin2 = lg2_approx(d2min);
           float ax = 0.f, ay = 0.f, al = 0.f;
@@ -734,15 +744,16 @@ __global__ void __launch_bounds__(kLocalThreads)
               ay = fmaf(ar, dy, ay);
               al = fmaf(a, lg2_approx(d2) - lmin2, al);
             }
-          const float k1 = gj * pf / s0;
+          const float c = gj / s0, k1 = c * pf;
           gqx = -k1 * ax;
           gqy = -k1 * ay;
-          gp = -0.5 * double(gj) * double(al) * 0.6931471805599453 / double(s0);
+          const float gpf = (-0.5f * 0.6931471805599453f) * c * al;  // FP32: no FP64 divide
+          gp = gpf;
           out.code = kGradF32;
-          out.c = double(gj / s0);
+          out.c = c;
           out.z = Z;
           out.d2min = d2min;
-          f32 = isfinite(Z) && isfinite(gqx) && isfinite(gqy) && isfinite(gp) && isfinite(gj / s0);
+          f32 = isfinite(Z) && isfinite(gqx) && isfinite(gqy) && isfinite(gpf) && isfinite(c);
         }
         if (!f32) {  // FP64: weights scaled by the exact d2_min^(p/2)
           double dmin = INFINITY;
@@ -784,9 +795,7 @@ __global__ void __launch_bounds__(kLocalThreads)
           gqy = static_cast<float>(-double(gj) * p / s0 * ay);
           gp = -0.5 * double(gj) * al / s0;
           out.code = kGradF64;
-          out.c = double(gj) / s0;
-          out.z = Z;
-          out.d2min = dmin;
+          rec64[t] = LocalGradRec64{dmin, double(gj) / s0, Z};
         }
       }
       rec[t] = out;
@@ -809,7 +818,8 @@ __global__ void __launch_bounds__(kLocalThreads)
                            const int32_t* __restrict__ base_d,
                            const int32_t* __restrict__ starts_q,
                            const int32_t* __restrict__ base_q, const float4* __restrict__ qrec,
-                           int64_t m, const LocalGradRec* __restrict__ rec, double p, float r2f,
+                           int64_t m, const LocalGradRec* __restrict__ rec,
+                           const LocalGradRec64* __restrict__ rec64, double p, float r2f,
                            float* __restrict__ grad_z, float* __restrict__ grad_xy) {
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const GridDev g = *grid;
@@ -823,33 +833,33 @@ __global__ void __launch_bounds__(kLocalThreads)
   float gz = 0.f, gx = 0.f, gy = 0.f;
 #pragma unroll
   for (int rr = 0; rr < 5; ++rr)
+#pragma unroll 2
     for (int t = runs.a[rr]; t < runs.b[rr]; ++t) {
       if (!dcheck(t >= 0 && t < m, kSiteGather)) break;
-      const LocalGradRec R = rec[t];
+      const LocalGradRec R = rec[t];  // both loads issue before any branch
+      const float4 q = qrec[t];
       if (R.code == kGradHitNone) continue;
       if (R.code >= 0) {
-        if (R.code == idx) gz += static_cast<float>(R.c);
+        if (R.code == idx) gz += R.c;
         continue;
       }
-      const float4 q = qrec[t];
       const float dx = __fsub_rn(q.x, v.x), dy = __fsub_rn(q.y, v.y);
       const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
       if (!(d2 < r2f)) continue;  // the query's membership test, bit for bit
       if (R.code == kGradF32) {
-        const float d2min = static_cast<float>(R.d2min);
-        const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
-        const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
-        const float c = static_cast<float>(R.c);
-        gz = fmaf(c, w, gz);
-        const float a = c * pf * (v.z - static_cast<float>(R.z)) * w * rcp_approx(d2);
+        const float lmin = MODE == kPow2 ? 0.f : lg2_approx(R.d2min);
+        const float w = grad_weight<MODE>(d2, R.d2min, lmin, hp);
+        gz = fmaf(R.c, w, gz);
+        const float a = R.c * pf * (v.z - R.z) * w * rcp_approx(d2);
         gx = fmaf(a, dx, gx);
         gy = fmaf(a, dy, gy);
       } else {
+        const LocalGradRec64 D = rec64[t];
         const double ex = double(q.x) - v.x, ey = double(q.y) - v.y;
         const double e2 = ex * ex + ey * ey;
-        const double w = pow(R.d2min / e2, 0.5 * p);
-        gz += static_cast<float>(R.c * w);
-        const double a = R.c * p * (double(v.z) - R.z) * w / e2;
+        const double w = pow(D.d2min / e2, 0.5 * p);
+        gz += static_cast<float>(D.c * w);
+        const double a = D.c * p * (double(v.z) - D.z) * w / e2;
         gx += static_cast<float>(a * ex);
         gy += static_cast<float>(a * ey);
       }
@@ -1276,7 +1286,10 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   return cudaGetLastError();
 }
 
-size_t local_grad_record_bytes(int64_t m) { return round_up(size_t(m) * sizeof(LocalGradRec), 256); }
+size_t local_grad_record_bytes(int64_t m) {
+  return round_up(size_t(m) * sizeof(LocalGradRec), 256) +
+         round_up(size_t(m) * sizeof(LocalGradRec64), 256);
+}
 
 cudaError_t launch_local_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                   double p, double radius, const float* grad_out, float* grad_z,
@@ -1296,6 +1309,8 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   const float4* sorted = reinterpret_cast<const float4*>(ws + L.off_sorted);
   const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
   LocalGradRec* rec = reinterpret_cast<LocalGradRec*>(ws + L.bytes);
+  LocalGradRec64* rec64 = reinterpret_cast<LocalGradRec64*>(
+      ws + L.bytes + round_up(size_t(m) * sizeof(LocalGradRec), 256));
   const float r2f = static_cast<float>(radius * radius);
   const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
@@ -1303,16 +1318,20 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   const bool data_side = grad_z || grad_xy;
   if (p == 2.0) {
     local_grad_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
-        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec);
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec,
+        rec64);
     if (data_side)
       local_grad_data_kernel<kPow2><<<dgrid, kLocalThreads, 0, s>>>(
-          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, p, r2f, grad_z, grad_xy);
+          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, rec64, p, r2f, grad_z,
+          grad_xy);
   } else {
     local_grad_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
-        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec);
+        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec,
+        rec64);
     if (data_side)
       local_grad_data_kernel<kPowGeneral><<<dgrid, kLocalThreads, 0, s>>>(
-          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, p, r2f, grad_z, grad_xy);
+          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, rec64, p, r2f, grad_z,
+          grad_xy);
   }
   return cudaGetLastError();
 }
