@@ -669,6 +669,57 @@ __device__ __forceinline__ float grad_weight(float d2, float d2min, float lmin, 
   return ex2_approx(-hp * (lg2_approx(d2) - lmin));
 }
 
+// The FP64 path of one query (weights scaled by its exact d2_min^(p/2)):
+// dL/dq, its dL/dp share and the record the data-side kernel reads.  Out of
+// line, so that the rare FP64 branch adds no registers to the FP32 loops.
+struct GradF64 {
+  float gqx, gqy;
+  double gp;
+  LocalGradRec64 rec;
+};
+__device__ __noinline__ GradF64 grad_query_f64(const Runs runs, const float4* __restrict__ sorted,
+                                               float qx, float qy, float r2f, double p,
+                                               float gj) {
+  double dmin = INFINITY;
+  for (int rr = 0; rr < 5; ++rr)
+    for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+      const float4 v = sorted[k];
+      if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+      const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+      dmin = fmin(dmin, ex * ex + ey * ey);
+    }
+  double s0 = 0.0, s1 = 0.0;
+  for (int rr = 0; rr < 5; ++rr)
+    for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+      const float4 v = sorted[k];
+      if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+      const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+      const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+      s0 += w;
+      s1 += w * double(v.z);
+    }
+  const double Z = s1 / s0;
+  double ax = 0.0, ay = 0.0, al = 0.0;
+  for (int rr = 0; rr < 5; ++rr)
+    for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
+      const float4 v = sorted[k];
+      if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
+      const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+      const double d2 = ex * ex + ey * ey;
+      const double w = pow(dmin / d2, 0.5 * p);
+      const double a = (double(v.z) - Z) * w;
+      ax += a * ex / d2;
+      ay += a * ey / d2;
+      al += a * log(d2 / dmin);
+    }
+  GradF64 r;
+  r.gqx = static_cast<float>(-double(gj) * p / s0 * ax);
+  r.gqy = static_cast<float>(-double(gj) * p / s0 * ay);
+  r.gp = -0.5 * double(gj) * al / s0;
+  r.rec = LocalGradRec64{dmin, double(gj) / s0, Z};
+  return r;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kLocalThreads)
     local_grad_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
@@ -756,46 +807,12 @@ __global__ void __launch_bounds__(kLocalThreads)
           f32 = isfinite(Z) && isfinite(gqx) && isfinite(gqy) && isfinite(gpf) && isfinite(c);
         }
         if (!f32) {  // FP64: weights scaled by the exact d2_min^(p/2)
-          double dmin = INFINITY;
-#pragma unroll
-          for (int rr = 0; rr < 5; ++rr)
-            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
-              const float4 v = sorted[k];
-              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
-              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-              dmin = fmin(dmin, ex * ex + ey * ey);
-            }
-          double s0 = 0.0, s1 = 0.0;
-#pragma unroll
-          for (int rr = 0; rr < 5; ++rr)
-            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
-              const float4 v = sorted[k];
-              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
-              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-              const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
-              s0 += w;
-              s1 += w * double(v.z);
-            }
-          const double Z = s1 / s0;
-          double ax = 0.0, ay = 0.0, al = 0.0;
-#pragma unroll
-          for (int rr = 0; rr < 5; ++rr)
-            for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
-              const float4 v = sorted[k];
-              if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
-              const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-              const double d2 = ex * ex + ey * ey;
-              const double w = pow(dmin / d2, 0.5 * p);
-              const double a = (double(v.z) - Z) * w;
-              ax += a * ex / d2;
-              ay += a * ey / d2;
-              al += a * log(d2 / dmin);
-            }
-          gqx = static_cast<float>(-double(gj) * p / s0 * ax);
-          gqy = static_cast<float>(-double(gj) * p / s0 * ay);
-          gp = -0.5 * double(gj) * al / s0;
+          const GradF64 r64 = grad_query_f64(runs, sorted, qx, qy, r2f, p, gj);
+          gqx = r64.gqx;
+          gqy = r64.gqy;
+          gp = r64.gp;
           out.code = kGradF64;
-          rec64[t] = LocalGradRec64{dmin, double(gj) / s0, Z};
+          rec64[t] = r64.rec;
         }
       }
       rec[t] = out;
@@ -809,6 +826,18 @@ __global__ void __launch_bounds__(kLocalThreads)
     gp = warp_sum(gp);
     if ((threadIdx.x & 31) == 0 && gp != 0.0) atomicAdd(grad_p, gp);
   }
+}
+
+// The FP64 path's share of one (point, query) pair: (dL/dz, dL/dx, dL/dy).
+// Out of line, so that the rare FP64 branch adds no registers to the loop.
+__device__ __noinline__ float3 grad_pair_f64(LocalGradRec64 D, float qx, float qy, float4 v,
+                                             double p) {
+  const double ex = double(qx) - v.x, ey = double(qy) - v.y;
+  const double e2 = ex * ex + ey * ey;
+  const double w = pow(D.d2min / e2, 0.5 * p);
+  const double a = D.c * p * (double(v.z) - D.z) * w / e2;
+  return make_float3(static_cast<float>(D.c * w), static_cast<float>(a * ex),
+                     static_cast<float>(a * ey));
 }
 
 template <int MODE>
@@ -854,14 +883,10 @@ __global__ void __launch_bounds__(kLocalThreads)
         gx = fmaf(a, dx, gx);
         gy = fmaf(a, dy, gy);
       } else {
-        const LocalGradRec64 D = rec64[t];
-        const double ex = double(q.x) - v.x, ey = double(q.y) - v.y;
-        const double e2 = ex * ex + ey * ey;
-        const double w = pow(D.d2min / e2, 0.5 * p);
-        gz += static_cast<float>(D.c * w);
-        const double a = D.c * p * (double(v.z) - D.z) * w / e2;
-        gx += static_cast<float>(a * ex);
-        gy += static_cast<float>(a * ey);
+        const float3 f = grad_pair_f64(rec64[t], q.x, q.y, v, p);
+        gz += f.x;
+        gx += f.y;
+        gy += f.z;
       }
     }
   if (grad_z) grad_z[idx] = gz;
