@@ -68,6 +68,9 @@ def bind(lib):
     lib.oracle_idw_local_grad.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_double, d,
                                           d, d, d, d, d, ctypes.c_int]
     lib.oracle_idw_local_grad.restype = ctypes.c_int
+    lib.oracle_idw_knn_grad.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_int, d, d, d, d,
+                                        d, d, ctypes.c_int]
+    lib.oracle_idw_knn_grad.restype = ctypes.c_int
     return lib
 
 
@@ -213,4 +216,28 @@ def idw_local_grad(data_xyz, queries_xy, p: float, radius: float, g, threads: in
                                    _ptr(Z), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), int(threads))
     if rc < 0:
         raise ValueError("oracle_idw_local_grad rejected its arguments")
+    return {"Z": Z, "grad_z": gz, "grad_xy": gxy, "grad_q": gq, "grad_p": float(gp[0])}
+
+
+def idw_knn_grad(data_xyz, queries_xy, p: float, k: int, g, threads: int = 0):
+    """Gradients of L = sum_j g_j Z(q_j) for the k-NN form (FP64).
+
+    Each query's selection (``idw_knn``) is held fixed, so each derivative
+    is the global one summed over the selected points.  Returns a dict with
+    Z[m], grad_z[n], grad_xy[n,2], grad_q[m,2], grad_p.
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    n, m = data.shape[0], q.shape[0]
+    g = np.ascontiguousarray(np.asarray(g), dtype=np.float64).reshape(m)
+    Z = np.empty(m, np.float64)
+    gz = np.empty(n, np.float64)
+    gxy = np.empty((n, 2), np.float64)
+    gq = np.empty((m, 2), np.float64)
+    gp = np.empty(1, np.float64)
+    rc = lib.oracle_idw_knn_grad(_ptr(data), n, _ptr(q), m, float(p), int(k), _ptr(g), _ptr(Z),
+                                 _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_knn_grad rejected its arguments")
     return {"Z": Z, "grad_z": gz, "grad_xy": gxy, "grad_q": gq, "grad_p": float(gp[0])}

@@ -45,6 +45,7 @@
  *   - its gradients hold each membership set fixed (the sets are piecewise
  *     constant in every input), so they are the global form's derivatives
  *     summed over the members; a query without members contributes none.
+ *     The k-NN form's gradients hold each selection fixed the same way.
  *
  * k-nearest-neighbour variant (the other local form of the related work,
  * Sec. 1): Eq. 1 over the k data points nearest to the query.  Readings:
@@ -815,3 +816,93 @@ int oracle_idw_grad(const double *data, int64_t n, const double *q, int64_t m, d
     free(gp);
     return t;
 }
+
+/* -------------------------------------------------- k-NN gradients */
+
+/*
+ * Gradient of L = sum_j g_j Z(q_j) for the k-NN form (oracle_idw_knn): each
+ * query's selection, the k smallest keys (fl32 d2, index), is held fixed (it
+ * is piecewise constant in every input), so each derivative is the global
+ * one summed over the selected points.  A query with an exact hit passes
+ * g_j to dL/dz of the hit point and nothing else; a query that selects
+ * nothing contributes nothing.  Arguments as oracle_idw_local_grad, with k
+ * in place of the radius.  The selection runs on `nthreads` threads, the
+ * gradient sums on one.  Returns threads used, or -1 on bad arguments / no
+ * memory.
+ */
+int oracle_idw_knn_grad(const double *data, int64_t n, const double *q, int64_t m, double p,
+                        int k, const double *g, double *Z, double *grad_z, double *grad_xy,
+                        double *grad_q, double *grad_p, int nthreads)
+{
+    if (!data || !q || !g || !Z || !grad_z || !grad_xy || !grad_q || !grad_p || n < 1 ||
+        m < 1 || k < 1 || !(p > 0.0) || !isfinite(p))
+        return -1;
+    int64_t *hit = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    float *kd2 = (float *)malloc((size_t)m * sizeof(float));
+    int64_t *nbr = (int64_t *)malloc((size_t)m * (size_t)k * sizeof(int64_t));
+    int32_t *count = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    nsum *acc = (nsum *)calloc((size_t)n * 3, sizeof(nsum)); /* per point: z, x, y */
+    int t = -1;
+    if (hit && kd2 && nbr && count && acc)
+        t = oracle_idw_knn(data, n, q, m, p, k, Z, hit, kd2, nbr, count, nthreads);
+    if (t >= 0) {
+        nsum ptot = {0, 0};
+        for (int64_t j = 0; j < m; j++) {
+            const double gj = g[j], qx = q[2 * j], qy = q[2 * j + 1];
+            const int64_t *sel = nbr + j * (int64_t)k;
+            grad_q[2 * j] = 0.0;
+            grad_q[2 * j + 1] = 0.0;
+            if (hit[j] >= 0) { /* the hit point takes the whole of g_j */
+                nsum_add(&acc[3 * hit[j]], gj);
+                continue;
+            }
+            const int cnt = count[j];
+            if (cnt <= 0)
+                continue;
+            double dmin = INFINITY;
+            for (int s = 0; s < cnt; s++) {
+                const double d2 = sqdist(qx, qy, data[3 * sel[s]], data[3 * sel[s] + 1]);
+                if (d2 < dmin)
+                    dmin = d2;
+            }
+            nsum w0 = {0, 0}, w1 = {0, 0};
+            for (int s = 0; s < cnt; s++) {
+                const double *x = data + 3 * sel[s];
+                const double w = scaled_weight(dmin, sqdist(qx, qy, x[0], x[1]), p);
+                nsum_add(&w0, w);
+                nsum_add(&w1, w * x[2]);
+            }
+            const double S0 = nsum_value(&w0), Zj = nsum_value(&w1) / S0;
+            nsum qsx = {0, 0}, qsy = {0, 0}, qsp = {0, 0};
+            for (int s = 0; s < cnt; s++) {
+                const double *x = data + 3 * sel[s];
+                const double ex = qx - x[0], ey = qy - x[1], e2 = ex * ex + ey * ey;
+                const double w = scaled_weight(dmin, e2, p);
+                const double b = (x[2] - Zj) * w; /* (z_i - Z) w_i */
+                nsum_add(&qsx, b * ex / e2);
+                nsum_add(&qsy, b * ey / e2);
+                nsum_add(&qsp, b * log(e2));
+                nsum_add(&acc[3 * sel[s]], gj * w / S0);
+                const double f = gj * (p / S0) * b / e2;
+                nsum_add(&acc[3 * sel[s] + 1], f * ex);
+                nsum_add(&acc[3 * sel[s] + 2], f * ey);
+            }
+            grad_q[2 * j] = -gj * (p / S0) * nsum_value(&qsx);
+            grad_q[2 * j + 1] = -gj * (p / S0) * nsum_value(&qsy);
+            nsum_add(&ptot, -gj * nsum_value(&qsp) / (2.0 * S0));
+        }
+        for (int64_t i = 0; i < n; i++) {
+            grad_z[i] = nsum_value(&acc[3 * i]);
+            grad_xy[2 * i] = nsum_value(&acc[3 * i + 1]);
+            grad_xy[2 * i + 1] = nsum_value(&acc[3 * i + 2]);
+        }
+        *grad_p = nsum_value(&ptot);
+    }
+    free(hit);
+    free(kd2);
+    free(nbr);
+    free(count);
+    free(acc);
+    return t;
+}
+

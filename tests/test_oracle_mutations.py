@@ -63,6 +63,15 @@ MUTATIONS = [
      "c->grad_p_part[j] = -gj * nsum_value(&sp) / S0;"),
     ("local data-gradient sign", "const double a = gj * (c->p / S0) * (z - c->Z[j]) * w / d2;",
      "const double a = gj * (c->p / S0) * (c->Z[j] - z) * w / d2;"),
+    ("knn gradient over one point fewer",
+     "            for (int s = 0; s < cnt; s++) {\n                const double *x = data + 3 * sel[s];\n                const double ex",
+     "            for (int s = 0; s < cnt - 1; s++) {\n                const double *x = data + 3 * sel[s];\n                const double ex"),
+    ("knn query-gradient sign", "grad_q[2 * j] = -gj * (p / S0) * nsum_value(&qsx);",
+     "grad_q[2 * j] = gj * (p / S0) * nsum_value(&qsx);"),
+    ("knn p-gradient factor 1/2 dropped", "nsum_add(&ptot, -gj * nsum_value(&qsp) / (2.0 * S0));",
+     "nsum_add(&ptot, -gj * nsum_value(&qsp) / S0);"),
+    ("knn data-gradient uses dy for x", "nsum_add(&acc[3 * sel[s] + 1], f * ex);",
+     "nsum_add(&acc[3 * sel[s] + 1], f * ey);"),
 ]
 
 PINS = [
@@ -95,6 +104,10 @@ PINS = [
     pins.test_local_gradient_with_huge_radius_is_the_global_gradient,
     pins.test_local_gradient_sums_and_translation,
     pins.test_local_gradient_at_hits_and_empty_neighbourhoods,
+    lambda: pins.test_knn_gradient_matches_central_differences(3.0),
+    pins.test_knn_gradient_with_k_at_least_n_is_the_global_gradient,
+    pins.test_knn_gradient_sums_and_translation,
+    pins.test_knn_gradient_at_hits_and_empty_selections,
 ]
 
 

@@ -643,3 +643,85 @@ def test_local_gradient_at_hits_and_empty_neighbourhoods():
     assert np.array_equal(G["grad_z"], [0.0, 3.0, 0.0, 0.0])
     assert np.all(G["grad_xy"] == 0) and np.all(G["grad_q"] == 0) and G["grad_p"] == 0
     assert G["Z"][0] == -1.0 and np.isnan(G["Z"][1])
+
+
+# --------------------------------------------------- k-NN gradients
+
+def _knn_loss(data, q, p, k, g, ok):
+    return float(np.dot(g[ok], oracle.idw_knn(data, q, p, k)["Z"][ok]))
+
+
+@pytest.mark.parametrize("p", [2.0, 3.0])
+def test_knn_gradient_matches_central_differences(p):
+    """Central differences of the k-NN oracle's loss, for coordinates whose
+    perturbation changes no selection, against the analytic gradient."""
+    rng = np.random.default_rng(51)
+    n = m = 96
+    k = 9
+    data = np.empty((n, 3), np.float64)
+    data[:, :2] = synthetic.separated_xy(rng, n, 2e-3).astype(np.float32)
+    data[:, 2] = rng.standard_normal(n)
+    q = (synthetic.separated_xy(rng, m, 2e-3) + 1e-3 * rng.random((m, 2))).astype(np.float32)
+    q = q.astype(np.float64)
+    g = rng.standard_normal(m)
+    base = oracle.idw_knn(data, q, p, k)["nbr"]
+    ok = np.ones(m, bool)
+    G = oracle.idw_knn_grad(data, q, p, k, g)
+    eps = 1e-6
+
+    def fd(arr, idx):
+        a = arr.copy(); a[idx] += eps
+        b = arr.copy(); b[idx] -= eps
+        args = ((a, q), (b, q)) if arr is data else ((data, a), (data, b))
+        for d_, q_ in args:  # the selections must not move
+            if not np.array_equal(oracle.idw_knn(d_, q_, p, k)["nbr"], base):
+                return None
+        return (_knn_loss(*args[0], p, k, g, ok) - _knn_loss(*args[1], p, k, g, ok)) / (2 * eps)
+
+    scale_d = max(np.abs(G["grad_xy"]).max(), np.abs(G["grad_z"]).max())
+    checked = 0
+    for i in rng.choice(n, 16, replace=False):
+        for col, ref in ((2, G["grad_z"][i]), (0, G["grad_xy"][i, 0]), (1, G["grad_xy"][i, 1])):
+            v = fd(data, (i, col))
+            if v is not None:
+                assert abs(v - ref) <= 1e-6 * scale_d, (i, col, v, ref)
+                checked += 1
+    scale_q = np.abs(G["grad_q"]).max()
+    for j in rng.choice(m, 16, replace=False):
+        for col in (0, 1):
+            v = fd(q, (j, col))
+            if v is not None:
+                assert abs(v - G["grad_q"][j, col]) <= 1e-6 * scale_q, (j, col)
+                checked += 1
+    assert checked >= 40
+    dp = (_knn_loss(data, q, p + eps, k, g, ok) - _knn_loss(data, q, p - eps, k, g, ok)) / (2 * eps)
+    assert abs(dp - G["grad_p"]) <= 1e-6 * max(1.0, abs(dp))
+
+
+def test_knn_gradient_with_k_at_least_n_is_the_global_gradient():
+    prob = synthetic.uniform_problem(300, 120, seed=52)
+    g = np.random.default_rng(53).standard_normal(120)
+    K = oracle.idw_knn_grad(prob["data"], prob["queries"], 2.5, 300, g)
+    G = oracle.idw_grad(prob["data"], prob["queries"], 2.5, g)
+    for key in ("grad_z", "grad_xy", "grad_q"):
+        assert np.abs(K[key] - G[key]).max() <= 1e-12 * np.abs(G[key]).max(), key
+    assert abs(K["grad_p"] - G["grad_p"]) <= 1e-12 * abs(G["grad_p"])
+
+
+def test_knn_gradient_sums_and_translation():
+    prob = synthetic.config_local(seed=54, n=600, m=400, clustered=True)
+    data, q = prob["data"], prob["queries"]
+    K = oracle.idw_knn_grad(data, q, 2.0, 12, np.ones(q.shape[0]))
+    assert abs(K["grad_z"].sum() - q.shape[0]) <= 1e-10
+    assert np.abs(K["grad_xy"].sum(0) + K["grad_q"].sum(0)).max() <= 1e-9 * np.abs(K["grad_q"]).max()
+
+
+def test_knn_gradient_at_hits_and_empty_selections():
+    data = np.array([[0.1, 0.2, 1.5], [0.7, 0.4, -1.0], [0.3, 0.9, 2.0], [0.7, 0.4, 9.0]],
+                    np.float64)  # index 3 duplicates index 1
+    q = np.array([[0.7, 0.4], [np.nan, 0.5], [0.5, 0.5]], np.float64)
+    g = np.array([3.0, 7.0, -2.0])
+    K = oracle.idw_knn_grad(data, q, 2.0, 8, g)  # k > n: all finite points
+    G = oracle.idw_grad(data, q[2:], 2.0, g[2:])
+    assert np.allclose(K["grad_z"] - np.array([0.0, 3.0, 0.0, 0.0]), G["grad_z"], rtol=0, atol=1e-14)
+    assert np.all(K["grad_q"][:2] == 0) and np.isnan(K["Z"][1]) and K["Z"][0] == -1.0
