@@ -754,6 +754,16 @@ def run_knn(args):
                          "neighbours_match_oracle": bool(np.array_equal(
                              nbr.cpu().numpy()[idx], r["nbr"])),
                          "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+        gout = torch.from_numpy(np.random.default_rng(8).standard_normal(m).astype(np.float32)).cuda()
+        bms = _events_ms(lambda: idw.knn_backward(d, q, 2.0, k, gout), 10, warm=3)
+        _, _, gq, _ = idw.knn_backward(d, q, 2.0, k, gout)
+        Gs = oracle.idw_knn_grad(prob["data"], prob["queries"][np.sort(idx)], 2.0, k,
+                                 gout.cpu().numpy()[np.sort(idx)])
+        gerr = float(np.max(np.abs(gq.cpu().numpy()[np.sort(idx)] - Gs["grad_q"])) /
+                     np.max(np.abs(Gs["grad_q"])))
+        rows.append({"data": "clustered" if clustered else "uniform", "call": "backward",
+                     "n": n, "m": m, "k": k, "p": 2.0, "ms": bms, "queries_s": m / (bms / 1e3),
+                     "grad_q_error_vs_fp64_oracle": gerr, "error_sample_queries": len(idx)})
         build_ms = _events_ms(lambda: idw.LocalIndex(d, k=k).close(), 3, warm=1)
         ix = idw.LocalIndex(d, k=k)
         ms = _events_ms(lambda: ix.knn(q, 2.0, k, out=out), 10, warm=3)
@@ -766,7 +776,8 @@ def run_knn(args):
     _emit("k-nearest-neighbour Eq. 1: N = M = 2^20, queries uniform on [0,1)^2; data uniform "
           "(wave field) or 64 Gaussian blobs (bump field); a one-shot call's time includes the "
           "grid build, a prepared index's call sorts the queries only (index_build_ms: building "
-          "it, allocation included)", rows, metric="knn queries/s", unit="queries/s")
+          "it, allocation included); backward = every gradient (z, data xy, query xy, p) "
+          "including its search", rows, metric="knn queries/s", unit="queries/s")
 
 
 def main():

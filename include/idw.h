@@ -478,6 +478,25 @@ idw_status idw_local_backward(idw_handle_t handle, const float *data_xyz, int64_
                               float *grad_query_xy, double *grad_p, void *stream);
 
 /*
+ * Gradients of the k-nearest-neighbour form: as idw_local_backward, for Z
+ * from idw_interpolate_knn with the same k (1 <= k <= 64).  Each query's
+ * selection (its k smallest keys) is held fixed, so each derivative is the
+ * global one summed over the selected points; a hit passes grad_out[j] to
+ * dL/dz of the lowest coincident index, a query that selects nothing
+ * contributes nothing.  Method: the search of idw_interpolate_knn with its
+ * neighbour lists kept in the workspace, then one thread per query (cell
+ * order) computes dL/dq and its dL/dp share and adds its data-side terms
+ * with FP32 atomics (their order, and so the last bits of grad_z and
+ * grad_data_xy, can vary between calls).  FP64 where the FP32 values leave
+ * their range.  Workspace: that of idw_interpolate_knn plus 4 (k + 2)
+ * bytes per query.  Errors as in idw_interpolate_knn.
+ */
+idw_status idw_knn_backward(idw_handle_t handle, const float *data_xyz, int64_t n,
+                            const float *queries_xy, int64_t m, double p, int32_t k,
+                            const float *grad_out, float *grad_z, float *grad_data_xy,
+                            float *grad_query_xy, double *grad_p, void *stream);
+
+/*
  * Prepared index of the local forms: the data side of idw_interpolate_local
  * or idw_interpolate_knn (bounding box, grid plan, counting sort of the
  * data, and for k-NN the cell-count tables) built once, then queried by any

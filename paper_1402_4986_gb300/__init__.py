@@ -22,7 +22,8 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
     "interpolate_batched", "interpolate_local", "interpolate_knn", "LocalIndex",
-    "local_backward", "LocalIDWFunction", "idw_local",
+    "local_backward", "LocalIDWFunction", "idw_local", "knn_backward", "KnnIDWFunction",
+    "idw_knn",
     "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
@@ -442,6 +443,55 @@ class LocalIDWFunction(torch.autograd.Function):
 def idw_local(data, queries, p=2.0, radius=1.0):
     """Autograd entry for the radius form; p may be a tensor to get dL/dp."""
     return LocalIDWFunction.apply(data, queries, p, radius)
+
+
+def knn_backward(data, queries, p, k, grad_out, need_z=True, need_data_xy=True,
+                 need_query_xy=True, need_p=True, handle: Handle | None = None):
+    """Gradients of the k-NN form (``idw_knn_backward``); returns
+    (gz, gxy, gq, gp), each None when not requested."""
+    _check_inputs(data, queries, PREC_F32_COMP)
+    n, m = data.shape[0], queries.shape[0]
+    dev = data.device
+    gz = torch.empty(n, dtype=torch.float32, device=dev) if need_z else None
+    gxy = torch.empty(n, 2, dtype=torch.float32, device=dev) if need_data_xy else None
+    gq = torch.empty(m, 2, dtype=torch.float32, device=dev) if need_query_xy else None
+    gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
+    h = handle or get_handle(dev)
+    g = grad_out.contiguous().to(torch.float32)
+    st = h.lib.idw_knn_backward(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), int(k),
+                                _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), _stream(data))
+    _lib.check(st, "idw_knn_backward", h.ptr)
+    return gz, gxy, gq, gp
+
+
+class KnnIDWFunction(torch.autograd.Function):
+    """Differentiable k-NN form with the hand-written adjoint (each query's
+    selection held fixed)."""
+
+    @staticmethod
+    def forward(ctx, data, queries, p, k):
+        pv = float(p.item()) if torch.is_tensor(p) else float(p)
+        Z = interpolate_knn(data.detach().contiguous(), queries.detach().contiguous(), pv, int(k))
+        ctx.save_for_backward(data, queries)
+        ctx.p, ctx.k, ctx.p_is_tensor = pv, int(k), torch.is_tensor(p)
+        return Z
+
+    @staticmethod
+    def backward(ctx, grad):
+        data, queries = ctx.saved_tensors
+        need_d, need_q, need_p, _ = ctx.needs_input_grad
+        want_p = need_p and ctx.p_is_tensor
+        gz, gxy, gq, gp = knn_backward(data.detach().contiguous(), queries.detach().contiguous(),
+                                       ctx.p, ctx.k, grad, need_z=need_d, need_data_xy=need_d,
+                                       need_query_xy=need_q, need_p=want_p)
+        gdata = torch.cat([gxy, gz[:, None]], 1) if need_d else None
+        gp_out = gp.to(torch.float32).reshape(()) if want_p else None
+        return gdata, gq if need_q else None, gp_out, None
+
+
+def idw_knn(data, queries, p=2.0, k=16):
+    """Autograd entry for the k-NN form; p may be a tensor to get dL/dp."""
+    return KnnIDWFunction.apply(data, queries, p, k)
 
 
 def sync_status(device=None, handle: Handle | None = None):

@@ -980,7 +980,7 @@ __global__ void __maxnreg__(64)
                      const float4* __restrict__ qrec, const float* __restrict__ data, int64_t n,
                      int64_t m,
                      double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
-                     float* __restrict__ kd2_out) {
+                     float* __restrict__ kd2_out, int32_t* __restrict__ hit_out) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= m) return;  // no block-wide barrier in this kernel
@@ -1201,6 +1201,7 @@ __global__ void __maxnreg__(64)
     }
   }
   out[j] = zv;
+  if (hit_out) hit_out[j] = best_hit != INT_MAX ? best_hit : -1;
   if (nbr_out) {
     // Heap sort: the largest remaining key goes to the end of the row.
     int32_t* row = nbr_out + int64_t(j) * k;
@@ -1211,6 +1212,152 @@ __global__ void __maxnreg__(64)
       const u64 last = hp.h[(n - 1) * kKnnThreads];
       if (n > 1) hp.replace_top(last, n - 1);
     }
+  }
+}
+
+// ------------------------------------------------------ k-NN gradients
+//
+// The k-NN form's gradients hold each query's selection fixed (it is
+// piecewise constant in every input): the derivatives of Eq. 1 summed over
+// the selected points, as for the radius form.  The search runs first, with
+// neighbour lists and hits kept in the workspace; then one thread per query
+// (cell order, so neighbouring threads share points) walks its list, which
+// is in key order: its first entry's FP32 d^2 is d2_min, so the scaled
+// weights (d2_min / d^2)^(p/2) need no rescaling.  A selection is not
+// bounded by a fixed radius, so the data-side terms are added with FP32
+// atomics (their order, and so the last bits, can vary between calls).
+
+// The FP64 path of one k-NN query: adds its data-side terms, returns
+// (dL/dqx, dL/dqy) and its dL/dp share.  Out of line (rare).
+struct KnnGradF64 {
+  float gqx, gqy;
+  double gp;
+};
+__device__ __noinline__ KnnGradF64 knn_grad_query_f64(const int32_t* __restrict__ row, int cnt,
+                                                      const float* __restrict__ data, float qx,
+                                                      float qy, double p, float gj,
+                                                      float* __restrict__ grad_z,
+                                                      float* __restrict__ grad_xy) {
+  double dmin = INFINITY;
+  for (int s = 0; s < cnt; ++s) {
+    const float* x = data + 3 * int64_t(row[s]);
+    const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+    dmin = fmin(dmin, ex * ex + ey * ey);
+  }
+  double s0 = 0.0, s1 = 0.0;
+  for (int s = 0; s < cnt; ++s) {
+    const float* x = data + 3 * int64_t(row[s]);
+    const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+    const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+    s0 += w;
+    s1 += w * double(x[2]);
+  }
+  const double Z = s1 / s0, c = double(gj) / s0;
+  double ax = 0.0, ay = 0.0, al = 0.0;
+  for (int s = 0; s < cnt; ++s) {
+    const int64_t i = row[s];
+    const float* x = data + 3 * i;
+    const double ex = double(qx) - x[0], ey = double(qy) - x[1], e2 = ex * ex + ey * ey;
+    const double w = pow(dmin / e2, 0.5 * p);
+    const double a = (double(x[2]) - Z) * w;
+    ax += a * ex / e2;
+    ay += a * ey / e2;
+    al += a * log(e2 / dmin);
+    if (grad_z) atomicAdd(&grad_z[i], static_cast<float>(c * w));
+    if (grad_xy) {
+      atomicAdd(&grad_xy[2 * i], static_cast<float>(c * p * a * ex / e2));
+      atomicAdd(&grad_xy[2 * i + 1], static_cast<float>(c * p * a * ey / e2));
+    }
+  }
+  KnnGradF64 r;
+  r.gqx = static_cast<float>(-c * p * ax);
+  r.gqy = static_cast<float>(-c * p * ay);
+  r.gp = -0.5 * c * al;
+  return r;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLocalThreads)
+    knn_grad_kernel(const float4* __restrict__ qrec, int64_t m, const float* __restrict__ data,
+                    int64_t n, const int32_t* __restrict__ nbr, const int32_t* __restrict__ hit,
+                    int k, double p, const float* __restrict__ grad_out,
+                    float* __restrict__ grad_z, float* __restrict__ grad_xy,
+                    float* __restrict__ grad_q, double* __restrict__ grad_p) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double gp = 0.0;  // every lane joins the warp sum
+  if (t < m) {
+    const float4 r = qrec[t];
+    const float qx = r.x, qy = r.y;
+    const int j = __float_as_int(r.z);
+    if (dcheck(j >= 0 && j < m, kSiteOutput)) {
+      const float gj = grad_out[j];
+      const int32_t* row = nbr + int64_t(j) * k;
+      const int h = hit[j];
+      int cnt = 0;
+      while (cnt < k && row[cnt] >= 0) ++cnt;
+      float gqx = 0.f, gqy = 0.f;
+      if (h >= 0) {
+        if (grad_z && dcheck(h < n, kSiteData)) atomicAdd(&grad_z[h], gj);
+      } else if (cnt > 0) {
+        const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+        const float* x0 = data + 3 * int64_t(row[0]);
+        const float d2min = fp32_d2(qx, qy, x0[0], x0[1]);  // the smallest key
+        bool f32 = d2min >= 0x1p-100f;
+        if (f32) {
+          const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
+          float s0 = 0.f, s1 = 0.f;
+          for (int s = 0; s < cnt; ++s) {
+            const float* x = data + 3 * int64_t(row[s]);
+            const float w = grad_weight<MODE>(fp32_d2(qx, qy, x[0], x[1]), d2min, lmin, hp);
+            s0 += w;
+            s1 = fmaf(w, x[2], s1);
+          }
+          const float Z = s1 / s0, c = gj / s0;
+          const float lmin2 = lg2_approx(d2min);
+          f32 = isfinite(Z) && isfinite(c);
+          if (f32) {
+            float ax = 0.f, ay = 0.f, al = 0.f;
+            for (int s = 0; s < cnt; ++s) {
+              const int64_t i = row[s];
+              if (!dcheck(i >= 0 && i < n, kSiteData)) continue;
+              const float* x = data + 3 * i;
+              const float dx = __fsub_rn(qx, x[0]), dy = __fsub_rn(qy, x[1]);
+              const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+              const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+              const float a = (x[2] - Z) * w, ar = a * rcp_approx(d2);
+              ax = fmaf(ar, dx, ax);
+              ay = fmaf(ar, dy, ay);
+              al = fmaf(a, lg2_approx(d2) - lmin2, al);
+              if (grad_z) atomicAdd(&grad_z[i], c * w);
+              if (grad_xy) {
+                const float b = c * pf * ar;
+                atomicAdd(&grad_xy[2 * i], b * dx);
+                atomicAdd(&grad_xy[2 * i + 1], b * dy);
+              }
+            }
+            gqx = -c * pf * ax;
+            gqy = -c * pf * ay;
+            const float gpf = (-0.5f * 0.6931471805599453f) * c * al;
+            gp = gpf;
+          }
+        }
+        if (!f32) {
+          const KnnGradF64 r64 =
+              knn_grad_query_f64(row, cnt, data, qx, qy, p, gj, grad_z, grad_xy);
+          gqx = r64.gqx;
+          gqy = r64.gqy;
+          gp = r64.gp;
+        }
+      }
+      if (grad_q) {
+        grad_q[2 * int64_t(j)] = gqx;
+        grad_q[2 * int64_t(j) + 1] = gqy;
+      }
+    }
+  }
+  if (grad_p) {
+    gp = warp_sum(gp);
+    if ((threadIdx.x & 31) == 0 && gp != 0.0) atomicAdd(grad_p, gp);
   }
 }
 
@@ -1361,6 +1508,37 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   return cudaGetLastError();
 }
 
+size_t knn_grad_scratch_bytes(int64_t m, int k) {
+  return round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(m) * size_t(k) * 4, 256);
+}
+
+cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
+                                double p, int k, const float* grad_out, float* grad_z,
+                                float* grad_xy, float* grad_q, double* grad_p, void* workspace,
+                                const LocalLayout& L, int sm_count, cudaStream_t s) {
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  float* zbuf = reinterpret_cast<float*>(ws + L.bytes);
+  int32_t* hit = reinterpret_cast<int32_t*>(ws + L.bytes + round_up(size_t(m) * 4, 256));
+  int32_t* nbr = reinterpret_cast<int32_t*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256));
+  cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
+                             s, hit);
+  if (e != cudaSuccess) return e;
+  if (grad_z && (e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
+  if (grad_xy && (e = cudaMemsetAsync(grad_xy, 0, size_t(n) * 8, s)) != cudaSuccess) return e;
+  if (grad_p && (e = cudaMemsetAsync(grad_p, 0, sizeof(double), s)) != cudaSuccess) return e;
+  const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
+  const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
+  if (p == 2.0)
+    knn_grad_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k, p,
+                                                           grad_out, grad_z, grad_xy, grad_q,
+                                                           grad_p);
+  else
+    knn_grad_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k,
+                                                                 p, grad_out, grad_z, grad_xy,
+                                                                 grad_q, grad_p);
+  return cudaGetLastError();
+}
+
 cudaError_t debug_check_failures(unsigned* sites, bool* enabled) {
 #ifdef IDW_DEBUG_CHECKS
   *enabled = true;
@@ -1379,7 +1557,7 @@ size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
 
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
-                       const LocalLayout& L, int sm_count, cudaStream_t s) {
+                       const LocalLayout& L, int sm_count, cudaStream_t s, int32_t* hit_out) {
   const size_t smem = knn_smem_bytes(k);
   cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1403,10 +1581,12 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
+        hit_out);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
+        hit_out);
   return cudaGetLastError();
 }
 
@@ -1576,10 +1756,12 @@ cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const 
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out,
+        nullptr);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out);
+        grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out,
+        nullptr);
   return cudaGetLastError();
 }
 

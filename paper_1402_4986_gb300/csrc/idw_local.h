@@ -44,11 +44,23 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
 cudaError_t debug_check_failures(unsigned* sites, bool* enabled);
 
 // The k-nearest-neighbour form (1 <= k <= kKnnMax): same grid build, then
-// a ring search per query.  nbr_out (m x k) and kd2_out (m) may be null.
+// a square search per query.  nbr_out (m x k), kd2_out (m) and hit_out (m:
+// the lowest coincident data index, or -1) may be null.
 constexpr int kKnnMax = 64;
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
-                       const LocalLayout& L, int sm_count, cudaStream_t s);
+                       const LocalLayout& L, int sm_count, cudaStream_t s,
+                       int32_t* hit_out = nullptr);
+
+// Gradients of the k-NN form (each selection held fixed): the search with
+// neighbour lists and hits kept in the workspace after L.bytes (plus
+// knn_grad_scratch_bytes(m, k)), then one kernel per query that adds the
+// data-side terms with atomics.  Outputs as launch_local_backward.
+size_t knn_grad_scratch_bytes(int64_t m, int k);
+cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
+                                double p, int k, const float* grad_out, float* grad_z,
+                                float* grad_xy, float* grad_q, double* grad_p, void* workspace,
+                                const LocalLayout& L, int sm_count, cudaStream_t s);
 
 // A prepared index: the data side of a local form built once and queried
 // by many calls.  The index's own buffer holds the plan, the data cell

@@ -55,6 +55,9 @@ for name, data, q in cases:
     assert np.max(np.abs(gzl - Gl)) <= 1e-4 * max(np.max(np.abs(Gl)), 1e-30), name
     _, cnt_ix = idw.LocalIndex(d, radius=0.03).interpolate(qq, 2.0, 0.02, counts=True)
     assert np.array_equal(cnt_ix.cpu().numpy(), oracle.idw_local(data, q, 2.0, 0.02)[2]), name
+    gzk = idw.knn_backward(d, qq, 2.0, 9, gl)[0].cpu().numpy()
+    Gk = oracle.idw_knn_grad(data, q, 2.0, 9, gl.cpu().numpy())["grad_z"]
+    assert np.max(np.abs(gzk - Gk)) <= 1e-4 * max(np.max(np.abs(Gk)), 1e-30), name
     kix = idw.LocalIndex(d, k=9)
     for k in (1, 9, 33):
         Zk, nbr = idw.interpolate_knn(d, qq, 2.0, k, neighbours=True)

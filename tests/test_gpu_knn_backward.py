@@ -1,0 +1,141 @@
+"""GPU parity of the k-NN form's gradients against the FP64 oracle.
+
+``idw_knn_backward`` holds each query's selection fixed, as the oracle does
+(``oracle.idw_knn_grad``, pinned by central differences and invariants).
+Each gradient must match the oracle's to 1e-4 of its largest magnitude.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def idw():
+    from paper_1402_4986_gb300 import build
+    build.build()
+    import paper_1402_4986_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / scale) if scale > 0 else float(np.max(np.abs(a)))
+
+
+def _compare(idw, data, q, p, k, g, tol=TOL):
+    gz, gxy, gq, gp = idw.knn_backward(_dev(data), _dev(q), p, k, _dev(g))
+    torch.cuda.synchronize()
+    G = oracle.idw_knn_grad(data, q, p, k, g)
+    errs = {"z": _rel(gz.cpu().numpy(), G["grad_z"]),
+            "xy": _rel(gxy.cpu().numpy(), G["grad_xy"]),
+            "q": _rel(gq.cpu().numpy(), G["grad_q"]),
+            "p": abs(float(gp.cpu()[0]) - G["grad_p"]) / max(abs(G["grad_p"]), 1e-300)}
+    for key, e in errs.items():
+        assert e <= tol, (key, errs)
+    return G, (gz, gxy, gq, gp)
+
+
+@pytest.mark.parametrize("k", [1, 8, 32, 64])
+@pytest.mark.parametrize("p", [2.0, 3.5])
+def test_uniform_ragged_with_hits(idw, k, p):
+    prob = synthetic.uniform_problem(5003, 2001, seed=131, exact_hits=7)
+    g = np.random.default_rng(132).standard_normal(2001).astype(np.float32)
+    _compare(idw, prob["data"], prob["queries"], p, k, g)
+
+
+def test_clustered(idw):
+    prob = synthetic.config_local(seed=133, n=20000, m=3000, clustered=True)
+    g = np.random.default_rng(134).standard_normal(3000).astype(np.float32)
+    for k in (4, 32):
+        _compare(idw, prob["data"], prob["queries"], 2.0, k, g)
+
+
+def test_hits_duplicates_and_few_points(idw):
+    data = np.array([[0.1, 0.2, 1.5], [0.7, 0.4, -1.0], [0.3, 0.9, 2.0], [0.7, 0.4, 9.0]],
+                    np.float32)  # index 3 duplicates index 1
+    q = np.array([[0.7, 0.4], [np.nan, 0.5], [0.5, 0.5], [0.31, 0.88]], np.float32)
+    g = np.array([3.0, 7.0, -2.0, 1.5], np.float32)
+    for k in (1, 3, 8):  # k = 8 > n: every finite point
+        G, (_, _, gq, _) = _compare(idw, data, q, 2.0, k, g)
+        assert np.all(gq.cpu().numpy()[:2] == 0)
+
+
+def test_fp64_path_and_non_finite_points(idw):
+    rng = np.random.default_rng(135)
+    xy = (rng.random((500, 2)) * 1e-17).astype(np.float32)
+    tiny = np.concatenate([xy, rng.standard_normal((500, 1)).astype(np.float32)], 1)
+    q = (rng.random((120, 2)) * 1e-17).astype(np.float32)
+    _compare(idw, tiny, q, 2.5, 8, rng.standard_normal(120).astype(np.float32))
+    prob = synthetic.uniform_problem(3000, 600, seed=136)
+    data = prob["data"].copy()
+    data[::11, 0] = np.nan
+    data[3::13, 1] = np.inf
+    G, (gz, gxy, _, _) = _compare(idw, data, prob["queries"], 12.0, 16,
+                                  rng.standard_normal(600).astype(np.float32))
+    bad = ~np.isfinite(data[:, :2]).all(1)
+    assert np.all(gz.cpu().numpy()[bad] == 0) and np.all(gxy.cpu().numpy()[bad] == 0)
+
+
+def test_partial_outputs_and_errors(idw):
+    prob = synthetic.uniform_problem(2000, 500, seed=137)
+    d, q = _dev(prob["data"]), _dev(prob["queries"])
+    g = _dev(np.ones(500))
+    full = idw.knn_backward(d, q, 2.0, 8, g)
+    only_q = idw.knn_backward(d, q, 2.0, 8, g, need_z=False, need_data_xy=False, need_p=False)
+    assert only_q[0] is None and only_q[1] is None and only_q[3] is None
+    assert torch.allclose(only_q[2], full[2], rtol=0, atol=1e-5 * float(full[2].abs().max()))
+    for bad_k in (0, 65):
+        with pytest.raises(idw.IDWError):
+            idw.knn_backward(d, q, 2.0, bad_k, g)
+    gz, gxy, gq, gp = idw.knn_backward(d, q[:0], 2.0, 8, g[:0])
+    assert float(gz.abs().max()) == 0 and float(gxy.abs().max()) == 0 and float(gp[0]) == 0
+
+
+def test_autograd_function(idw):
+    prob = synthetic.uniform_problem(4000, 1500, seed=138)
+    data, q = prob["data"], prob["queries"]
+    d = _dev(data).requires_grad_(True)
+    qq = _dev(q).requires_grad_(True)
+    p = torch.tensor(2.5, device="cuda", requires_grad=True)
+    Z = idw.idw_knn(d, qq, p, 16)
+    w = torch.from_numpy(np.random.default_rng(139).standard_normal(1500).astype(np.float32)).cuda()
+    (Z * w).sum().backward()
+    G = oracle.idw_knn_grad(data, q, 2.5, 16, w.cpu().numpy())
+    gd = d.grad.cpu().numpy().astype(np.float64)
+    assert _rel(gd[:, 2], G["grad_z"]) <= TOL
+    assert _rel(gd[:, :2], G["grad_xy"]) <= TOL
+    assert _rel(qq.grad.cpu().numpy(), G["grad_q"]) <= TOL
+    assert abs(float(p.grad) - G["grad_p"]) <= TOL * abs(G["grad_p"])
+
+
+def test_full_size_sampled_and_sum_rules(idw):
+    """N = M = 2^20, k = 32: dL/dq on 128 sampled queries against the oracle;
+    over all queries, dL/dz sums to sum_j g_j and the coordinate gradients
+    cancel (translation)."""
+    prob = synthetic.config_local()
+    data, q = prob["data"], prob["queries"]
+    m = q.shape[0]
+    g = np.random.default_rng(140).standard_normal(m).astype(np.float32)
+    gz, gxy, gq, gp = idw.knn_backward(_dev(data), _dev(q), 2.0, 32, _dev(g))
+    torch.cuda.synchronize()
+    idx = np.sort(np.random.default_rng(141).choice(m, 128, replace=False))
+    G = oracle.idw_knn_grad(data, q[idx], 2.0, 32, g[idx])
+    assert _rel(gq.cpu().numpy()[idx], G["grad_q"]) <= TOL
+    want = float(np.sum(g.astype(np.float64)))
+    assert abs(float(gz.double().sum()) - want) <= 1e-4 * float(np.sum(np.abs(g)))
+    tot = gxy.double().sum(0) + gq.double().sum(0)
+    assert float(tot.abs().max()) <= 1e-4 * float(gq.double().abs().sum(0).max())
