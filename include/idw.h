@@ -486,10 +486,12 @@ idw_status idw_local_backward(idw_handle_t handle, const float *data_xyz, int64_
  * contributes nothing.  Method: the search of idw_interpolate_knn with its
  * neighbour lists kept in the workspace, then one thread per query (cell
  * order) computes dL/dq and its dL/dp share and adds its data-side terms
- * with FP32 atomics (their order, and so the last bits of grad_z and
+ * with one 16-byte vector atomic per (query, neighbour) pair into a
+ * per-point accumulator (their order, and so the last bits of grad_z and
  * grad_data_xy, can vary between calls).  FP64 where the FP32 values leave
  * their range.  Workspace: that of idw_interpolate_knn plus 4 (k + 2)
- * bytes per query.  Errors as in idw_interpolate_knn.
+ * bytes per query and 16 per data point.  Errors as in idw_interpolate_knn;
+ * grad_data_xy must be 8-byte aligned.
  */
 idw_status idw_knn_backward(idw_handle_t handle, const float *data_xyz, int64_t n,
                             const float *queries_xy, int64_t m, double p, int32_t k,

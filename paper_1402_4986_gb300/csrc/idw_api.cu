@@ -716,7 +716,7 @@ idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const 
   idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, grad_out);
   if (st != IDW_OK) return st;
   if (k < 1 || k > idw::kKnnMax) return IDW_ERR_INVALID_ARG;
-  if ((grad_z && !aligned(grad_z, 4)) || (grad_data_xy && !aligned(grad_data_xy, 4)) ||
+  if ((grad_z && !aligned(grad_z, 4)) || (grad_data_xy && !aligned(grad_data_xy, 8)) ||
       (grad_query_xy && !aligned(grad_query_xy, 4)) || (grad_p && !aligned(grad_p, 8)))
     return IDW_ERR_ALIGNMENT;
   DeviceGuard guard(h->device);
@@ -732,7 +732,7 @@ idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const 
   st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}, {grad_out, m, false}}, s);
   if (st != IDW_OK) return st;
   const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
-  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::knn_grad_scratch_bytes(m, k));
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::knn_grad_scratch_bytes(n, m, k));
   if (st != IDW_OK) return st;
   e = idw::launch_knn_backward(data, n, queries, m, p, k, grad_out, grad_z, grad_data_xy,
                                grad_query_xy, grad_p, h->ws, L, h->sm_count, s);

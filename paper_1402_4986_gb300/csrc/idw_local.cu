@@ -1224,8 +1224,10 @@ __global__ void __maxnreg__(64)
 // (cell order, so neighbouring threads share points) walks its list, which
 // is in key order: its first entry's FP32 d^2 is d2_min, so the scaled
 // weights (d2_min / d^2)^(p/2) need no rescaling.  A selection is not
-// bounded by a fixed radius, so the data-side terms are added with FP32
-// atomics (their order, and so the last bits, can vary between calls).
+// bounded by a fixed radius, so the data-side terms (dL/dz, dL/dx, dL/dy)
+// are added to a per-point float4 with one 16-byte vector atomic per pair
+// (a third of the L2 operations of three scalar ones; their order, and so
+// the last bits, can vary between calls), then copied out.
 
 // The FP64 path of one k-NN query: adds its data-side terms, returns
 // (dL/dqx, dL/dqy) and its dL/dp share.  Out of line (rare).
@@ -1236,8 +1238,7 @@ struct KnnGradF64 {
 __device__ __noinline__ KnnGradF64 knn_grad_query_f64(const int32_t* __restrict__ row, int cnt,
                                                       const float* __restrict__ data, float qx,
                                                       float qy, double p, float gj,
-                                                      float* __restrict__ grad_z,
-                                                      float* __restrict__ grad_xy) {
+                                                      float4* __restrict__ acc) {
   double dmin = INFINITY;
   for (int s = 0; s < cnt; ++s) {
     const float* x = data + 3 * int64_t(row[s]);
@@ -1263,11 +1264,9 @@ __device__ __noinline__ KnnGradF64 knn_grad_query_f64(const int32_t* __restrict_
     ax += a * ex / e2;
     ay += a * ey / e2;
     al += a * log(e2 / dmin);
-    if (grad_z) atomicAdd(&grad_z[i], static_cast<float>(c * w));
-    if (grad_xy) {
-      atomicAdd(&grad_xy[2 * i], static_cast<float>(c * p * a * ex / e2));
-      atomicAdd(&grad_xy[2 * i + 1], static_cast<float>(c * p * a * ey / e2));
-    }
+    if (acc)
+      atomicAdd(&acc[i], make_float4(static_cast<float>(c * w), static_cast<float>(c * p * a * ex / e2),
+                                     static_cast<float>(c * p * a * ey / e2), 0.f));
   }
   KnnGradF64 r;
   r.gqx = static_cast<float>(-c * p * ax);
@@ -1281,8 +1280,8 @@ __global__ void __launch_bounds__(kLocalThreads)
     knn_grad_kernel(const float4* __restrict__ qrec, int64_t m, const float* __restrict__ data,
                     int64_t n, const int32_t* __restrict__ nbr, const int32_t* __restrict__ hit,
                     int k, double p, const float* __restrict__ grad_out,
-                    float* __restrict__ grad_z, float* __restrict__ grad_xy,
-                    float* __restrict__ grad_q, double* __restrict__ grad_p) {
+                    float4* __restrict__ acc, float* __restrict__ grad_q,
+                    double* __restrict__ grad_p) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double gp = 0.0;  // every lane joins the warp sum
   if (t < m) {
@@ -1297,7 +1296,7 @@ __global__ void __launch_bounds__(kLocalThreads)
       while (cnt < k && row[cnt] >= 0) ++cnt;
       float gqx = 0.f, gqy = 0.f;
       if (h >= 0) {
-        if (grad_z && dcheck(h < n, kSiteData)) atomicAdd(&grad_z[h], gj);
+        if (acc && dcheck(h < n, kSiteData)) atomicAdd(&acc[h], make_float4(gj, 0.f, 0.f, 0.f));
       } else if (cnt > 0) {
         const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
         const float* x0 = data + 3 * int64_t(row[0]);
@@ -1328,11 +1327,9 @@ __global__ void __launch_bounds__(kLocalThreads)
               ax = fmaf(ar, dx, ax);
               ay = fmaf(ar, dy, ay);
               al = fmaf(a, lg2_approx(d2) - lmin2, al);
-              if (grad_z) atomicAdd(&grad_z[i], c * w);
-              if (grad_xy) {
+              if (acc) {
                 const float b = c * pf * ar;
-                atomicAdd(&grad_xy[2 * i], b * dx);
-                atomicAdd(&grad_xy[2 * i + 1], b * dy);
+                atomicAdd(&acc[i], make_float4(c * w, b * dx, b * dy, 0.f));
               }
             }
             gqx = -c * pf * ax;
@@ -1343,7 +1340,7 @@ __global__ void __launch_bounds__(kLocalThreads)
         }
         if (!f32) {
           const KnnGradF64 r64 =
-              knn_grad_query_f64(row, cnt, data, qx, qy, p, gj, grad_z, grad_xy);
+              knn_grad_query_f64(row, cnt, data, qx, qy, p, gj, acc);
           gqx = r64.gqx;
           gqy = r64.gqy;
           gp = r64.gp;
@@ -1359,6 +1356,17 @@ __global__ void __launch_bounds__(kLocalThreads)
     gp = warp_sum(gp);
     if ((threadIdx.x & 31) == 0 && gp != 0.0) atomicAdd(grad_p, gp);
   }
+}
+
+// Copies the per-point accumulators out to the caller's gradient arrays.
+__global__ void __launch_bounds__(256)
+    knn_grad_copy_kernel(const float4* __restrict__ acc, int64_t n, float* __restrict__ grad_z,
+                         float* __restrict__ grad_xy) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 v = acc[i];
+  if (grad_z) grad_z[i] = v.x;
+  if (grad_xy) reinterpret_cast<float2*>(grad_xy)[i] = make_float2(v.y, v.z);
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -1508,8 +1516,9 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   return cudaGetLastError();
 }
 
-size_t knn_grad_scratch_bytes(int64_t m, int k) {
-  return round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(m) * size_t(k) * 4, 256);
+size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k) {
+  return round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(m) * size_t(k) * 4, 256) +
+         round_up(size_t(n) * 16, 256);
 }
 
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
@@ -1523,19 +1532,23 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
   cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
                              s, hit);
   if (e != cudaSuccess) return e;
-  if (grad_z && (e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
-  if (grad_xy && (e = cudaMemsetAsync(grad_xy, 0, size_t(n) * 8, s)) != cudaSuccess) return e;
+  const bool data_side = grad_z || grad_xy;
+  float4* acc = data_side ? reinterpret_cast<float4*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256) +
+                                                      round_up(size_t(m) * size_t(k) * 4, 256))
+                          : nullptr;
+  if (acc && (e = cudaMemsetAsync(acc, 0, size_t(n) * 16, s)) != cudaSuccess) return e;
   if (grad_p && (e = cudaMemsetAsync(grad_p, 0, sizeof(double), s)) != cudaSuccess) return e;
   const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
   if (p == 2.0)
     knn_grad_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k, p,
-                                                           grad_out, grad_z, grad_xy, grad_q,
-                                                           grad_p);
+                                                           grad_out, acc, grad_q, grad_p);
   else
     knn_grad_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k,
-                                                                 p, grad_out, grad_z, grad_xy,
-                                                                 grad_q, grad_p);
+                                                                 p, grad_out, acc, grad_q, grad_p);
+  if (acc)
+    knn_grad_copy_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(acc, n, grad_z,
+                                                                               grad_xy);
   return cudaGetLastError();
 }
 

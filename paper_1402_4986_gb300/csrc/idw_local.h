@@ -54,9 +54,9 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
 
 // Gradients of the k-NN form (each selection held fixed): the search with
 // neighbour lists and hits kept in the workspace after L.bytes (plus
-// knn_grad_scratch_bytes(m, k)), then one kernel per query that adds the
+// knn_grad_scratch_bytes(n, m, k)), then one kernel per query that adds the
 // data-side terms with atomics.  Outputs as launch_local_backward.
-size_t knn_grad_scratch_bytes(int64_t m, int k);
+size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k);
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
