@@ -12,7 +12,10 @@
  * an arbitrary positive real (Sec. 2.1; typically 2).  The two local forms
  * the paper names among its related work (Sec. 1) are here too: Eq. 1 over
  * the data points within a radius R (idw_interpolate_local) and over the k
- * nearest data points (idw_interpolate_knn).
+ * nearest data points (idw_interpolate_knn), each with a prepared index for
+ * repeated queries (idw_local_index_*).  Every form has gradients with
+ * respect to z, the data and query coordinates, and p (idw_backward,
+ * idw_local_backward, idw_knn_backward).
  *
  * Conventions shared by every entry point:
  *   - A data point is a row (x, y, z): d is the 2-D Euclidean distance in
