@@ -1,7 +1,8 @@
 """Data sets whose 16-byte staged records pass 2^32 bytes (n > 2^28): every
 byte offset and record index on the device must be 64-bit clean.  The
 global, radius-limited and k-NN forms are checked on sampled queries
-against the oracle.  About 12 GB of device memory and 3.3 GB of host memory.
+against the oracle, and the local forms' gradients through their hit and
+sum rules.  About 12 GB of device memory and 3.3 GB of host memory.
 """
 import numpy as np
 import pytest
@@ -81,6 +82,26 @@ def test_adjoint_past_4gb_of_staged_records(problem):
     gxy = gxy.cpu().numpy().astype(np.float64)
     total = gxy.sum(0) + gq.sum(0)
     assert np.all(np.abs(total) <= 1e-4 * (np.abs(gxy).sum(0) + np.abs(gq).sum(0)))
+
+
+def test_local_gradients_past_4gb_of_records(problem):
+    """Both local forms' gradients at n > 2^28: the exact hit's dL/dz lands
+    on data point N - 3, dL/dz sums to sum_j g_j, and the coordinate
+    gradients cancel (translation)."""
+    idw, data, q, d, qq, idx = problem
+    g = np.random.default_rng(6).standard_normal(q.shape[0]).astype(np.float32)
+    gt = torch.from_numpy(g).cuda()
+    for name, fn in (("local", lambda: idw.local_backward(d, qq, 2.0, 2e-4, gt)),
+                     ("knn", lambda: idw.knn_backward(d, qq, 2.0, 16, gt))):
+        gz, gxy, gq, _ = fn()
+        torch.cuda.synchronize()
+        assert abs(float(gz[N - 3]) - float(g[7])) <= 1e-6 * abs(float(g[7])), name
+        assert abs(float(gz.double().sum()) - float(g.astype(np.float64).sum())) <= \
+            1e-4 * float(np.abs(g).sum()), name
+        tot = gxy.double().sum(0) + gq.double().sum(0)
+        assert float(tot.abs().max()) <= 1e-4 * float(gq.double().abs().sum(0).max()), name
+        del gz, gxy, gq
+        torch.cuda.empty_cache()
 
 
 def test_large_m_past_4gb_of_partials_and_query_records():
