@@ -402,6 +402,24 @@ def _events_ms(fn, reps, warm=1):
     return a.elapsed_time(b) / reps
 
 
+def _oracle_queries_s(args, fn, m, label):
+    """The FP64 oracle timed on the host cores over a bounded random sample
+    of the workload's queries (about a third of --cpu-seconds)."""
+    if args.no_cpu_baseline:
+        return None
+    cores = os.cpu_count() or 1
+    t = time.perf_counter()
+    fn(np.arange(64), cores)
+    rate = 64 / (time.perf_counter() - t)
+    S = int(min(max(256, args.cpu_seconds / 3 * rate), m))
+    idx = np.sort(np.random.default_rng(9).choice(m, S, replace=False))
+    t = time.perf_counter()
+    fn(idx, cores)
+    cpu_s = time.perf_counter() - t
+    return {"value": S / cpu_s, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{S} random queries of {label} ({cpu_s:.1f} s)"}
+
+
 def _emit(workload, rows, **extra):
     line = {"metric": "pairs/s", "unit": UNIT, "data": "synthetic", "dtype": "f32",
             "config": {"workload": workload}, "rows": rows}
@@ -715,12 +733,17 @@ def run_local(args):
                      "queries_s": m / (ms / 1e3), "index_build_ms": build_ms,
                      "counts_match_one_shot": bool(torch.equal(cix, cnt))})
         ix.close()
+    base = synthetic.config_local(members=32.0)
+    cpu = _oracle_queries_s(
+        args, lambda ix, c: oracle.idw_local(base["data"], base["queries"][ix], 2.0,
+                                             base["radius"], threads=c),
+        base["queries"].shape[0], "the uniform K = 32, p = 2 workload, each against all N points")
     _emit("local (radius-limited) Eq. 1: N = M = 2^20, queries uniform on [0,1)^2, "
           "R = sqrt(K / (pi N)); data uniform (wave field) or 64 Gaussian blobs (bump field); "
           "a one-shot call's time includes the grid build, a prepared index's call sorts the "
           "queries only (index_build_ms: building it, allocation included); backward = every "
           "gradient (z, data xy, query xy, p) including its grid build", rows,
-          metric="local queries/s", unit="queries/s")
+          metric="local queries/s", unit="queries/s", cpu_baseline=cpu)
 
 
 def run_knn(args):
@@ -773,11 +796,16 @@ def run_knn(args):
                      "index_build_ms": build_ms,
                      "neighbours_match_one_shot": bool(torch.equal(nix, nbr))})
         ix.close()
+    base = synthetic.config_local()
+    cpu = _oracle_queries_s(
+        args, lambda ix, c: oracle.idw_knn(base["data"], base["queries"][ix], 2.0, 32, threads=c),
+        base["queries"].shape[0], "the uniform k = 32, p = 2 workload, each against all N points")
     _emit("k-nearest-neighbour Eq. 1: N = M = 2^20, queries uniform on [0,1)^2; data uniform "
           "(wave field) or 64 Gaussian blobs (bump field); a one-shot call's time includes the "
           "grid build, a prepared index's call sorts the queries only (index_build_ms: building "
           "it, allocation included); backward = every gradient (z, data xy, query xy, p) "
-          "including its search", rows, metric="knn queries/s", unit="queries/s")
+          "including its search", rows, metric="knn queries/s", unit="queries/s",
+          cpu_baseline=cpu)
 
 
 def main():
