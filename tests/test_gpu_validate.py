@@ -60,10 +60,23 @@ def test_every_entry_point_refuses_non_finite_inputs(idw, vh, bad):
         _expect_not_finite(idw, lambda: idw.interpolate_knn(dd, qq, 2.0, 8, handle=vh))
         _expect_not_finite(idw, lambda: idw.paper_interpolate(dd, qq, 2.0, handle=vh))
         _expect_not_finite(idw, lambda: idw.interpolate_batched([d, dd], [q, qq], 2.0, handle=vh))
+        _expect_not_finite(idw, lambda: idw.local_backward(dd, qq, 2.0, 0.05, torch.ones(
+            qq.shape[0], device="cuda"), handle=vh))
+        _expect_not_finite(idw, lambda: idw.knn_backward(dd, qq, 2.0, 8, torch.ones(
+            qq.shape[0], device="cuda"), handle=vh))
+    # The prepared index scans its data when built and its queries per call.
+    _expect_not_finite(idw, lambda: idw.LocalIndex(dbad, radius=0.05, handle=vh))
+    _expect_not_finite(idw, lambda: idw.LocalIndex(dbad, k=8, handle=vh))
+    rix = idw.LocalIndex(d, radius=0.05, handle=vh)
+    kix = idw.LocalIndex(d, k=8, handle=vh)
+    _expect_not_finite(idw, lambda: rix.interpolate(qbad, 2.0))
+    _expect_not_finite(idw, lambda: kix.knn(qbad, 2.0))
     Z, s0, hit = idw.interpolate_saved(d, q, 2.0, handle=vh)
     g = torch.ones(q.shape[0], device="cuda")
     g[7] = bad
     _expect_not_finite(idw, lambda: idw.backward(d, q, 2.0, Z, s0, hit, g, handle=vh))
+    _expect_not_finite(idw, lambda: idw.local_backward(d, q, 2.0, 0.05, g, handle=vh))
+    _expect_not_finite(idw, lambda: idw.knn_backward(d, q, 2.0, 8, g, handle=vh))
 
 
 def test_clean_inputs_give_the_same_results(idw, vh):
@@ -71,7 +84,9 @@ def test_clean_inputs_give_the_same_results(idw, vh):
     plain = idw.Handle(torch.cuda.current_device())
     for fn in (lambda h: idw.interpolate(d, q, 2.0, handle=h),
                lambda h: idw.interpolate_local(d, q, 2.0, 0.05, handle=h),
-               lambda h: idw.interpolate_knn(d, q, 2.0, 8, handle=h)):
+               lambda h: idw.interpolate_knn(d, q, 2.0, 8, handle=h),
+               lambda h: idw.LocalIndex(d, radius=0.05, handle=h).interpolate(q, 2.0),
+               lambda h: idw.LocalIndex(d, k=8, handle=h).knn(q, 2.0)):
         a = fn(vh).cpu().numpy()
         b = fn(plain).cpu().numpy()
         assert np.array_equal(np.isnan(a), np.isnan(b))
