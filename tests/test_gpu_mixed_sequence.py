@@ -68,5 +68,18 @@ def test_interleaved_entry_points_on_one_handle(idw):
         Zd = idw.interpolate(_dev(data, torch.float64), _dev(q, torch.float64), 2.5, "f64",
                              handle=h)
         assert _err(Zd, Z64, data) <= 1e-13
+
+        # The local forms' gradients and prepared indexes on the same handle.
+        gl = torch.linspace(-1.0, 1.0, m, device="cuda")
+        Gl = oracle.idw_local_grad(data, q, 2.0, R, gl.cpu().numpy())
+        gz, _, gq, _ = idw.local_backward(d, qq, 2.0, R, gl, handle=h)
+        assert np.max(np.abs(gz.cpu().numpy() - Gl["grad_z"])) <= 1e-4 * np.max(np.abs(Gl["grad_z"]))
+        Gk = oracle.idw_knn_grad(data, q, 3.0, 7, gl.cpu().numpy())
+        _, _, gq, _ = idw.knn_backward(d, qq, 3.0, 7, gl, handle=h)
+        assert np.max(np.abs(gq.cpu().numpy() - Gk["grad_q"])) <= 1e-4 * np.max(np.abs(Gk["grad_q"]))
+        rix = idw.LocalIndex(d, radius=R, handle=h)
+        assert np.array_equal(rix.interpolate(qq, 2.0, counts=True)[1].cpu().numpy(), cnt64)
+        kix = idw.LocalIndex(d, k=7, handle=h)
+        assert np.array_equal(kix.knn(qq, 3.0, neighbours=True)[1].cpu().numpy(), rk["nbr"])
     idw.sync_status(handle=h)
     h.close()
