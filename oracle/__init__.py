@@ -1,6 +1,6 @@
 """FP64 CPU oracle for Shepard IDW (Sec. 2.1, Eq. 1): the global form, its
 gradients, and the radius-limited and k-nearest-neighbour local forms of
-the related work (Sec. 1).
+the related work (Sec. 1) with their gradients.
 
 TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import

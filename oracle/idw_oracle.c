@@ -1,6 +1,7 @@
 /*
  * FP64 CPU oracle for global (standard) Shepard inverse-distance weighting,
- * its gradients, and the radius-limited and k-nearest-neighbour local forms.
+ * its gradients, and the radius-limited and k-nearest-neighbour local forms
+ * with their gradients.
  *
  * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite, the
  * smoke check and the benchmark's CPU-baseline leg may load this library.
