@@ -402,6 +402,37 @@ def _events_ms(fn, reps, warm=1):
     return a.elapsed_time(b) / reps
 
 
+def _raster_order_rows(idw, d, form, arg, label):
+    """The same data queried on a 1024 x 1024 raster of cell centres (rows
+    in order): one-shot and prepared-index calls with the queries sorted
+    into cells (default) and in the caller's order."""
+    import torch
+    g = (torch.arange(1024, device="cuda", dtype=torch.float64) + 0.5) / 1024
+    yy, xx = torch.meshgrid(g, g, indexing="ij")
+    q = torch.stack([xx.reshape(-1), yy.reshape(-1)], 1).float().contiguous()
+    out = torch.empty(q.shape[0], device="cuda")
+    rows = []
+    for order in (0, 1):
+        h = idw.Handle(torch.cuda.current_device())
+        idw.set_option("local_query_order", order, handle=h)
+        if form == "local":
+            one = lambda: idw.interpolate_local(d, q, 2.0, arg, out=out, handle=h)
+            ix = idw.LocalIndex(d, radius=arg, handle=h)
+            call = lambda: ix.interpolate(q, 2.0, out=out)
+        else:
+            one = lambda: idw.interpolate_knn(d, q, 2.0, arg, out=out, handle=h)
+            ix = idw.LocalIndex(d, k=arg, handle=h)
+            call = lambda: ix.knn(q, 2.0, out=out)
+        for kind, fn in (("one-shot", one), ("prepared index", call)):
+            ms = _events_ms(fn, 10, warm=3)
+            rows.append({"data": "uniform", "queries": "raster 1024 x 1024", "call": kind,
+                         "query_order": "caller" if order else "sorted", label: arg, "p": 2.0,
+                         "ms": ms, "queries_s": q.shape[0] / (ms / 1e3)})
+        ix.close()
+        h.close()
+    return rows
+
+
 def _oracle_queries_s(args, fn, m, label):
     """The FP64 oracle timed on the host cores over a bounded random sample
     of the workload's queries (about a third of --cpu-seconds)."""
@@ -734,6 +765,8 @@ def run_local(args):
                      "counts_match_one_shot": bool(torch.equal(cix, cnt))})
         ix.close()
     base = synthetic.config_local(members=32.0)
+    rows += _raster_order_rows(idw, torch.from_numpy(base["data"]).cuda(), "local",
+                               base["radius"], "radius")
     cpu = _oracle_queries_s(
         args, lambda ix, c: oracle.idw_local(base["data"], base["queries"][ix], 2.0,
                                              base["radius"], threads=c),
@@ -797,6 +830,7 @@ def run_knn(args):
                      "neighbours_match_one_shot": bool(torch.equal(nix, nbr))})
         ix.close()
     base = synthetic.config_local()
+    rows += _raster_order_rows(idw, torch.from_numpy(base["data"]).cuda(), "knn", 32, "k")
     cpu = _oracle_queries_s(
         args, lambda ix, c: oracle.idw_knn(base["data"], base["queries"][ix], 2.0, 32, threads=c),
         base["queries"].shape[0], "the uniform k = 32, p = 2 workload, each against all N points")

@@ -245,6 +245,18 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *                               the stream is being captured.  Off, inputs are
  *                               not scanned and NaN propagates (Eq. 1 is
  *                               evaluated as given).
+ *   IDW_OPT_LOCAL_QUERY_ORDER   0 (default) or 1.  The local forms (radius
+ *                               and k-NN, one-shot and prepared index, and
+ *                               idw_knn_backward) sort the queries into the
+ *                               grid's cells so that neighbouring threads
+ *                               read the same data.  1 keeps the caller's
+ *                               order instead, which saves that sort when
+ *                               the queries already come in spatial order
+ *                               (a raster of prediction points) and costs
+ *                               locality when they do not.  Results are the
+ *                               same either way.  idw_local_backward always
+ *                               sorts (its data-side pass finds queries by
+ *                               cell).
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -256,7 +268,8 @@ typedef enum {
     IDW_OPT_LAST_VARIANT = 4,
     IDW_OPT_TUNED_CLASSES = 5,
     IDW_OPT_STAGING_LAYOUT = 6,
-    IDW_OPT_VALIDATE_INPUTS = 7
+    IDW_OPT_VALIDATE_INPUTS = 7,
+    IDW_OPT_LOCAL_QUERY_ORDER = 8
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

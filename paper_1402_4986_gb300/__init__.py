@@ -503,7 +503,8 @@ def sync_status(device=None, handle: Handle | None = None):
 
 
 def set_option(name: str, value: int, handle: Handle | None = None):
-    """Set a handle option: autotune, sweep_variant, force_general_power."""
+    """Set a handle option (``_lib.OPTIONS``): autotune, sweep_variant,
+    force_general_power, staging_layout, validate_inputs, local_query_order."""
     h = handle or get_handle()
     _lib.check(h.lib.idw_set_option(h.ptr, _lib.OPTIONS[name], int(value)), "idw_set_option")
 

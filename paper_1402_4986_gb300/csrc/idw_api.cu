@@ -37,6 +37,7 @@ struct idw_handle_s {
   // Options (idw_set_option).
   int opt_autotune = 0, opt_variant = -1, opt_force_general = 0, opt_layout = -1;
   int opt_validate = 0;         // scan inputs for NaN / inf before computing
+  int opt_query_order = 0;      // local forms: 1 keeps the caller's query order
   unsigned* vflag = nullptr;    // device word the scan sets
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
@@ -650,7 +651,8 @@ idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_local(data, n, queries, m, p, radius, out, count_out, h->ws, L,
-                                          h->sm_count, static_cast<cudaStream_t>(stream));
+                                          h->sm_count, static_cast<cudaStream_t>(stream),
+                                          h->opt_query_order == 0);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -673,7 +675,8 @@ idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, con
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_knn(data, n, queries, m, p, k, out, nbr_out, kd2_out, h->ws, L,
-                                        h->sm_count, static_cast<cudaStream_t>(stream));
+                                        h->sm_count, static_cast<cudaStream_t>(stream), nullptr,
+                                        h->opt_query_order == 0);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -735,7 +738,8 @@ idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const 
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::knn_grad_scratch_bytes(n, m, k));
   if (st != IDW_OK) return st;
   e = idw::launch_knn_backward(data, n, queries, m, p, k, grad_out, grad_z, grad_data_xy,
-                               grad_query_xy, grad_p, h->ws, L, h->sm_count, s);
+                               grad_query_xy, grad_p, h->ws, L, h->sm_count, s,
+                               h->opt_query_order == 0);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -795,7 +799,8 @@ idw_status idw_local_index_interpolate(idw_handle_t h, idw_local_index_t ix,
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_index_local(ix->mem, ix->X, queries, m, p, radius, out,
-                                                count_out, h->ws, Q, h->sm_count, s);
+                                                count_out, h->ws, Q, h->sm_count, s,
+                                                h->opt_query_order == 0);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -820,7 +825,8 @@ idw_status idw_local_index_knn(idw_handle_t h, idw_local_index_t ix, const float
   st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_index_knn(ix->mem, ix->X, queries, m, p, k, out, nbr_out,
-                                              kd2_out, h->ws, Q, h->sm_count, s);
+                                              kd2_out, h->ws, Q, h->sm_count, s,
+                                              h->opt_query_order == 0);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -870,6 +876,10 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
     case IDW_OPT_VALIDATE_INPUTS:
       h->opt_validate = value != 0;
       return IDW_OK;
+    case IDW_OPT_LOCAL_QUERY_ORDER:
+      if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
+      h->opt_query_order = static_cast<int>(value);
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -885,6 +895,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_TUNED_CLASSES: *value = static_cast<int64_t>(h->tuned.size()); return IDW_OK;
     case IDW_OPT_STAGING_LAYOUT: *value = h->opt_layout; return IDW_OK;
     case IDW_OPT_VALIDATE_INPUTS: *value = h->opt_validate; return IDW_OK;
+    case IDW_OPT_LOCAL_QUERY_ORDER: *value = h->opt_query_order; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

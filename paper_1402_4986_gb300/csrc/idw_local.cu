@@ -439,6 +439,17 @@ __global__ void __launch_bounds__(kSatCols * kSatWarps)
   }
 }
 
+// Query records in the caller's order, (x, y, index, 0): used in place of
+// the query sort when the caller's order is kept.
+__global__ void __launch_bounds__(256)
+    query_identity_kernel(const float* __restrict__ queries, int64_t m,
+                          float4* __restrict__ qrec) {
+  const int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  qrec[j] = make_float4(queries[2 * j], queries[2 * j + 1], __int_as_float(static_cast<int>(j)),
+                        0.f);
+}
+
 // Threads [0, n) place data points as (x, y, z, index), [n, n + m) place
 // queries as (x, y, index, 0).
 __global__ void __launch_bounds__(256)
@@ -1412,7 +1423,7 @@ namespace {
 // histograms, scans, scatter of data and queries into cell order.
 cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries, int64_t m,
                              double radius, int knn_k, void* workspace, const LocalLayout& L,
-                             int sm_count, cudaStream_t s) {
+                             int sm_count, cudaStream_t s, bool sort_queries = true) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   GridDev* grid = reinterpret_cast<GridDev*>(ws + L.off_grid);
   int32_t* counts_d = reinterpret_cast<int32_t*>(ws + L.off_counts_d);
@@ -1432,12 +1443,17 @@ cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries,
   const unsigned zgrid = static_cast<unsigned>(
       std::min<int64_t>(int64_t(sm_count) * 8, (L.max_cells + 4 + 255) / 256));
   zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts_d, counts_q);
-  const unsigned pgrid = static_cast<unsigned>((n + m + 255) / 256);
-  count_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, counts_d, counts_q);
-  scan_kernel<<<dim3(max_tiles, 2), kScanBlock, 0, s>>>(grid, counts_d, counts_q, starts_d,
-                                                        starts_q, sums, max_tiles, 0);
-  scatter_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, m, starts_d, starts_q, sums,
+  // Without the query sort, the queries join none of the three passes and
+  // their records are written in the caller's order.
+  const int64_t mq = sort_queries ? m : 0;
+  const unsigned pgrid = static_cast<unsigned>((n + mq + 255) / 256);
+  count_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, mq, counts_d, counts_q);
+  scan_kernel<<<dim3(max_tiles, sort_queries ? 2 : 1), kScanBlock, 0, s>>>(
+      grid, counts_d, counts_q, starts_d, starts_q, sums, max_tiles, 0);
+  scatter_kernel<<<pgrid, 256, 0, s>>>(grid, data, n, queries, mq, starts_d, starts_q, sums,
                                        max_tiles, counts_d, counts_q, sorted, qrec);
+  if (!sort_queries && m > 0)
+    query_identity_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(queries, m, qrec);
   return cudaGetLastError();
 }
 
@@ -1445,8 +1461,9 @@ cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries,
 
 cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
                          double radius, float* out, int32_t* count_out, void* workspace,
-                         const LocalLayout& L, int sm_count, cudaStream_t s) {
-  cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s);
+                         const LocalLayout& L, int sm_count, cudaStream_t s, bool sort_queries) {
+  cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s,
+                                   sort_queries);
   if (e != cudaSuccess) return e;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   const GridDev* grid = reinterpret_cast<const GridDev*>(ws + L.off_grid);
@@ -1524,13 +1541,14 @@ size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k) {
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
-                                const LocalLayout& L, int sm_count, cudaStream_t s) {
+                                const LocalLayout& L, int sm_count, cudaStream_t s,
+                                bool sort_queries) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   float* zbuf = reinterpret_cast<float*>(ws + L.bytes);
   int32_t* hit = reinterpret_cast<int32_t*>(ws + L.bytes + round_up(size_t(m) * 4, 256));
   int32_t* nbr = reinterpret_cast<int32_t*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256));
   cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
-                             s, hit);
+                             s, hit, sort_queries);
   if (e != cudaSuccess) return e;
   const bool data_side = grad_z || grad_xy;
   float4* acc = data_side ? reinterpret_cast<float4*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256) +
@@ -1570,7 +1588,8 @@ size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
 
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
-                       const LocalLayout& L, int sm_count, cudaStream_t s, int32_t* hit_out) {
+                       const LocalLayout& L, int sm_count, cudaStream_t s, int32_t* hit_out,
+                       bool sort_queries) {
   const size_t smem = knn_smem_bytes(k);
   cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1578,7 +1597,7 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
     e = cudaFuncSetAttribute(knn_query_kernel<kPowGeneral>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  e = launch_grid_sort(data, n, queries, m, 0.0, k, workspace, L, sm_count, s);
+  e = launch_grid_sort(data, n, queries, m, 0.0, k, workspace, L, sm_count, s, sort_queries);
   if (e != cudaSuccess) return e;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   const GridDev* grid = reinterpret_cast<const GridDev*>(ws + L.off_grid);
@@ -1623,7 +1642,7 @@ __global__ void index_prep_kernel(const GridDev* __restrict__ src, GridDev* __re
 // sort of the queries alone (the scan runs its query half only).
 cudaError_t launch_query_sort(const GridDev* xgrid, const float* queries, int64_t m, double radius,
                               int64_t max_cells, void* workspace, const QueryLayout& Q,
-                              int sm_count, cudaStream_t s) {
+                              int sm_count, cudaStream_t s, bool sort_queries) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   GridDev* grid = reinterpret_cast<GridDev*>(ws + Q.off_grid);
   int32_t* counts = reinterpret_cast<int32_t*>(ws + Q.off_counts);
@@ -1632,6 +1651,10 @@ cudaError_t launch_query_sort(const GridDev* xgrid, const float* queries, int64_
   float4* qrec = reinterpret_cast<float4*>(ws + Q.off_qrec);
   const int max_tiles = scan_tiles_of(max_cells);
   index_prep_kernel<<<1, 1, 0, s>>>(xgrid, grid, radius);
+  if (!sort_queries) {
+    query_identity_kernel<<<static_cast<unsigned>((m + 255) / 256), 256, 0, s>>>(queries, m, qrec);
+    return cudaGetLastError();
+  }
   const unsigned zgrid = static_cast<unsigned>(
       std::min<int64_t>(int64_t(sm_count) * 8, (max_cells + 4 + 255) / 256));
   zero_counts_kernel<<<zgrid, 256, 0, s>>>(grid, counts, counts);
@@ -1719,10 +1742,11 @@ cudaError_t launch_index_build(const float* data, int64_t n, double radius, int 
 cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
                                int64_t m, double p, double radius, float* out, int32_t* count_out,
                                void* workspace, const QueryLayout& Q, int sm_count,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool sort_queries) {
   const unsigned char* mem = static_cast<const unsigned char*>(index_mem);
   const GridDev* xgrid = reinterpret_cast<const GridDev*>(mem + X.off_grid);
-  cudaError_t e = launch_query_sort(xgrid, queries, m, radius, X.max_cells, workspace, Q, sm_count, s);
+  cudaError_t e = launch_query_sort(xgrid, queries, m, radius, X.max_cells, workspace, Q, sm_count,
+                                    s, sort_queries);
   if (e != cudaSuccess) return e;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   const GridDev* grid = reinterpret_cast<const GridDev*>(ws + Q.off_grid);
@@ -1745,7 +1769,7 @@ cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, cons
 cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const float* queries,
                              int64_t m, double p, int k, float* out, int32_t* nbr_out,
                              float* kd2_out, void* workspace, const QueryLayout& Q, int sm_count,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool sort_queries) {
   const size_t smem = knn_smem_bytes(k);
   cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1755,7 +1779,8 @@ cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const 
   if (e != cudaSuccess) return e;
   const unsigned char* mem = static_cast<const unsigned char*>(index_mem);
   const GridDev* xgrid = reinterpret_cast<const GridDev*>(mem + X.off_grid);
-  e = launch_query_sort(xgrid, queries, m, 0.0, X.max_cells, workspace, Q, sm_count, s);
+  e = launch_query_sort(xgrid, queries, m, 0.0, X.max_cells, workspace, Q, sm_count, s,
+                        sort_queries);
   if (e != cudaSuccess) return e;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   const GridDev* grid = reinterpret_cast<const GridDev*>(ws + Q.off_grid);

@@ -24,9 +24,11 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells);
 
 // Enqueues the whole local form on `s`: bounding box, grid plan, counting
 // sort of data and queries, gather.  No host synchronisation.
+// sort_queries = false keeps the caller's query order (no query sort).
 cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
                          double radius, float* out, int32_t* count_out, void* workspace,
-                         const LocalLayout& L, int sm_count, cudaStream_t s);
+                         const LocalLayout& L, int sm_count, cudaStream_t s,
+                         bool sort_queries = true);
 
 // Gradients of L = sum_j grad_out[j] Z(q_j) for the radius form (membership
 // sets held fixed): the grid build, then one kernel per query and one per
@@ -50,7 +52,7 @@ constexpr int kKnnMax = 64;
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s,
-                       int32_t* hit_out = nullptr);
+                       int32_t* hit_out = nullptr, bool sort_queries = true);
 
 // Gradients of the k-NN form (each selection held fixed): the search with
 // neighbour lists and hits kept in the workspace after L.bytes (plus
@@ -60,7 +62,8 @@ size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k);
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
-                                const LocalLayout& L, int sm_count, cudaStream_t s);
+                                const LocalLayout& L, int sm_count, cudaStream_t s,
+                                bool sort_queries = true);
 
 // A prepared index: the data side of a local form built once and queried
 // by many calls.  The index's own buffer holds the plan, the data cell
@@ -94,12 +97,12 @@ cudaError_t launch_index_build(const float* data, int64_t n, double radius, int 
 cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
                                int64_t m, double p, double radius, float* out, int32_t* count_out,
                                void* workspace, const QueryLayout& Q, int sm_count,
-                               cudaStream_t s);
+                               cudaStream_t s, bool sort_queries = true);
 
 // One query call on a k-NN index (1 <= k <= kKnnMax).
 cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const float* queries,
                              int64_t m, double p, int k, float* out, int32_t* nbr_out,
                              float* kd2_out, void* workspace, const QueryLayout& Q, int sm_count,
-                             cudaStream_t s);
+                             cudaStream_t s, bool sort_queries = true);
 
 }  // namespace idw
