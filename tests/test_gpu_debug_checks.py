@@ -49,6 +49,13 @@ for name, data, q in cases:
     Z, cnt = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True)
     Zo, _, co = oracle.idw_local(data, q, 2.0, 0.03)
     assert np.array_equal(cnt.cpu().numpy(), co), name
+    ho = idw.Handle(torch.cuda.current_device())  # the caller's query order
+    idw.set_option("local_query_order", 1, handle=ho)
+    _, cnt_o = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True, handle=ho)
+    assert np.array_equal(cnt_o.cpu().numpy(), co), name
+    _, nbr_o = idw.interpolate_knn(d, qq, 2.0, 9, neighbours=True, handle=ho)
+    assert np.array_equal(nbr_o.cpu().numpy(), oracle.idw_knn(data, q, 2.0, 9)["nbr"]), name
+    ho.close()
     gl = torch.linspace(-1.0, 1.0, q.shape[0], device="cuda")
     gzl = idw.local_backward(d, qq, 2.0, 0.03, gl)[0].cpu().numpy()
     Gl = oracle.idw_local_grad(data, q, 2.0, 0.03, gl.cpu().numpy())["grad_z"]
