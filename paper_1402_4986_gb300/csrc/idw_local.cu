@@ -991,7 +991,8 @@ __global__ void __maxnreg__(64)
                      const float4* __restrict__ qrec, const float* __restrict__ data, int64_t n,
                      int64_t m,
                      double p, int k, float* __restrict__ out, int32_t* __restrict__ nbr_out,
-                     float* __restrict__ kd2_out, int32_t* __restrict__ hit_out) {
+                     float* __restrict__ kd2_out, int32_t* __restrict__ hit_out,
+                     bool sort_rows) {
   extern __shared__ __align__(16) unsigned char knn_smem[];
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= m) return;  // no block-wide barrier in this kernel
@@ -1214,9 +1215,13 @@ __global__ void __maxnreg__(64)
   out[j] = zv;
   if (hit_out) hit_out[j] = best_hit != INT_MAX ? best_hit : -1;
   if (nbr_out) {
-    // Heap sort: the largest remaining key goes to the end of the row.
     int32_t* row = nbr_out + int64_t(j) * k;
     for (int s = size; s < k; ++s) row[s] = -1;
+    if (!sort_rows) {  // the selection in heap order (the gradient needs no order)
+      for (int s = 0; s < size; ++s) row[s] = key_index(hp.h[s * kKnnThreads]);
+      return;
+    }
+    // Heap sort: the largest remaining key goes to the end of the row.
     for (int n = size; n > 0; --n) {
       const u64 top = hp.top();
       row[n - 1] = key_index(top);
@@ -1232,9 +1237,10 @@ __global__ void __maxnreg__(64)
 // piecewise constant in every input): the derivatives of Eq. 1 summed over
 // the selected points, as for the radius form.  The search runs first, with
 // neighbour lists and hits kept in the workspace; then one thread per query
-// (cell order, so neighbouring threads share points) walks its list, which
-// is in key order: its first entry's FP32 d^2 is d2_min, so the scaled
-// weights (d2_min / d^2)^(p/2) need no rescaling.  A selection is not
+// (cell order, so neighbouring threads share points) walks its list, left
+// in heap order (the search skips the heap sort): one pass finds d2_min and
+// the sums of the scaled weights (d2_min / d^2)^(p/2), rescaling them when a
+// smaller d^2 appears, a second the gradients.  A selection is not
 // bounded by a fixed radius, so the data-side terms (dL/dz, dL/dx, dL/dy)
 // are added to a per-point float4 with one 16-byte vector atomic per pair
 // (a third of the L2 operations of three scalar ones; their order, and so
@@ -1310,18 +1316,29 @@ __global__ void __launch_bounds__(kLocalThreads)
         if (acc && dcheck(h < n, kSiteData)) atomicAdd(&acc[h], make_float4(gj, 0.f, 0.f, 0.f));
       } else if (cnt > 0) {
         const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
-        const float* x0 = data + 3 * int64_t(row[0]);
-        const float d2min = fp32_d2(qx, qy, x0[0], x0[1]);  // the smallest key
+        // One pass: d2_min and the sums with weights scaled by the smallest
+        // d^2 so far, rescaled when a smaller one appears (the row is in
+        // heap order).
+        float d2min = INFINITY, lmin = 0.f, s0 = 0.f, s1 = 0.f;
+        for (int s = 0; s < cnt; ++s) {
+          const float* x = data + 3 * int64_t(row[s]);
+          const float d2 = fp32_d2(qx, qy, x[0], x[1]);
+          if (d2 < d2min) {
+            const float l = MODE == kPow2 ? 0.f : lg2_approx(d2);
+            if (s > 0) {
+              const float f = grad_weight<MODE>(d2min, d2, l, hp);  // (d2 / d2min_old)^(p/2)
+              s0 *= f;
+              s1 *= f;
+            }
+            d2min = d2;
+            lmin = l;
+          }
+          const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
+          s0 += w;
+          s1 = fmaf(w, x[2], s1);
+        }
         bool f32 = d2min >= 0x1p-100f;
         if (f32) {
-          const float lmin = MODE == kPow2 ? 0.f : lg2_approx(d2min);
-          float s0 = 0.f, s1 = 0.f;
-          for (int s = 0; s < cnt; ++s) {
-            const float* x = data + 3 * int64_t(row[s]);
-            const float w = grad_weight<MODE>(fp32_d2(qx, qy, x[0], x[1]), d2min, lmin, hp);
-            s0 += w;
-            s1 = fmaf(w, x[2], s1);
-          }
           const float Z = s1 / s0, c = gj / s0;
           const float lmin2 = lg2_approx(d2min);
           f32 = isfinite(Z) && isfinite(c);
@@ -1548,7 +1565,7 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
   int32_t* hit = reinterpret_cast<int32_t*>(ws + L.bytes + round_up(size_t(m) * 4, 256));
   int32_t* nbr = reinterpret_cast<int32_t*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256));
   cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
-                             s, hit, sort_queries);
+                             s, hit, sort_queries, false);
   if (e != cudaSuccess) return e;
   const bool data_side = grad_z || grad_xy;
   float4* acc = data_side ? reinterpret_cast<float4*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256) +
@@ -1589,7 +1606,7 @@ size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s, int32_t* hit_out,
-                       bool sort_queries) {
+                       bool sort_queries, bool sort_rows) {
   const size_t smem = knn_smem_bytes(k);
   cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -1614,11 +1631,11 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
         grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
-        hit_out);
+        hit_out, sort_rows);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
         grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
-        hit_out);
+        hit_out, sort_rows);
   return cudaGetLastError();
 }
 
@@ -1795,11 +1812,11 @@ cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const 
   if (p == 2.0)
     knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
         grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out,
-        nullptr);
+        nullptr, true);
   else
     knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
         grid, sorted, starts, sums, bpre, sat, qrec, data, X.n, m, p, k, out, nbr_out, kd2_out,
-        nullptr);
+        nullptr, true);
   return cudaGetLastError();
 }
 

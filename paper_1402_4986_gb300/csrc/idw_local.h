@@ -47,12 +47,14 @@ cudaError_t debug_check_failures(unsigned* sites, bool* enabled);
 
 // The k-nearest-neighbour form (1 <= k <= kKnnMax): same grid build, then
 // a square search per query.  nbr_out (m x k), kd2_out (m) and hit_out (m:
-// the lowest coincident data index, or -1) may be null.
+// the lowest coincident data index, or -1) may be null.  sort_rows = false
+// leaves each row of nbr_out in heap order (the selection, unordered).
 constexpr int kKnnMax = 64;
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s,
-                       int32_t* hit_out = nullptr, bool sort_queries = true);
+                       int32_t* hit_out = nullptr, bool sort_queries = true,
+                       bool sort_rows = true);
 
 // Gradients of the k-NN form (each selection held fixed): the search with
 // neighbour lists and hits kept in the workspace after L.bytes (plus
