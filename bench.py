@@ -23,6 +23,13 @@ Besides ``value`` (device-resident pairs/s) the line carries:
   cpu_baseline  the FP64 oracle on the host cores (bounded query sample);
   clocks        nvidia-smi samples taken during the timed region.
 ``--impl reference`` times the oracle alone (the CPU reference arm).
+
+``--config NAME`` prints one line per other workload instead (``all`` runs
+the headline and every one of them): scale, clustered, adjoint, batched,
+layout, paper, and the local forms.  The ``local`` and ``knn`` lines carry
+rows for one-shot calls, gradients (``backward``), prepared-index calls,
+and a raster of queries in sorted and caller order, plus a ``cpu_baseline``
+of the oracle; ``--members`` and ``--data`` pick their cases.
 """
 from __future__ import annotations
 
