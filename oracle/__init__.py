@@ -71,6 +71,10 @@ def bind(lib):
     lib.oracle_idw_knn_grad.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_int, d, d, d, d,
                                         d, d, ctypes.c_int]
     lib.oracle_idw_knn_grad.restype = ctypes.c_int
+    lib.oracle_idw_modified.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_double, d,
+                                        ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
+    lib.oracle_idw_modified.restype = ctypes.c_int
     return lib
 
 
@@ -241,3 +245,23 @@ def idw_knn_grad(data_xyz, queries_xy, p: float, k: int, g, threads: int = 0):
     if rc < 0:
         raise ValueError("oracle_idw_knn_grad rejected its arguments")
     return {"Z": Z, "grad_z": gz, "grad_xy": gxy, "grad_q": gq, "grad_p": float(gp[0])}
+
+
+def idw_modified(data_xyz, queries_xy, p: float, radius: float, threads: int = 0):
+    """Modified Shepard (FP64): Eq. 1 over the radius form's members with
+    weights ((R - d)/(R d))^p.  Returns (Z, hit, count) as ``idw_local``.
+    """
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    m = q.shape[0]
+    Z = np.empty(m, np.float64)
+    hit = np.empty(m, np.int64)
+    count = np.empty(m, np.int32)
+    rc = lib.oracle_idw_modified(_ptr(data), data.shape[0], _ptr(q), m, float(p), float(radius),
+                                 _ptr(Z), hit.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 count.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                 int(threads))
+    if rc < 0:
+        raise ValueError("oracle_idw_modified rejected its arguments")
+    return Z, hit, count

@@ -1,7 +1,7 @@
 /*
  * FP64 CPU oracle for global (standard) Shepard inverse-distance weighting,
- * its gradients, and the radius-limited and k-nearest-neighbour local forms
- * with their gradients.
+ * its gradients, the radius-limited and k-nearest-neighbour local forms
+ * with their gradients, and modified Shepard weights on the radius form.
  *
  * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite, the
  * smoke check and the benchmark's CPU-baseline leg may load this library.
@@ -528,6 +528,101 @@ int oracle_idw_local_grad(const double *data, int64_t n, const double *q, int64_
     free(d2min);
     free(gp);
     return t;
+}
+
+/* ------------------------------------------- modified Shepard variant */
+
+typedef struct {
+    const double *data;
+    int64_t n;
+    const double *q;
+    double p;
+    double radius;
+    float r2f; /* fl32(R^2) */
+    double *Z;
+    int64_t *hit;
+    int32_t *count;
+} modified_ctx;
+
+/* The modified Shepard weight's base t = (R - d) / (R d) = 1/d - 1/R of a
+ * member, taken as 0 where exact arithmetic puts the point at or beyond R
+ * (the FP32 membership test can admit such points). */
+static double modified_base(double radius, double d)
+{
+    const double t = isinf(radius) ? 1.0 / d : (radius - d) / (radius * d);
+    return t > 0.0 ? t : 0.0;
+}
+
+static void modified_range(void *vctx, int64_t b, int64_t e)
+{
+    modified_ctx *c = (modified_ctx *)vctx;
+    for (int64_t j = b; j < e; j++) {
+        const double qx = c->q[2 * j], qy = c->q[2 * j + 1];
+        const float qxf = (float)qx, qyf = (float)qy;
+        int64_t k = -1;
+        int32_t members = 0;
+        double tmax = 0.0;
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            if (!isfinite(x) || !isfinite(y))
+                continue;
+            if (x == qx && y == qy) {
+                k = i;
+                break;
+            }
+            if (local_member(qxf, qyf, (float)x, (float)y, c->r2f)) {
+                const double t = modified_base(c->radius, sqrt(sqdist(qx, qy, x, y)));
+                if (t > tmax)
+                    tmax = t;
+                members++;
+            }
+        }
+        c->hit[j] = k;
+        if (k >= 0) {
+            c->Z[j] = c->data[3 * k + 2];
+            c->count[j] = -1;
+            continue;
+        }
+        c->count[j] = members;
+        if (members == 0 || tmax == 0.0) { /* no member with a positive weight */
+            c->Z[j] = NAN;
+            continue;
+        }
+        /* Weights relative to the largest, (t_i / t_max)^p in (0, 1]. */
+        nsum m0 = {0.0, 0.0}, m1 = {0.0, 0.0};
+        for (int64_t i = 0; i < c->n; i++) {
+            const double x = c->data[3 * i], y = c->data[3 * i + 1];
+            const int inside = local_member(qxf, qyf, (float)x, (float)y, c->r2f);
+            if (!inside)
+                continue;
+            const double t = modified_base(c->radius, sqrt(sqdist(qx, qy, x, y)));
+            const double w = pow(t / tmax, c->p);
+            nsum_add(&m0, w);
+            nsum_add(&m1, w * c->data[3 * i + 2]);
+        }
+        c->Z[j] = nsum_value(&m1) / nsum_value(&m0);
+    }
+}
+
+/*
+ * Modified Shepard interpolation (Franke & Nielson's local weights, a local
+ * variant in the family of the paper's related work, Sec. 1): Eq. 1 over
+ * the members of the radius form (the same FP32 test), with the weights
+ *     w_i = ((R - d_i) / (R d_i))^p = (1/d_i - 1/R)^p,
+ * which fall to 0 continuously at d = R.  R = +inf gives d^-p, the global
+ * form.  Exact hit: z of the lowest coincident index (count -1); no member
+ * with a positive weight: NaN.  Outputs and return as oracle_idw_local.
+ */
+int oracle_idw_modified(const double *data, int64_t n, const double *q, int64_t m, double p,
+                        double radius, double *Z, int64_t *hit, int32_t *count, int nthreads)
+{
+    if (!data || !q || !Z || !hit || !count || n < 1 || m < 0 || !(p > 0.0) || !isfinite(p) ||
+        !(radius > 0.0))
+        return -1;
+    modified_ctx c = {data, n, q, p, radius, (float)(radius * radius), Z, hit, count};
+    if (m == 0)
+        return 0;
+    return parallel_for(m, nthreads, modified_range, &c);
 }
 
 /* ------------------------------------------------------- k-NN variant */

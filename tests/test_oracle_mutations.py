@@ -72,6 +72,13 @@ MUTATIONS = [
      "nsum_add(&ptot, -gj * nsum_value(&qsp) / S0);"),
     ("knn data-gradient uses dy for x", "nsum_add(&acc[3 * sel[s] + 1], f * ex);",
      "nsum_add(&acc[3 * sel[s] + 1], f * ey);"),
+    ("modified weight without the radius term",
+     "const double t = isinf(radius) ? 1.0 / d : (radius - d) / (radius * d);",
+     "const double t = 1.0 / d;"),
+    ("modified weight with R + d", "const double t = isinf(radius) ? 1.0 / d : (radius - d) / (radius * d);",
+     "const double t = isinf(radius) ? 1.0 / d : (radius + d) / (radius * d);"),
+    ("modified power halved", "const double w = pow(t / tmax, c->p);",
+     "const double w = pow(t / tmax, 0.5 * c->p);"),
 ]
 
 PINS = [
@@ -108,6 +115,10 @@ PINS = [
     pins.test_knn_gradient_with_k_at_least_n_is_the_global_gradient,
     pins.test_knn_gradient_sums_and_translation,
     pins.test_knn_gradient_at_hits_and_empty_selections,
+    pins.test_modified_closed_form_two_points,
+    pins.test_modified_with_infinite_radius_is_the_global_form,
+    pins.test_modified_is_continuous_at_the_radius,
+    pins.test_modified_members_and_hits_are_the_radius_form_s,
 ]
 
 

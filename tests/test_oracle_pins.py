@@ -725,3 +725,57 @@ def test_knn_gradient_at_hits_and_empty_selections():
     G = oracle.idw_grad(data, q[2:], 2.0, g[2:])
     assert np.allclose(K["grad_z"] - np.array([0.0, 3.0, 0.0, 0.0]), G["grad_z"], rtol=0, atol=1e-14)
     assert np.all(K["grad_q"][:2] == 0) and np.isnan(K["Z"][1]) and K["Z"][0] == -1.0
+
+
+# ------------------------------------------------- modified Shepard
+
+def test_modified_closed_form_two_points():
+    """Points at d = 1/2 and 1/4 from the query with R = 1: the bases
+    1/d - 1/R are 1 and 3, so Z = (z1 + 3^p z2) / (1 + 3^p) exactly; a point
+    beyond R takes no part."""
+    data = np.array([[0.5, 0.0, 1.0], [0.0, 0.25, 3.0], [0.0, -1.5, 100.0]], np.float64)
+    q = np.array([[0.0, 0.0]], np.float64)
+    for p in (1, 2, 3):
+        Z, hit, cnt = oracle.idw_modified(data, q, float(p), 1.0)
+        want = Fraction(1) * 1 + Fraction(3) ** p * 3
+        want = want / (1 + Fraction(3) ** p)
+        # FP64 with weights scaled by the largest: within a few ulps.
+        assert abs(Z[0] - float(want)) <= 4 * np.spacing(float(want))
+        assert cnt[0] == 2 and hit[0] == -1
+
+
+def test_modified_with_infinite_radius_is_the_global_form():
+    prob = synthetic.uniform_problem(400, 150, seed=61, exact_hits=3)
+    for p in (2.0, 3.5):
+        Zg, _ = oracle.idw(prob["data"], prob["queries"], p)
+        for R in (float("inf"), 1e30):
+            Zm, _, _ = oracle.idw_modified(prob["data"], prob["queries"], p, R)
+            assert np.max(np.abs(Zm - Zg)) <= 1e-12 * np.max(np.abs(prob["data"][:, 2]))
+
+
+def test_modified_is_continuous_at_the_radius():
+    """A point just inside R carries a weight of order (1e-7)^p, so moving it
+    out of the neighbourhood changes Z by almost nothing; the standard local
+    form jumps."""
+    rng = np.random.default_rng(62)
+    data = np.concatenate([rng.random((30, 2)) * 0.2 - 0.1, rng.standard_normal((30, 1))], 1)
+    data = data.astype(np.float32).astype(np.float64)
+    q = np.array([[0.0, 0.0]], np.float64)
+    R = 0.25
+    inside = np.array([[np.float32(R * (1 - 1e-6)), 0.0, 50.0]])
+    outside = np.array([[np.float32(R * (1 + 1e-6)), 0.0, 50.0]])
+    Zin, _, cin = oracle.idw_modified(np.concatenate([data, inside]), q, 2.0, R)
+    Zout, _, cout = oracle.idw_modified(np.concatenate([data, outside]), q, 2.0, R)
+    assert cin[0] == cout[0] + 1
+    assert abs(Zin[0] - Zout[0]) <= 1e-9
+    Lin, _, _ = oracle.idw_local(np.concatenate([data, inside]), q, 2.0, R)
+    Lout, _, _ = oracle.idw_local(np.concatenate([data, outside]), q, 2.0, R)
+    assert abs(Lin[0] - Lout[0]) > 1e-3
+
+
+def test_modified_members_and_hits_are_the_radius_form_s():
+    prob = synthetic.uniform_problem(2000, 500, seed=63, exact_hits=6)
+    R = 0.06
+    _, hm, cm = oracle.idw_modified(prob["data"], prob["queries"], 2.0, R)
+    _, hl, cl = oracle.idw_local(prob["data"], prob["queries"], 2.0, R)
+    assert np.array_equal(hm, hl) and np.array_equal(cm, cl)
