@@ -750,6 +750,15 @@ def run_local(args):
                          "empty_queries": int((c == 0).sum()),
                          "counts_match_oracle": bool(np.array_equal(c[idx], c64)),
                          "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+        mms = _events_ms(lambda: idw.interpolate_modified(d, q, 2.0, R, out=out), 10, warm=3)
+        Zm64, _, _ = oracle.idw_modified(prob["data"], prob["queries"][idx], 2.0, R)
+        okm = ~np.isnan(Zm64)
+        merr = float(np.max(np.abs(out.cpu().numpy()[idx][okm] - Zm64[okm]), initial=0.0) /
+                     np.max(np.abs(prob["data"][:, 2])))
+        rows.append({"data": "clustered" if clustered else "uniform", "call": "modified Shepard",
+                     "n": n, "m": m, "radius": R, "p": 2.0, "ms": mms,
+                     "queries_s": m / (mms / 1e3), "error_vs_fp64_oracle": merr,
+                     "error_sample_queries": len(idx)})
         gout = torch.from_numpy(np.random.default_rng(7).standard_normal(m).astype(np.float32)).cuda()
         bms = _events_ms(lambda: idw.local_backward(d, q, 2.0, R, gout), 10, warm=3)
         _, _, gq, _ = idw.local_backward(d, q, 2.0, R, gout)

@@ -426,6 +426,24 @@ idw_status idw_interpolate_local(idw_handle_t handle, const float *data_xyz, int
                                  float *out, int32_t *count_out, void *stream);
 
 /*
+ * Modified Shepard interpolation: the radius form's members (the same FP32
+ * test as idw_interpolate_local) with Franke and Nielson's local weights
+ *
+ *     w_i = ((R - d_i) / (R d_i))^p = (1/d_i - 1/R)^p,
+ *
+ * which fall to 0 continuously as d_i reaches R, so Z has no jump when a
+ * point crosses the radius (the plain radius form's weights d^-p do).  p = 2
+ * is the classic choice.  R = +inf gives d^-p, the global form.  The base
+ * 1/d - 1/R is taken from the FP32 reciprocal square root and clamped at 0;
+ * hits, NaN and the FP64 pass are as in idw_interpolate_local (an FP64
+ * query with no member of positive weight gets NaN).  Arguments, counts,
+ * workspace, errors and the method are those of idw_interpolate_local.
+ */
+idw_status idw_interpolate_modified(idw_handle_t handle, const float *data_xyz, int64_t n,
+                                    const float *queries_xy, int64_t m, double p, double radius,
+                                    float *out, int32_t *count_out, void *stream);
+
+/*
  * k-nearest-neighbour Shepard interpolation, the other local form of the
  * related work the paper cites (Sec. 1): Z(q) is Eq. 1 over the k finite
  * data points nearest to q.  Nearness is the key (d2, index) with

@@ -21,7 +21,8 @@ from ._lib import IDWError, PREC_F32_COMP, PREC_F64_PLAIN, PlanInfo
 
 __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
-    "interpolate_batched", "interpolate_local", "interpolate_knn", "LocalIndex",
+    "interpolate_batched", "interpolate_local", "interpolate_modified", "interpolate_knn",
+    "LocalIndex",
     "local_backward", "LocalIDWFunction", "idw_local", "knn_backward", "KnnIDWFunction",
     "idw_knn",
     "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
@@ -219,7 +220,8 @@ def interpolate_local(data, queries, p: float = 2.0, radius: float = float("inf"
 
     Returns ``out`` (float32[m], NaN where no data point is within R), or
     ``(out, count)`` with ``count`` int32[m] (members per query, -1 at an
-    exact hit) when ``counts`` is true.  Synchronises the stream once.
+    exact hit) when ``counts`` is true.  Asynchronous on the current stream
+    (graph-capturable).
     """
     _check_inputs(data, queries, PREC_F32_COMP)
     m = queries.shape[0]
@@ -231,6 +233,24 @@ def interpolate_local(data, queries, p: float = 2.0, radius: float = float("inf"
                                      float(radius), _ptr(out), _ptr(cnt),
                                      _stream(data))
     _lib.check(st, "idw_interpolate_local", h.ptr)
+    return (out, cnt) if counts else out
+
+
+def interpolate_modified(data, queries, p: float = 2.0, radius: float = float("inf"), out=None,
+                         counts: bool = False, handle: Handle | None = None):
+    """Modified Shepard (``idw_interpolate_modified``): the radius form's
+    members with weights ((R - d)/(R d))^p, which vanish at d = R.  Returns
+    as ``interpolate_local``."""
+    _check_inputs(data, queries, PREC_F32_COMP)
+    m = queries.shape[0]
+    h = handle or get_handle(data.device)
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=data.device)
+    cnt = torch.empty(m, dtype=torch.int32, device=data.device) if counts else None
+    st = h.lib.idw_interpolate_modified(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m,
+                                        float(p), float(radius), _ptr(out), _ptr(cnt),
+                                        _stream(data))
+    _lib.check(st, "idw_interpolate_modified", h.ptr)
     return (out, cnt) if counts else out
 
 

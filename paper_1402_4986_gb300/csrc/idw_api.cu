@@ -656,6 +656,29 @@ idw_status idw_interpolate_local(idw_handle_t h, const float* data, int64_t n,
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
+idw_status idw_interpolate_modified(idw_handle_t h, const float* data, int64_t n,
+                                    const float* queries, int64_t m, double p, double radius,
+                                    float* out, int32_t* count_out, void* stream) {
+  NvtxRange nvtx("idw_interpolate_modified");
+  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, out);
+  if (st != IDW_OK) return st;
+  if (!(radius > 0.0)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (count_out && !aligned(count_out, 4)) return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}},
+                       static_cast<cudaStream_t>(stream));
+  if (st != IDW_OK) return st;
+  const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_local(data, n, queries, m, p, radius, out, count_out, h->ws, L,
+                                          h->sm_count, static_cast<cudaStream_t>(stream),
+                                          h->opt_query_order == 0, true);
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
 idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, const float* queries,
                                int64_t m, double p, int32_t k, float* out, int32_t* nbr_out,
                                float* kd2_out, void* stream) {

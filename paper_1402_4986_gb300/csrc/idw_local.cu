@@ -543,13 +543,31 @@ struct Runs {
 // hit, or with sums outside FP32's range, falls through to the FP64 pass,
 // which takes the z of the lowest coincident index or recomputes the sums
 // with weights scaled by d2_min^(p/2).
+// Weights of the radius form: d^-p (kWeightShepard) or the modified
+// Shepard weights ((R - d)/(R d))^p = (1/d - 1/R)^p (kWeightModified), which
+// fall to 0 at d = R.  The modified base comes from the MUFU reciprocal
+// square root (relative error ~2^-22) and is clamped at 0 for members that
+// rounding puts at the boundary; a coincident point gives an infinite base.
+constexpr int kWeightShepard = 0, kWeightModified = 1;
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 template <int MODE>
+__device__ __forceinline__ float modified_weight(float d2, float inv_r, float pw) {
+  const float t = fmaxf(rsqrt_approx(d2) - inv_r, 0.f);
+  if (MODE == kPow2) return t * t;
+  return ex2_approx(pw * lg2_approx(t));
+}
+
+template <int MODE, int WMODE = kWeightShepard>
 __global__ void __launch_bounds__(kLocalThreads)
     local_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                        int64_t n, const int32_t* __restrict__ starts,
                        const int32_t* __restrict__ base, const float4* __restrict__ qrec,
                        int64_t m, double p, float r2f, float r2t, float* __restrict__ out,
-                       int32_t* __restrict__ count_out) {
+                       int32_t* __restrict__ count_out, double radius = 0.0) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= m) return;
   const float4 r = qrec[t];
@@ -558,6 +576,8 @@ __global__ void __launch_bounds__(kLocalThreads)
   if (!dcheck(j >= 0 && j < m, kSiteOutput)) return;
   const Runs runs(*grid, qx, qy, starts, base);
   const float hp = static_cast<float>(0.5 * p), nhp = -hp;
+  const float pw = static_cast<float>(p);
+  const float inv_r = WMODE == kWeightModified ? static_cast<float>(1.0 / radius) : 0.f;
 
   // (sum w, sum w z) and their TwoSum errors.  The products w z are rounded
   // once (2^-24), below the error of the MUFU weights themselves (2^-23).
@@ -571,7 +591,8 @@ __global__ void __launch_bounds__(kLocalThreads)
       const float4 v = sorted[k];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       if (d2 < r2t) {
-        const float w = local_weight<MODE>(d2, hp, nhp);
+        const float w = WMODE == kWeightModified ? modified_weight<MODE>(d2, inv_r, pw)
+                                                 : local_weight<MODE>(d2, hp, nhp);
         two_sum_acc(hi, lo, pk(w, __fmul_rn(w, v.z)));
         ++cnt;
       }
@@ -594,10 +615,16 @@ __global__ void __launch_bounds__(kLocalThreads)
     if (count_out) count_out[j] = cnt;
     return;
   }
-  // FP64 pass: exact hits first, then the members' d2_min.
+  // FP64 pass: exact hits first, then the members' d2_min (or, for the
+  // modified weights, their largest base (R - d)/(R d), clamped at 0).
   int best = INT_MAX, members = 0;
   float bestz = 0.f;
-  double dmin = INFINITY;
+  double dmin = INFINITY, tmax = 0.0;
+  auto base64 = [&](double e2) {
+    const double d = sqrt(e2);
+    const double t = isinf(radius) ? 1.0 / d : (radius - d) / (radius * d);
+    return t > 0.0 ? t : 0.0;
+  };
 #pragma unroll
   for (int r = 0; r < 5; ++r)
     for (int k = runs.a[r]; k < runs.b[r]; ++k) {
@@ -611,12 +638,13 @@ __global__ void __launch_bounds__(kLocalThreads)
       } else if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
         const double ex = double(qx) - v.x, ey = double(qy) - v.y;
         dmin = fmin(dmin, ex * ex + ey * ey);
+        if (WMODE == kWeightModified) tmax = fmax(tmax, base64(ex * ex + ey * ey));
         ++members;
       }
     }
-  if (best != INT_MAX || members == 0) {
+  if (best != INT_MAX || members == 0 || (WMODE == kWeightModified && !(tmax > 0.0))) {
     out[j] = best != INT_MAX ? bestz : __int_as_float(0x7fc00000);
-    if (count_out) count_out[j] = best != INT_MAX ? -1 : 0;
+    if (count_out) count_out[j] = best != INT_MAX ? -1 : members;
     return;
   }
   double s0 = 0.0, s1 = 0.0;
@@ -626,7 +654,8 @@ __global__ void __launch_bounds__(kLocalThreads)
       const float4 v = sorted[k];
       if (fp32_d2(qx, qy, v.x, v.y) < r2f) {
         const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-        const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+        const double w = WMODE == kWeightModified ? pow(base64(ex * ex + ey * ey) / tmax, p)
+                                                  : pow(dmin / (ex * ex + ey * ey), 0.5 * p);
         s0 += w;
         s1 += w * double(v.z);
       }
@@ -1478,7 +1507,8 @@ cudaError_t launch_grid_sort(const float* data, int64_t n, const float* queries,
 
 cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
                          double radius, float* out, int32_t* count_out, void* workspace,
-                         const LocalLayout& L, int sm_count, cudaStream_t s, bool sort_queries) {
+                         const LocalLayout& L, int sm_count, cudaStream_t s, bool sort_queries,
+                         bool modified) {
   cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s,
                                    sort_queries);
   if (e != cudaSuccess) return e;
@@ -1491,12 +1521,20 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
   const float r2f = static_cast<float>(radius * radius);
   const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
-  if (p == 2.0)
+  if (modified) {
+    if (p == 2.0)
+      local_query_kernel<kPow2, kWeightModified><<<qgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out, radius);
+    else
+      local_query_kernel<kPowGeneral, kWeightModified><<<qgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out, radius);
+  } else if (p == 2.0) {
     local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
-  else
+  } else {
     local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, out, count_out);
+  }
   return cudaGetLastError();
 }
 

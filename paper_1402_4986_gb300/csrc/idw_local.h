@@ -24,11 +24,12 @@ LocalLayout local_layout(int64_t n, int64_t m, int64_t max_cells);
 
 // Enqueues the whole local form on `s`: bounding box, grid plan, counting
 // sort of data and queries, gather.  No host synchronisation.
-// sort_queries = false keeps the caller's query order (no query sort).
+// sort_queries = false keeps the caller's query order (no query sort);
+// modified = true uses the modified Shepard weights (1/d - 1/R)^p.
 cudaError_t launch_local(const float* data, int64_t n, const float* queries, int64_t m, double p,
                          double radius, float* out, int32_t* count_out, void* workspace,
                          const LocalLayout& L, int sm_count, cudaStream_t s,
-                         bool sort_queries = true);
+                         bool sort_queries = true, bool modified = false);
 
 // Gradients of L = sum_j grad_out[j] Z(q_j) for the radius form (membership
 // sets held fixed): the grid build, then one kernel per query and one per

@@ -49,6 +49,8 @@ for name, data, q in cases:
     Z, cnt = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True)
     Zo, _, co = oracle.idw_local(data, q, 2.0, 0.03)
     assert np.array_equal(cnt.cpu().numpy(), co), name
+    _, cm = idw.interpolate_modified(d, qq, 2.0, 0.03, counts=True)
+    assert np.array_equal(cm.cpu().numpy(), co), name
     ho = idw.Handle(torch.cuda.current_device())  # the caller's query order
     idw.set_option("local_query_order", 1, handle=ho)
     _, cnt_o = idw.interpolate_local(d, qq, 2.0, 0.03, counts=True, handle=ho)

@@ -1,0 +1,104 @@
+"""GPU parity of modified Shepard interpolation against the FP64 oracle.
+
+``idw_interpolate_modified`` weights the radius form's members by
+((R - d)/(R d))^p (Franke and Nielson's local weights).  Member counts must
+equal the oracle's (the FP32 test is the radius form's), values within 2e-6
+of max |z|, NaN where no member has a positive weight, exact z at hits.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def idw():
+    from paper_1402_4986_gb300 import build
+    build.build()
+    import paper_1402_4986_gb300 as m
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return m
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _compare(idw, data, q, p, radius, tol=TOL):
+    Z, cnt = idw.interpolate_modified(_dev(data), _dev(q), p, radius, counts=True)
+    torch.cuda.synchronize()
+    Z, cnt = Z.cpu().numpy(), cnt.cpu().numpy()
+    Z64, hit64, cnt64 = oracle.idw_modified(data, q, p, radius)
+    assert np.array_equal(cnt, cnt64), np.nonzero(cnt != cnt64)[0][:10]
+    assert np.array_equal(np.isnan(Z), np.isnan(Z64))
+    h = hit64 >= 0
+    assert np.array_equal(Z[h], data[hit64[h], 2])
+    ok = ~np.isnan(Z64)
+    if ok.any():
+        err = np.max(np.abs(Z[ok].astype(np.float64) - Z64[ok])) / np.max(np.abs(data[:, 2]))
+        assert err <= tol, err
+    return Z, cnt
+
+
+@pytest.mark.parametrize("p", [1.0, 2.0, 3.5])
+@pytest.mark.parametrize("members", [8.0, 40.0])
+def test_uniform_ragged_with_hits(idw, p, members):
+    prob = synthetic.config_local(n=5003, m=3001, members=members, seed=161)
+    data, q = prob["data"], prob["queries"].copy()
+    q[::400] = data[:8 * 400:400, :2][: q[::400].shape[0]]
+    _compare(idw, data, q, p, prob["radius"])
+
+
+def test_clustered(idw):
+    prob = synthetic.config_local(n=20000, m=4000, members=16.0, clustered=True, seed=162)
+    _, cnt = _compare(idw, prob["data"], prob["queries"], 2.0, prob["radius"])
+    assert (cnt == 0).any() and cnt.max() > 100
+
+
+def test_infinite_radius_is_the_global_form(idw):
+    prob = synthetic.uniform_problem(3000, 800, seed=163, exact_hits=4)
+    for p in (2.0, 3.5):
+        Z = idw.interpolate_modified(_dev(prob["data"]), _dev(prob["queries"]), p,
+                                     float("inf")).cpu().numpy()
+        Zg, _ = oracle.idw(prob["data"], prob["queries"], p)
+        assert np.max(np.abs(Z - Zg)) / np.max(np.abs(prob["data"][:, 2])) <= TOL
+
+
+def test_range_edges_take_the_fp64_pass(idw):
+    """3e-19 coordinates (weights near 1e38 overflow the FP32 sums) and 1e17
+    coordinates (weights below 2^-100 per member): the FP64 pass computes the
+    scaled modified weights."""
+    rng = np.random.default_rng(164)
+    for scale, R in ((3e-19, 1e-19), (1e17, 3e16)):
+        xy = (rng.random((400, 2)) * scale).astype(np.float32)
+        data = np.concatenate([xy, rng.standard_normal((400, 1)).astype(np.float32)], 1)
+        q = (rng.random((120, 2)) * scale).astype(np.float32)
+        _compare(idw, data, q, 2.0, R)
+
+
+def test_matches_the_radius_form_membership_and_errors(idw):
+    prob = synthetic.config_local(n=4000, m=1000, members=20.0, seed=165)
+    d, q = _dev(prob["data"]), _dev(prob["queries"])
+    _, cm = idw.interpolate_modified(d, q, 2.0, prob["radius"], counts=True)
+    _, cl = idw.interpolate_local(d, q, 2.0, prob["radius"], counts=True)
+    assert torch.equal(cm, cl)
+    for bad in ((2.0, 0.0), (0.0, 0.1), (2.0, float("nan"))):
+        with pytest.raises(idw.IDWError):
+            idw.interpolate_modified(d, q, bad[0], bad[1])
+
+
+def test_full_size_sampled(idw):
+    prob = synthetic.config_local()
+    data, q = prob["data"], prob["queries"]
+    Z = idw.interpolate_modified(_dev(data), _dev(q), 2.0, prob["radius"]).cpu().numpy()
+    idx = np.sort(np.random.default_rng(166).choice(q.shape[0], 256, replace=False))
+    Z64, _, _ = oracle.idw_modified(data, q[idx], 2.0, prob["radius"])
+    ok = ~np.isnan(Z64)
+    assert np.array_equal(np.isnan(Z[idx]), ~ok)
+    assert np.max(np.abs(Z[idx][ok] - Z64[ok])) / np.max(np.abs(data[:, 2])) <= TOL
