@@ -13,7 +13,8 @@
  * the paper names among its related work (Sec. 1) are here too: Eq. 1 over
  * the data points within a radius R (idw_interpolate_local) and over the k
  * nearest data points (idw_interpolate_knn), each with a prepared index for
- * repeated queries (idw_local_index_*).  Every form has gradients with
+ * repeated queries (idw_local_index_*), and modified Shepard weights on the
+ * radius form (idw_interpolate_modified).  Every form has gradients with
  * respect to z, the data and query coordinates, and p (idw_backward,
  * idw_local_backward, idw_knn_backward).
  *
