@@ -560,7 +560,8 @@ idw_status idw_knn_backward(idw_handle_t handle, const float *data_xyz, int64_t 
  *
  * idw_local_index_interpolate is idw_interpolate_local on a radius index,
  * for any 0 < radius <= the build radius (a smaller radius still uses the
- * build's cells).  idw_local_index_knn is idw_interpolate_knn on a k-NN
+ * build's cells); idw_local_index_modified is idw_interpolate_modified
+ * there.  idw_local_index_knn is idw_interpolate_knn on a k-NN
  * index, for any 1 <= k <= 64.  Outputs, NaN and hit rules are those of
  * the one-shot calls.  Both run on `stream` without host synchronisation
  * (graph-capturable once the handle's workspace has grown) and take the
@@ -582,6 +583,9 @@ idw_status idw_local_index_interpolate(idw_handle_t handle, idw_local_index_t in
                                        const float *queries_xy, int64_t m, double p,
                                        double radius, float *out, int32_t *count_out,
                                        void *stream);
+idw_status idw_local_index_modified(idw_handle_t handle, idw_local_index_t index,
+                                    const float *queries_xy, int64_t m, double p, double radius,
+                                    float *out, int32_t *count_out, void *stream);
 idw_status idw_local_index_knn(idw_handle_t handle, idw_local_index_t index,
                                const float *queries_xy, int64_t m, double p, int32_t k,
                                float *out, int32_t *nbr_out, float *kd2_out, void *stream);

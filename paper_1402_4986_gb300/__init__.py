@@ -318,9 +318,10 @@ class LocalIndex:
         return queries.shape[0]
 
     def interpolate(self, queries, p: float = 2.0, radius: float | None = None, out=None,
-                    counts: bool = False, handle: Handle | None = None):
+                    counts: bool = False, handle: Handle | None = None, modified: bool = False):
         """``interpolate_local`` on the indexed data (radius defaults to the
-        build radius and may not exceed it).  ``handle`` (default: the
+        build radius and may not exceed it); ``modified`` selects the modified
+        Shepard weights (``interpolate_modified``).  ``handle`` (default: the
         build's) supplies the workspace: one handle per concurrent stream."""
         m = self._queries(queries)
         h = handle or self.handle
@@ -328,10 +329,11 @@ class LocalIndex:
         if out is None:
             out = torch.empty(m, dtype=torch.float32, device=self.device)
         cnt = torch.empty(m, dtype=torch.int32, device=self.device) if counts else None
-        st = h.lib.idw_local_index_interpolate(
-            h.ptr, self.ptr, _ptr(queries), m, float(p), 0.0 if r is None else r,
-            _ptr(out), _ptr(cnt), _stream(queries))
-        _lib.check(st, "idw_local_index_interpolate", h.ptr)
+        fn = h.lib.idw_local_index_modified if modified else h.lib.idw_local_index_interpolate
+        st = fn(h.ptr, self.ptr, _ptr(queries), m, float(p), 0.0 if r is None else r,
+                _ptr(out), _ptr(cnt), _stream(queries))
+        _lib.check(st, "idw_local_index_modified" if modified else "idw_local_index_interpolate",
+                   h.ptr)
         return (out, cnt) if counts else out
 
     def knn(self, queries, p: float = 2.0, k: int | None = None, out=None,

@@ -96,6 +96,8 @@ SIGNATURES = {
                                        ctypes.POINTER(c_void_p), c_void_p]),
     "idw_local_index_interpolate": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double,
                                             c_double, c_void_p, c_void_p, c_void_p]),
+    "idw_local_index_modified": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double,
+                                         c_double, c_void_p, c_void_p, c_void_p]),
     "idw_local_index_knn": (c_int, [c_void_p, c_void_p, c_void_p, c_int64, c_double, c_int32,
                                     c_void_p, c_void_p, c_void_p, c_void_p]),
     "idw_local_index_destroy": (c_int, [c_void_p]),

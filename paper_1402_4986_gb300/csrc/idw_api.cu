@@ -363,6 +363,32 @@ idw_status check_common(idw_handle_t h, const void* data, int64_t n, const void*
   return IDW_OK;
 }
 
+// One query call on a radius index, plain or modified Shepard weights.
+idw_status index_radius_call(idw_handle_t h, idw_local_index_t ix,
+                              const float* queries, int64_t m, double p, double radius,
+                              float* out, int32_t* count_out, void* stream, bool modified) {
+  if (!h || !ix || ix->radius <= 0.0 || h->device != ix->device) return IDW_ERR_INVALID_ARG;
+  if (m < 0 || m >= kMaxCount || !(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
+  if (!(radius > 0.0 && radius <= ix->radius)) return IDW_ERR_INVALID_ARG;
+  if (m == 0) return IDW_OK;
+  if (!queries || !out) return IDW_ERR_INVALID_ARG;
+  if (!aligned(queries, 4) || !aligned(out, 4) || (count_out && !aligned(count_out, 4)))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  idw_status st = validate_inputs(h, {{queries, 2 * m, false}}, s);
+  if (st != IDW_OK) return st;
+  const idw::QueryLayout Q = idw::query_layout(m, ix->X.max_cells);
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
+  if (st != IDW_OK) return st;
+  const cudaError_t e = idw::launch_index_local(ix->mem, ix->X, queries, m, p, radius, out,
+                                                count_out, h->ws, Q, h->sm_count, s,
+                                                h->opt_query_order == 0, modified);
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -802,29 +828,19 @@ idw_status idw_local_index_create(idw_handle_t h, const float* data, int64_t n, 
   return IDW_OK;
 }
 
+
 idw_status idw_local_index_interpolate(idw_handle_t h, idw_local_index_t ix,
                                        const float* queries, int64_t m, double p, double radius,
                                        float* out, int32_t* count_out, void* stream) {
   NvtxRange nvtx("idw_local_index_interpolate");
-  if (!h || !ix || ix->radius <= 0.0 || h->device != ix->device) return IDW_ERR_INVALID_ARG;
-  if (m < 0 || m >= kMaxCount || !(p > 0.0) || !std::isfinite(p)) return IDW_ERR_INVALID_ARG;
-  if (!(radius > 0.0 && radius <= ix->radius)) return IDW_ERR_INVALID_ARG;
-  if (m == 0) return IDW_OK;
-  if (!queries || !out) return IDW_ERR_INVALID_ARG;
-  if (!aligned(queries, 4) || !aligned(out, 4) || (count_out && !aligned(count_out, 4)))
-    return IDW_ERR_ALIGNMENT;
-  DeviceGuard guard(h->device);
-  if (!guard.ok) return IDW_ERR_CUDA;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  idw_status st = validate_inputs(h, {{queries, 2 * m, false}}, s);
-  if (st != IDW_OK) return st;
-  const idw::QueryLayout Q = idw::query_layout(m, ix->X.max_cells);
-  st = ensure_buffer(h, &h->ws, &h->ws_bytes, Q.bytes);
-  if (st != IDW_OK) return st;
-  const cudaError_t e = idw::launch_index_local(ix->mem, ix->X, queries, m, p, radius, out,
-                                                count_out, h->ws, Q, h->sm_count, s,
-                                                h->opt_query_order == 0);
-  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+  return index_radius_call(h, ix, queries, m, p, radius, out, count_out, stream, false);
+}
+
+idw_status idw_local_index_modified(idw_handle_t h, idw_local_index_t ix, const float* queries,
+                                    int64_t m, double p, double radius, float* out,
+                                    int32_t* count_out, void* stream) {
+  NvtxRange nvtx("idw_local_index_modified");
+  return index_radius_call(h, ix, queries, m, p, radius, out, count_out, stream, true);
 }
 
 idw_status idw_local_index_knn(idw_handle_t h, idw_local_index_t ix, const float* queries,

@@ -1797,7 +1797,7 @@ cudaError_t launch_index_build(const float* data, int64_t n, double radius, int 
 cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
                                int64_t m, double p, double radius, float* out, int32_t* count_out,
                                void* workspace, const QueryLayout& Q, int sm_count,
-                               cudaStream_t s, bool sort_queries) {
+                               cudaStream_t s, bool sort_queries, bool modified) {
   const unsigned char* mem = static_cast<const unsigned char*>(index_mem);
   const GridDev* xgrid = reinterpret_cast<const GridDev*>(mem + X.off_grid);
   cudaError_t e = launch_query_sort(xgrid, queries, m, radius, X.max_cells, workspace, Q, sm_count,
@@ -1812,12 +1812,20 @@ cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, cons
   const float r2f = static_cast<float>(radius * radius);
   const float r2t = r2f > 0.f ? r2f : 0x1p-149f;
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
-  if (p == 2.0)
+  if (modified) {
+    if (p == 2.0)
+      local_query_kernel<kPow2, kWeightModified><<<qgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out, radius);
+    else
+      local_query_kernel<kPowGeneral, kWeightModified><<<qgrid, kLocalThreads, 0, s>>>(
+          grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out, radius);
+  } else if (p == 2.0) {
     local_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out);
-  else
+  } else {
     local_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, X.n, starts, sums, qrec, m, p, r2f, r2t, out, count_out);
+  }
   return cudaGetLastError();
 }
 

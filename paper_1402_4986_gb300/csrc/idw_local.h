@@ -96,11 +96,12 @@ cudaError_t launch_index_build(const float* data, int64_t n, double radius, int 
                                void* index_mem, const IndexLayout& X, int sm_count,
                                cudaStream_t s);
 
-// One query call on a radius index (0 < radius <= the build radius).
+// One query call on a radius index (0 < radius <= the build radius), with
+// the plain or (modified = true) the modified Shepard weights.
 cudaError_t launch_index_local(const void* index_mem, const IndexLayout& X, const float* queries,
                                int64_t m, double p, double radius, float* out, int32_t* count_out,
                                void* workspace, const QueryLayout& Q, int sm_count,
-                               cudaStream_t s, bool sort_queries = true);
+                               cudaStream_t s, bool sort_queries = true, bool modified = false);
 
 // One query call on a k-NN index (1 <= k <= kKnnMax).
 cudaError_t launch_index_knn(const void* index_mem, const IndexLayout& X, const float* queries,

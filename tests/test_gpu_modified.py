@@ -102,3 +102,20 @@ def test_full_size_sampled(idw):
     ok = ~np.isnan(Z64)
     assert np.array_equal(np.isnan(Z[idx]), ~ok)
     assert np.max(np.abs(Z[idx][ok] - Z64[ok])) / np.max(np.abs(data[:, 2])) <= TOL
+
+
+def test_prepared_index(idw):
+    """The radius index serves modified Shepard queries too, at the build
+    radius and below it."""
+    prob = synthetic.config_local(n=6000, m=2000, members=30.0, seed=167)
+    data, q = prob["data"], prob["queries"]
+    ix = idw.LocalIndex(_dev(data), radius=prob["radius"])
+    for r in (prob["radius"], prob["radius"] / 2):
+        Z, cnt = ix.interpolate(_dev(q), 2.5, r, counts=True, modified=True)
+        Z64, _, c64 = oracle.idw_modified(data, q, 2.5, r)
+        assert np.array_equal(cnt.cpu().numpy(), c64)
+        ok = ~np.isnan(Z64)
+        Zc = Z.cpu().numpy()
+        assert np.array_equal(np.isnan(Zc), ~ok)
+        assert np.max(np.abs(Zc[ok] - Z64[ok])) / np.max(np.abs(data[:, 2])) <= TOL
+
