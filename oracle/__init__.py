@@ -75,6 +75,9 @@ def bind(lib):
                                         ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int32), ctypes.c_int]
     lib.oracle_idw_modified.restype = ctypes.c_int
+    lib.oracle_idw_modified_grad.argtypes = [d, i64, d, i64, ctypes.c_double, ctypes.c_double, d,
+                                             d, d, d, d, d]
+    lib.oracle_idw_modified_grad.restype = ctypes.c_int
     return lib
 
 
@@ -265,3 +268,24 @@ def idw_modified(data_xyz, queries_xy, p: float, radius: float, threads: int = 0
     if rc < 0:
         raise ValueError("oracle_idw_modified rejected its arguments")
     return Z, hit, count
+
+
+def idw_modified_grad(data_xyz, queries_xy, p: float, radius: float, g):
+    """Gradients of L = sum_j g_j Z(q_j) for modified Shepard (FP64, the
+    membership sets held fixed).  Returns a dict as ``idw_local_grad``."""
+    lib = _load()
+    data = _f64(data_xyz, 3)
+    q = _f64(queries_xy, 2)
+    n, m = data.shape[0], q.shape[0]
+    g = np.ascontiguousarray(np.asarray(g), dtype=np.float64).reshape(m)
+    Z = np.empty(m, np.float64)
+    gz = np.empty(n, np.float64)
+    gxy = np.empty((n, 2), np.float64)
+    gq = np.empty((m, 2), np.float64)
+    gp = np.empty(1, np.float64)
+    rc = lib.oracle_idw_modified_grad(_ptr(data), n, _ptr(q), m, float(p), float(radius),
+                                      _ptr(g), _ptr(Z), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp))
+    if rc < 0:
+        raise ValueError("oracle_idw_modified_grad rejected its arguments")
+    return {"Z": Z, "grad_z": gz, "grad_xy": gxy, "grad_q": gq, "grad_p": float(gp[0])}
+

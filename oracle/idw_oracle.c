@@ -625,6 +625,93 @@ int oracle_idw_modified(const double *data, int64_t n, const double *q, int64_t 
     return parallel_for(m, nthreads, modified_range, &c);
 }
 
+/* Gradient of L = sum_j g_j Z(q_j) for modified Shepard (oracle_idw_modified),
+ * membership held fixed as for the radius form.  With t_i = 1/d_i - 1/R and
+ * w_i = t_i^p (scaled by t_max^p, which cancels):
+ *     dw_i/dq = -p w_i (q - x_i) / (t_i d_i^3) = -dw_i/dx_i,   dw_i/dp = w_i ln t_i,
+ * so dZ/dq = -(p/S0) sum_i (z_i - Z) w_i (q - x_i)/(t_i d_i^3), dZ/dx_i the
+ * negated term, dZ/dz_i = w_i/S0 and dZ/dp = (1/S0) sum_i (z_i - Z) w_i ln t_i.
+ * Members of zero weight (t_i = 0) contribute nothing.  Hits and empty
+ * neighbourhoods as oracle_idw_local_grad.  Returns threads used (1), or -1. */
+int oracle_idw_modified_grad(const double *data, int64_t n, const double *q, int64_t m, double p,
+                             double radius, const double *g, double *Z, double *grad_z,
+                             double *grad_xy, double *grad_q, double *grad_p)
+{
+    if (!data || !q || !g || !Z || !grad_z || !grad_xy || !grad_q || !grad_p || n < 1 ||
+        m < 1 || !(p > 0.0) || !isfinite(p) || !(radius > 0.0))
+        return -1;
+    int64_t *hit = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+    int32_t *count = (int32_t *)malloc((size_t)m * sizeof(int32_t));
+    nsum *acc = (nsum *)calloc((size_t)n * 3, sizeof(nsum)); /* per point: z, x, y */
+    int t = -1;
+    if (hit && count && acc)
+        t = oracle_idw_modified(data, n, q, m, p, radius, Z, hit, count, 1);
+    const float r2f = (float)(radius * radius);
+    if (t >= 0) {
+        nsum ptot = {0, 0};
+        for (int64_t j = 0; j < m; j++) {
+            const double gj = g[j], qx = q[2 * j], qy = q[2 * j + 1];
+            const float qxf = (float)qx, qyf = (float)qy;
+            grad_q[2 * j] = 0.0;
+            grad_q[2 * j + 1] = 0.0;
+            if (hit[j] >= 0) { /* exact hit: all of g_j goes to the point's z */
+                nsum_add(&acc[3 * hit[j]], gj);
+                continue;
+            }
+            if (isnan(Z[j]))
+                continue;
+            double tm = 0.0;
+            for (int64_t i = 0; i < n; i++) {
+                const double *x = data + 3 * i;
+                if (local_member(qxf, qyf, (float)x[0], (float)x[1], r2f)) {
+                    const double tt = modified_base(radius, sqrt(sqdist(qx, qy, x[0], x[1])));
+                    if (tt > tm)
+                        tm = tt;
+                }
+            }
+            nsum u0 = {0, 0};
+            for (int64_t i = 0; i < n; i++) {
+                const double *x = data + 3 * i;
+                if (local_member(qxf, qyf, (float)x[0], (float)x[1], r2f))
+                    nsum_add(&u0, pow(modified_base(radius, sqrt(sqdist(qx, qy, x[0], x[1]))) / tm, p));
+            }
+            const double S0 = nsum_value(&u0), Zj = Z[j];
+            nsum vx = {0, 0}, vy = {0, 0}, vp = {0, 0};
+            for (int64_t i = 0; i < n; i++) {
+                const double *x = data + 3 * i;
+                if (!local_member(qxf, qyf, (float)x[0], (float)x[1], r2f))
+                    continue;
+                const double ex = qx - x[0], ey = qy - x[1], d = sqrt(ex * ex + ey * ey);
+                const double tt = modified_base(radius, d);
+                if (tt == 0.0)
+                    continue; /* zero weight: no derivative either */
+                const double w = pow(tt / tm, p);
+                const double b = (x[2] - Zj) * w;
+                const double f = b / (tt * d * d * d); /* (z_i - Z) w_i / (t_i d_i^3) */
+                nsum_add(&vx, f * ex);
+                nsum_add(&vy, f * ey);
+                nsum_add(&vp, b * log(tt));
+                nsum_add(&acc[3 * i], gj * w / S0);
+                nsum_add(&acc[3 * i + 1], gj * (p / S0) * f * ex);
+                nsum_add(&acc[3 * i + 2], gj * (p / S0) * f * ey);
+            }
+            grad_q[2 * j] = -gj * (p / S0) * nsum_value(&vx);
+            grad_q[2 * j + 1] = -gj * (p / S0) * nsum_value(&vy);
+            nsum_add(&ptot, gj * nsum_value(&vp) / S0);
+        }
+        for (int64_t i = 0; i < n; i++) {
+            grad_z[i] = nsum_value(&acc[3 * i]);
+            grad_xy[2 * i] = nsum_value(&acc[3 * i + 1]);
+            grad_xy[2 * i + 1] = nsum_value(&acc[3 * i + 2]);
+        }
+        *grad_p = nsum_value(&ptot);
+    }
+    free(hit);
+    free(count);
+    free(acc);
+    return t;
+}
+
 /* ------------------------------------------------------- k-NN variant */
 
 typedef struct {

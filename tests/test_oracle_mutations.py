@@ -79,6 +79,12 @@ MUTATIONS = [
      "const double t = isinf(radius) ? 1.0 / d : (radius + d) / (radius * d);"),
     ("modified power halved", "const double w = pow(t / tmax, c->p);",
      "const double w = pow(t / tmax, 0.5 * c->p);"),
+    ("modified gradient with 1/d^2 in place of 1/(t d^3)",
+     "const double f = b / (tt * d * d * d); /* (z_i - Z) w_i / (t_i d_i^3) */",
+     "const double f = b / (d * d); /* (z_i - Z) w_i / (t_i d_i^3) */"),
+    ("modified p-gradient with the global factor -1/2",
+     "nsum_add(&ptot, gj * nsum_value(&vp) / S0);",
+     "nsum_add(&ptot, -0.5 * gj * nsum_value(&vp) / S0);"),
 ]
 
 PINS = [
@@ -119,6 +125,9 @@ PINS = [
     pins.test_modified_with_infinite_radius_is_the_global_form,
     pins.test_modified_is_continuous_at_the_radius,
     pins.test_modified_members_and_hits_are_the_radius_form_s,
+    lambda: pins.test_modified_gradient_matches_central_differences(3.0),
+    pins.test_modified_gradient_at_infinite_radius_is_the_global_gradient,
+    pins.test_modified_gradient_sums_translation_and_hits,
 ]
 
 

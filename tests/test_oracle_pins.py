@@ -779,3 +779,79 @@ def test_modified_members_and_hits_are_the_radius_form_s():
     _, hm, cm = oracle.idw_modified(prob["data"], prob["queries"], 2.0, R)
     _, hl, cl = oracle.idw_local(prob["data"], prob["queries"], 2.0, R)
     assert np.array_equal(hm, hl) and np.array_equal(cm, cl)
+
+
+def _modified_loss(data, q, p, radius, g, ok):
+    Z, _, _ = oracle.idw_modified(data, q, p, radius)
+    return float(np.dot(g[ok], Z[ok]))
+
+
+@pytest.mark.parametrize("p", [2.0, 3.0])
+def test_modified_gradient_matches_central_differences(p):
+    """Central differences of the modified Shepard oracle's loss, for
+    coordinates whose perturbation moves no membership set, against the
+    analytic gradient (the weights' derivative involves 1/(t d^3))."""
+    rng = np.random.default_rng(64)
+    n = m = 96
+    data = np.empty((n, 3), np.float64)
+    data[:, :2] = synthetic.separated_xy(rng, n, 2e-3).astype(np.float32)
+    data[:, 2] = rng.standard_normal(n)
+    q = (synthetic.separated_xy(rng, m, 2e-3) + 1e-3 * rng.random((m, 2))).astype(np.float32)
+    q = q.astype(np.float64)
+    R = 0.2
+    g = rng.standard_normal(m)
+    _, _, c0 = oracle.idw_modified(data, q, p, R)
+    ok = c0 > 0
+    G = oracle.idw_modified_grad(data, q, p, R, g)
+    eps = 1e-6
+
+    def fd(arr, idx):
+        a = arr.copy(); a[idx] += eps
+        b = arr.copy(); b[idx] -= eps
+        args = ((a, q), (b, q)) if arr is data else ((data, a), (data, b))
+        for d_, q_ in args:
+            if not np.array_equal(oracle.idw_modified(d_, q_, p, R)[2], c0):
+                return None
+        return (_modified_loss(*args[0], p, R, g, ok) -
+                _modified_loss(*args[1], p, R, g, ok)) / (2 * eps)
+
+    scale_d = max(np.abs(G["grad_xy"]).max(), np.abs(G["grad_z"]).max())
+    checked = 0
+    for i in rng.choice(n, 16, replace=False):
+        for col, ref in ((2, G["grad_z"][i]), (0, G["grad_xy"][i, 0]), (1, G["grad_xy"][i, 1])):
+            v = fd(data, (i, col))
+            if v is not None:
+                assert abs(v - ref) <= 1e-6 * scale_d, (i, col, v, ref)
+                checked += 1
+    scale_q = np.abs(G["grad_q"]).max()
+    for j in rng.choice(m, 16, replace=False):
+        for col in (0, 1):
+            v = fd(q, (j, col))
+            if v is not None:
+                assert abs(v - G["grad_q"][j, col]) <= 1e-6 * scale_q, (j, col)
+                checked += 1
+    assert checked >= 40
+    dp = (_modified_loss(data, q, p + eps, R, g, ok) -
+          _modified_loss(data, q, p - eps, R, g, ok)) / (2 * eps)
+    assert abs(dp - G["grad_p"]) <= 1e-6 * max(1.0, abs(dp))
+
+
+def test_modified_gradient_at_infinite_radius_is_the_global_gradient():
+    prob = synthetic.uniform_problem(300, 120, seed=65)
+    g = np.random.default_rng(66).standard_normal(120)
+    M = oracle.idw_modified_grad(prob["data"], prob["queries"], 2.5, float("inf"), g)
+    G = oracle.idw_grad(prob["data"], prob["queries"], 2.5, g)
+    for key in ("grad_z", "grad_xy", "grad_q"):
+        assert np.abs(M[key] - G[key]).max() <= 1e-12 * np.abs(G[key]).max(), key
+    assert abs(M["grad_p"] - G["grad_p"]) <= 1e-12 * abs(G["grad_p"])
+
+
+def test_modified_gradient_sums_translation_and_hits():
+    prob = synthetic.config_local(seed=67, n=600, m=400, members=6.0, clustered=True)
+    data, q, R = prob["data"], prob["queries"].copy(), prob["radius"]
+    q[5] = data[17, :2]  # an exact hit
+    M = oracle.idw_modified_grad(data, q, 2.0, R, np.ones(q.shape[0]))
+    Zm, hit, _ = oracle.idw_modified(data, q, 2.0, R)
+    assert hit[5] >= 0 and np.all(M["grad_q"][5] == 0)
+    assert abs(M["grad_z"].sum() - np.isfinite(Zm).sum()) <= 1e-10
+    assert np.abs(M["grad_xy"].sum(0) + M["grad_q"].sum(0)).max() <= 1e-9 * np.abs(M["grad_q"]).max()
