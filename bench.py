@@ -760,6 +760,10 @@ def run_local(args):
                      "queries_s": m / (mms / 1e3), "error_vs_fp64_oracle": merr,
                      "error_sample_queries": len(idx)})
         gout = torch.from_numpy(np.random.default_rng(7).standard_normal(m).astype(np.float32)).cuda()
+        mbms = _events_ms(lambda: idw.local_backward(d, q, 2.0, R, gout, modified=True), 10, warm=3)
+        rows.append({"data": "clustered" if clustered else "uniform",
+                     "call": "modified Shepard backward", "n": n, "m": m, "radius": R, "p": 2.0,
+                     "ms": mbms, "queries_s": m / (mbms / 1e3)})
         bms = _events_ms(lambda: idw.local_backward(d, q, 2.0, R, gout), 10, warm=3)
         _, _, gq, _ = idw.local_backward(d, q, 2.0, R, gout)
         sub = np.sort(idx[:128])

@@ -513,6 +513,17 @@ idw_status idw_local_backward(idw_handle_t handle, const float *data_xyz, int64_
                               float *grad_query_xy, double *grad_p, void *stream);
 
 /*
+ * Gradients of modified Shepard (idw_interpolate_modified): as
+ * idw_local_backward, with each pair's terms those of the weights
+ * w = t^p, t = 1/d - 1/R:  dw/dq = -p w (q - x) / (t d^3) = -dw/dx and
+ * dw/dp = w ln t.  Members of zero weight contribute nothing.
+ */
+idw_status idw_modified_backward(idw_handle_t handle, const float *data_xyz, int64_t n,
+                                 const float *queries_xy, int64_t m, double p, double radius,
+                                 const float *grad_out, float *grad_z, float *grad_data_xy,
+                                 float *grad_query_xy, double *grad_p, void *stream);
+
+/*
  * Gradients of the k-nearest-neighbour form: as idw_local_backward, for Z
  * from idw_interpolate_knn with the same k (1 <= k <= 64).  Each query's
  * selection (its k smallest keys) is held fixed, so each derivative is the

@@ -23,7 +23,8 @@ __all__ = [
     "IDWError", "Handle", "get_handle", "interpolate", "interpolate_saved", "interpolate_host",
     "interpolate_batched", "interpolate_local", "interpolate_modified", "interpolate_knn",
     "LocalIndex",
-    "local_backward", "LocalIDWFunction", "idw_local", "knn_backward", "KnnIDWFunction",
+    "local_backward", "LocalIDWFunction", "idw_local", "idw_modified", "knn_backward",
+    "KnnIDWFunction",
     "idw_knn",
     "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
     "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
@@ -416,8 +417,10 @@ def idw(data, queries, p=2.0):
 
 
 def local_backward(data, queries, p, radius, grad_out, need_z=True, need_data_xy=True,
-                   need_query_xy=True, need_p=True, handle: Handle | None = None):
-    """Gradients of the radius form (``idw_local_backward``); returns
+                   need_query_xy=True, need_p=True, handle: Handle | None = None,
+                   modified: bool = False):
+    """Gradients of the radius form (``idw_local_backward``), or with
+    ``modified`` of modified Shepard (``idw_modified_backward``); returns
     (gz, gxy, gq, gp), each None when not requested."""
     _check_inputs(data, queries, PREC_F32_COMP)
     n, m = data.shape[0], queries.shape[0]
@@ -428,43 +431,51 @@ def local_backward(data, queries, p, radius, grad_out, need_z=True, need_data_xy
     gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
     h = handle or get_handle(dev)
     g = grad_out.contiguous().to(torch.float32)
-    st = h.lib.idw_local_backward(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), float(radius),
-                                  _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), _stream(data))
-    _lib.check(st, "idw_local_backward", h.ptr)
+    name = "idw_modified_backward" if modified else "idw_local_backward"
+    st = getattr(h.lib, name)(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), float(radius),
+                              _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), _stream(data))
+    _lib.check(st, name, h.ptr)
     return gz, gxy, gq, gp
 
 
 class LocalIDWFunction(torch.autograd.Function):
     """Differentiable radius form: Eq. 1 over the data within ``radius`` of
-    each query, with the hand-written local adjoint (membership held fixed).
-    Queries without members give NaN and pass no gradient."""
+    each query (plain d^-p weights, or modified Shepard weights), with the
+    hand-written local adjoint (membership held fixed).  Queries without
+    members give NaN and pass no gradient."""
 
     @staticmethod
-    def forward(ctx, data, queries, p, radius):
+    def forward(ctx, data, queries, p, radius, modified=False):
         pv = float(p.item()) if torch.is_tensor(p) else float(p)
-        Z = interpolate_local(data.detach().contiguous(), queries.detach().contiguous(), pv,
-                              float(radius))
+        fwd = interpolate_modified if modified else interpolate_local
+        Z = fwd(data.detach().contiguous(), queries.detach().contiguous(), pv, float(radius))
         ctx.save_for_backward(data, queries)
         ctx.p, ctx.radius, ctx.p_is_tensor = pv, float(radius), torch.is_tensor(p)
+        ctx.modified = bool(modified)
         return Z
 
     @staticmethod
     def backward(ctx, grad):
         data, queries = ctx.saved_tensors
-        need_d, need_q, need_p, _ = ctx.needs_input_grad
+        need_d, need_q, need_p = ctx.needs_input_grad[:3]
         want_p = need_p and ctx.p_is_tensor
         gz, gxy, gq, gp = local_backward(data.detach().contiguous(), queries.detach().contiguous(),
                                          ctx.p, ctx.radius, grad, need_z=need_d,
                                          need_data_xy=need_d, need_query_xy=need_q,
-                                         need_p=want_p)
+                                         need_p=want_p, modified=ctx.modified)
         gdata = torch.cat([gxy, gz[:, None]], 1) if need_d else None
         gp_out = gp.to(torch.float32).reshape(()) if want_p else None
-        return gdata, gq if need_q else None, gp_out, None
+        return gdata, gq if need_q else None, gp_out, None, None
 
 
 def idw_local(data, queries, p=2.0, radius=1.0):
     """Autograd entry for the radius form; p may be a tensor to get dL/dp."""
-    return LocalIDWFunction.apply(data, queries, p, radius)
+    return LocalIDWFunction.apply(data, queries, p, radius, False)
+
+
+def idw_modified(data, queries, p=2.0, radius=1.0):
+    """Autograd entry for modified Shepard; p may be a tensor to get dL/dp."""
+    return LocalIDWFunction.apply(data, queries, p, radius, True)
 
 
 def knn_backward(data, queries, p, k, grad_out, need_z=True, need_data_xy=True,

@@ -106,6 +106,9 @@ SIGNATURES = {
                                    c_void_p]),
     "idw_interpolate_modified": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64,
                                          c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "idw_modified_backward": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
+                                      c_double, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]),
     "idw_knn_backward": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                  c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  c_void_p]),

@@ -389,6 +389,39 @@ idw_status index_radius_call(idw_handle_t h, idw_local_index_t ix,
 }
 
 
+// The radius form's gradients, plain or modified Shepard weights.
+idw_status radius_backward_call(idw_handle_t h, const float* data, int64_t n,
+                                const float* queries,
+                              int64_t m, double p, double radius, const float* grad_out,
+                              float* grad_z, float* grad_data_xy, float* grad_query_xy,
+                              double* grad_p, void* stream, bool modified) {
+  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, grad_out);
+  if (st != IDW_OK) return st;
+  if (!(radius > 0.0)) return IDW_ERR_INVALID_ARG;
+  if ((grad_z && !aligned(grad_z, 4)) || (grad_data_xy && !aligned(grad_data_xy, 4)) ||
+      (grad_query_xy && !aligned(grad_query_xy, 4)) || (grad_p && !aligned(grad_p, 8)))
+    return IDW_ERR_ALIGNMENT;
+  DeviceGuard guard(h->device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaSuccess;
+  if (m == 0) {  // no query: every gradient is zero
+    if (grad_z) e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s);
+    if (e == cudaSuccess && grad_data_xy) e = cudaMemsetAsync(grad_data_xy, 0, size_t(n) * 8, s);
+    if (e == cudaSuccess && grad_p) e = cudaMemsetAsync(grad_p, 0, sizeof(double), s);
+    return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+  }
+  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}, {grad_out, m, false}}, s);
+  if (st != IDW_OK) return st;
+  const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::local_grad_record_bytes(m));
+  if (st != IDW_OK) return st;
+  e = idw::launch_local_backward(data, n, queries, m, p, radius, grad_out, grad_z, grad_data_xy,
+                                 grad_query_xy, grad_p, h->ws, L, h->sm_count, s, modified);
+  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+}
+
+
 }  // namespace
 
 extern "C" {
@@ -734,30 +767,17 @@ idw_status idw_local_backward(idw_handle_t h, const float* data, int64_t n, cons
                               float* grad_z, float* grad_data_xy, float* grad_query_xy,
                               double* grad_p, void* stream) {
   NvtxRange nvtx("idw_local_backward");
-  idw_status st = check_common(h, data, n, queries, m, p, IDW_PREC_F32_COMP, grad_out);
-  if (st != IDW_OK) return st;
-  if (!(radius > 0.0)) return IDW_ERR_INVALID_ARG;
-  if ((grad_z && !aligned(grad_z, 4)) || (grad_data_xy && !aligned(grad_data_xy, 4)) ||
-      (grad_query_xy && !aligned(grad_query_xy, 4)) || (grad_p && !aligned(grad_p, 8)))
-    return IDW_ERR_ALIGNMENT;
-  DeviceGuard guard(h->device);
-  if (!guard.ok) return IDW_ERR_CUDA;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaSuccess;
-  if (m == 0) {  // no query: every gradient is zero
-    if (grad_z) e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s);
-    if (e == cudaSuccess && grad_data_xy) e = cudaMemsetAsync(grad_data_xy, 0, size_t(n) * 8, s);
-    if (e == cudaSuccess && grad_p) e = cudaMemsetAsync(grad_p, 0, sizeof(double), s);
-    return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
-  }
-  st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}, {grad_out, m, false}}, s);
-  if (st != IDW_OK) return st;
-  const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
-  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::local_grad_record_bytes(m));
-  if (st != IDW_OK) return st;
-  e = idw::launch_local_backward(data, n, queries, m, p, radius, grad_out, grad_z, grad_data_xy,
-                                 grad_query_xy, grad_p, h->ws, L, h->sm_count, s);
-  return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
+  return radius_backward_call(h, data, n, queries, m, p, radius, grad_out, grad_z, grad_data_xy,
+                              grad_query_xy, grad_p, stream, false);
+}
+
+idw_status idw_modified_backward(idw_handle_t h, const float* data, int64_t n,
+                                 const float* queries, int64_t m, double p, double radius,
+                                 const float* grad_out, float* grad_z, float* grad_data_xy,
+                                 float* grad_query_xy, double* grad_p, void* stream) {
+  NvtxRange nvtx("idw_modified_backward");
+  return radius_backward_call(h, data, n, queries, m, p, radius, grad_out, grad_z, grad_data_xy,
+                              grad_query_xy, grad_p, stream, true);
 }
 
 idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const float* queries,

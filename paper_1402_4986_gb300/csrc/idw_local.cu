@@ -44,6 +44,7 @@
 #include <cstdint>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "idw.h"
 #include "idw_device.cuh"
@@ -692,7 +693,8 @@ __global__ void __launch_bounds__(kLocalThreads)
 // (FP64-to-FP32 conversions run at the FP64 rate on this part); queries on
 // the FP64 path keep their values in a second array read only for them.
 struct LocalGradRec {
-  float d2min;  // the members' smallest d^2 (FP32 path)
+  float d2min;  // the weights' scale (FP32 path): the members' smallest d^2, or
+                // for the modified weights their largest base 1/d - 1/R
   float c;      // g_j / S0 (scaled), or g_j at an exact hit
   float z;      // Z_j
   int code;     // >= 0: exact hit (data index); -1: nothing; -2: FP32; -3: FP64
@@ -717,24 +719,50 @@ struct GradF64 {
   double gp;
   LocalGradRec64 rec;
 };
+// FP64 weight terms of one member at squared distance e2 under the scale:
+// the weight w, the pair factor f (w / d^2, or for the modified weights
+// w / (t d^3)) and the dL/dp log term (ln of d^2 / d2_min, or of t / t_max).
+struct GradTerms64 {
+  double w, f, l;
+};
+__device__ __forceinline__ GradTerms64 grad_terms64(double e2, double scale, double p,
+                                                    bool modified, double radius) {
+  if (!modified) {
+    const double w = pow(scale / e2, 0.5 * p);
+    return GradTerms64{w, w / e2, log(e2 / scale)};
+  }
+  const double d = sqrt(e2);
+  const double t = isinf(radius) ? 1.0 / d : (radius - d) / (radius * d);
+  if (!(t > 0.0)) return GradTerms64{0.0, 0.0, 0.0};
+  const double w = pow(t / scale, p);
+  return GradTerms64{w, w / (t * e2 * d), log(t / scale)};
+}
+
 __device__ __noinline__ GradF64 grad_query_f64(const Runs runs, const float4* __restrict__ sorted,
                                                float qx, float qy, float r2f, double p,
-                                               float gj) {
-  double dmin = INFINITY;
+                                               float gj, bool modified, double radius) {
+  double scale = modified ? 0.0 : INFINITY;  // d2_min, or the largest base t
   for (int rr = 0; rr < 5; ++rr)
     for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
       const float4 v = sorted[k];
       if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
-      const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-      dmin = fmin(dmin, ex * ex + ey * ey);
+      const double ex = double(qx) - v.x, ey = double(qy) - v.y, e2 = ex * ex + ey * ey;
+      if (modified) {
+        const double d = sqrt(e2);
+        scale = fmax(scale, isinf(radius) ? 1.0 / d : (radius - d) / (radius * d));
+      } else {
+        scale = fmin(scale, e2);
+      }
     }
+  GradF64 r{0.f, 0.f, 0.0, LocalGradRec64{0.0, 0.0, 0.0}};
+  if (!(scale > 0.0)) return r;  // no member of positive weight: no gradient
   double s0 = 0.0, s1 = 0.0;
   for (int rr = 0; rr < 5; ++rr)
     for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
       const float4 v = sorted[k];
       if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
       const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-      const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+      const double w = grad_terms64(ex * ex + ey * ey, scale, p, modified, radius).w;
       s0 += w;
       s1 += w * double(v.z);
     }
@@ -745,22 +773,30 @@ __device__ __noinline__ GradF64 grad_query_f64(const Runs runs, const float4* __
       const float4 v = sorted[k];
       if (!(fp32_d2(qx, qy, v.x, v.y) < r2f)) continue;
       const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-      const double d2 = ex * ex + ey * ey;
-      const double w = pow(dmin / d2, 0.5 * p);
-      const double a = (double(v.z) - Z) * w;
-      ax += a * ex / d2;
-      ay += a * ey / d2;
-      al += a * log(d2 / dmin);
+      const GradTerms64 g = grad_terms64(ex * ex + ey * ey, scale, p, modified, radius);
+      const double dz = double(v.z) - Z;
+      ax += dz * g.f * ex;
+      ay += dz * g.f * ey;
+      al += dz * g.w * g.l;
     }
-  GradF64 r;
   r.gqx = static_cast<float>(-double(gj) * p / s0 * ax);
   r.gqy = static_cast<float>(-double(gj) * p / s0 * ay);
-  r.gp = -0.5 * double(gj) * al / s0;
-  r.rec = LocalGradRec64{dmin, double(gj) / s0, Z};
+  r.gp = (modified ? 1.0 : -0.5) * double(gj) * al / s0;
+  r.rec = LocalGradRec64{scale, double(gj) / s0, Z};
   return r;
 }
 
+// (a / b)^p for the modified weights (lb = log2 b; p = 2 needs no log).
 template <int MODE>
+__device__ __forceinline__ float modified_ratio(float a, float b, float lb, float pf) {
+  if (MODE == kPow2) {
+    const float r = a * rcp_approx(b);
+    return r * r;
+  }
+  return ex2_approx(pf * (lg2_approx(a) - lb));
+}
+
+template <int MODE, int WMODE = kWeightShepard>
 __global__ void __launch_bounds__(kLocalThreads)
     local_grad_query_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                             int64_t n, const int32_t* __restrict__ starts,
@@ -768,7 +804,8 @@ __global__ void __launch_bounds__(kLocalThreads)
                             int64_t m, double p, float r2f, float r2t,
                             const float* __restrict__ grad_out, float* __restrict__ grad_q,
                             double* __restrict__ grad_p, LocalGradRec* __restrict__ rec,
-                            LocalGradRec64* __restrict__ rec64) {
+                            LocalGradRec64* __restrict__ rec64, double radius) {
+  constexpr bool kMod = WMODE == kWeightModified;
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double gp = 0.0;  // this query's share of dL/dp (every lane joins the warp sum)
   if (t < m) {
@@ -778,12 +815,14 @@ __global__ void __launch_bounds__(kLocalThreads)
     if (dcheck(j >= 0 && j < m, kSiteOutput)) {
       const float gj = grad_out[j];
       const Runs runs(*grid, qx, qy, starts, base);
-      // One pass: hit, members, d2_min, and the sums with weights scaled by
-      // the smallest d^2 so far (rescaled, as in an online softmax, when a
-      // smaller one appears, so every scaled weight stays <= 1).
+      // One pass: hit, members, and the sums with weights scaled by the
+      // heaviest member so far (the smallest d^2, or for the modified
+      // weights the largest base 1/d - 1/R), rescaled as in an online softmax
+      // when a heavier one appears, so every scaled weight stays <= 1.
       const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+      const float inv_r = kMod ? static_cast<float>(1.0 / radius) : 0.f;
       int best = INT_MAX, members = 0;
-      float d2min = INFINITY, lmin = 0.f, s0 = 0.f, s1 = 0.f;
+      float d2min = INFINITY, scale = kMod ? 0.f : INFINITY, lsc = 0.f, s0 = 0.f, s1 = 0.f;
 #pragma unroll
       for (int rr = 0; rr < 5; ++rr)
         for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
@@ -797,17 +836,35 @@ __global__ void __launch_bounds__(kLocalThreads)
           }
           if (!(d2 < r2f)) continue;
           ++members;
-          if (d2 < d2min) {
-            const float l = MODE == kPow2 ? 0.f : lg2_approx(d2);
-            if (members > 1) {
-              const float f = grad_weight<MODE>(d2min, d2, l, hp);  // (d2 / d2min_old)^(p/2)
-              s0 *= f;
-              s1 *= f;
+          d2min = fminf(d2min, d2);
+          float w;
+          if (kMod) {
+            const float tb = fmaxf(rsqrt_approx(d2) - inv_r, 0.f);
+            if (!(tb > 0.f)) continue;  // zero weight
+            if (tb > scale) {
+              const float l = MODE == kPow2 ? 0.f : lg2_approx(tb);
+              if (scale > 0.f) {
+                const float f = modified_ratio<MODE>(scale, tb, l, pf);  // (t_old / t)^p
+                s0 *= f;
+                s1 *= f;
+              }
+              scale = tb;
+              lsc = l;
             }
-            d2min = d2;
-            lmin = l;
+            w = modified_ratio<MODE>(tb, scale, lsc, pf);
+          } else {
+            if (d2 < scale) {
+              const float l = MODE == kPow2 ? 0.f : lg2_approx(d2);
+              if (members > 1) {
+                const float f = grad_weight<MODE>(scale, d2, l, hp);  // (d2 / d2min_old)^(p/2)
+                s0 *= f;
+                s1 *= f;
+              }
+              scale = d2;
+              lsc = l;
+            }
+            w = grad_weight<MODE>(d2, scale, lsc, hp);
           }
-          const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
           s0 += w;
           s1 = fmaf(w, v.z, s1);
         }
@@ -816,11 +873,11 @@ __global__ void __launch_bounds__(kLocalThreads)
       if (best != INT_MAX) {
         out.code = best;
         out.c = gj;
-      } else if (members > 0) {
+      } else if (members > 0 && (!kMod || scale > 0.f)) {
         bool f32 = d2min >= 0x1p-100f;
         if (f32) {
           const float Z = s1 / s0;
-          const float lmin2 = lg2_approx(d2min);
+          const float lsc2 = lg2_approx(scale);
           float ax = 0.f, ay = 0.f, al = 0.f;
 #pragma unroll
           for (int rr = 0; rr < 5; ++rr)
@@ -829,29 +886,42 @@ __global__ void __launch_bounds__(kLocalThreads)
               const float dx = __fsub_rn(qx, v.x), dy = __fsub_rn(qy, v.y);
               const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
               if (!(d2 < r2f)) continue;
-              const float w = grad_weight<MODE>(d2, d2min, lmin, hp);
-              const float a = (v.z - Z) * w, ar = a * rcp_approx(d2);
+              float w, ar, lt;
+              if (kMod) {
+                const float id = rsqrt_approx(d2);
+                const float tb = fmaxf(id - inv_r, 0.f);
+                if (!(tb > 0.f)) continue;
+                w = modified_ratio<MODE>(tb, scale, lsc, pf);
+                ar = (v.z - Z) * w * (id * id) * (id * rcp_approx(tb));  // / (t d^3)
+                lt = lg2_approx(tb) - lsc2;
+              } else {
+                w = grad_weight<MODE>(d2, scale, lsc, hp);
+                ar = (v.z - Z) * w * rcp_approx(d2);  // / d^2
+                lt = lg2_approx(d2) - lsc2;
+              }
               ax = fmaf(ar, dx, ax);
               ay = fmaf(ar, dy, ay);
-              al = fmaf(a, lg2_approx(d2) - lmin2, al);
+              al = fmaf((v.z - Z) * w, lt, al);
             }
           const float c = gj / s0, k1 = c * pf;
           gqx = -k1 * ax;
           gqy = -k1 * ay;
-          const float gpf = (-0.5f * 0.6931471805599453f) * c * al;  // FP32: no FP64 divide
+          // dL/dp share in FP32 (no FP64 divide): -ln2/2 c al for d^-p,
+          // +ln2 c al for the modified weights (dw/dp = w ln t).
+          const float gpf = (kMod ? 0.6931471805599453f : -0.5f * 0.6931471805599453f) * c * al;
           gp = gpf;
           out.code = kGradF32;
           out.c = c;
           out.z = Z;
-          out.d2min = d2min;
+          out.d2min = scale;
           f32 = isfinite(Z) && isfinite(gqx) && isfinite(gqy) && isfinite(gpf) && isfinite(c);
         }
-        if (!f32) {  // FP64: weights scaled by the exact d2_min^(p/2)
-          const GradF64 r64 = grad_query_f64(runs, sorted, qx, qy, r2f, p, gj);
+        if (!f32) {  // FP64: weights scaled by the exact scale
+          const GradF64 r64 = grad_query_f64(runs, sorted, qx, qy, r2f, p, gj, kMod, radius);
           gqx = r64.gqx;
           gqy = r64.gqy;
           gp = r64.gp;
-          out.code = kGradF64;
+          out.code = r64.rec.c == 0.0 && r64.rec.d2min == 0.0 ? kGradHitNone : kGradF64;
           rec64[t] = r64.rec;
         }
       }
@@ -870,17 +940,26 @@ __global__ void __launch_bounds__(kLocalThreads)
 
 // The FP64 path's share of one (point, query) pair: (dL/dz, dL/dx, dL/dy).
 // Out of line, so that the rare FP64 branch adds no registers to the loop.
-__device__ __noinline__ float3 grad_pair_f64(LocalGradRec64 D, float qx, float qy, float4 v,
-                                             double p) {
+// One instance per weight mode, so the plain one passes no radius.
+__device__ __forceinline__ float3 grad_pair_f64_terms(LocalGradRec64 D, float qx, float qy,
+                                                      float4 v, double p, bool modified,
+                                                      double radius) {
   const double ex = double(qx) - v.x, ey = double(qy) - v.y;
-  const double e2 = ex * ex + ey * ey;
-  const double w = pow(D.d2min / e2, 0.5 * p);
-  const double a = D.c * p * (double(v.z) - D.z) * w / e2;
-  return make_float3(static_cast<float>(D.c * w), static_cast<float>(a * ex),
+  const GradTerms64 g = grad_terms64(ex * ex + ey * ey, D.d2min, p, modified, radius);
+  const double a = D.c * p * (double(v.z) - D.z) * g.f;
+  return make_float3(static_cast<float>(D.c * g.w), static_cast<float>(a * ex),
                      static_cast<float>(a * ey));
 }
+__device__ __noinline__ float3 grad_pair_f64(LocalGradRec64 D, float qx, float qy, float4 v,
+                                             double p) {
+  return grad_pair_f64_terms(D, qx, qy, v, p, false, 0.0);
+}
+__device__ __noinline__ float3 grad_pair_f64_modified(LocalGradRec64 D, float qx, float qy,
+                                                      float4 v, double p, double radius) {
+  return grad_pair_f64_terms(D, qx, qy, v, p, true, radius);
+}
 
-template <int MODE>
+template <int MODE, int WMODE = kWeightShepard>
 __global__ void __launch_bounds__(kLocalThreads)
     local_grad_data_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
                            int64_t n, const int32_t* __restrict__ starts_d,
@@ -889,7 +968,9 @@ __global__ void __launch_bounds__(kLocalThreads)
                            const int32_t* __restrict__ base_q, const float4* __restrict__ qrec,
                            int64_t m, const LocalGradRec* __restrict__ rec,
                            const LocalGradRec64* __restrict__ rec64, double p, float r2f,
-                           float* __restrict__ grad_z, float* __restrict__ grad_xy) {
+                           float* __restrict__ grad_z, float* __restrict__ grad_xy,
+                           double radius) {
+  constexpr bool kMod = WMODE == kWeightModified;
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const GridDev g = *grid;
   if (k >= cell_start(starts_d, base_d, g.cells, g.cells)) return;  // placed (finite) points
@@ -899,6 +980,7 @@ __global__ void __launch_bounds__(kLocalThreads)
   if (!dcheck(idx >= 0 && idx < n, kSiteData)) return;
   const Runs runs(g, v.x, v.y, starts_q, base_q);
   const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+  const float inv_r = kMod ? static_cast<float>(1.0 / radius) : 0.f;
   float gz = 0.f, gx = 0.f, gy = 0.f;
 #pragma unroll
   for (int rr = 0; rr < 5; ++rr)
@@ -916,14 +998,25 @@ __global__ void __launch_bounds__(kLocalThreads)
       const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
       if (!(d2 < r2f)) continue;  // the query's membership test, bit for bit
       if (R.code == kGradF32) {
-        const float lmin = MODE == kPow2 ? 0.f : lg2_approx(R.d2min);
-        const float w = grad_weight<MODE>(d2, R.d2min, lmin, hp);
+        const float lsc = MODE == kPow2 ? 0.f : lg2_approx(R.d2min);
+        float w, fac;
+        if (kMod) {  // the scale is the query's largest base t
+          const float id = rsqrt_approx(d2);
+          const float tb = fmaxf(id - inv_r, 0.f);
+          if (!(tb > 0.f)) continue;
+          w = modified_ratio<MODE>(tb, R.d2min, lsc, pf);
+          fac = (id * id) * (id * rcp_approx(tb));  // 1 / (t d^3)
+        } else {
+          w = grad_weight<MODE>(d2, R.d2min, lsc, hp);
+          fac = rcp_approx(d2);  // 1 / d^2
+        }
         gz = fmaf(R.c, w, gz);
-        const float a = R.c * pf * (v.z - R.z) * w * rcp_approx(d2);
+        const float a = R.c * pf * (v.z - R.z) * w * fac;
         gx = fmaf(a, dx, gx);
         gy = fmaf(a, dy, gy);
       } else {
-        const float3 f = grad_pair_f64(rec64[t], q.x, q.y, v, p);
+        const float3 f = kMod ? grad_pair_f64_modified(rec64[t], q.x, q.y, v, p, radius)
+                              : grad_pair_f64(rec64[t], q.x, q.y, v, p);
         gz += f.x;
         gx += f.y;
         gy += f.z;
@@ -1546,7 +1639,8 @@ size_t local_grad_record_bytes(int64_t m) {
 cudaError_t launch_local_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                   double p, double radius, const float* grad_out, float* grad_z,
                                   float* grad_xy, float* grad_q, double* grad_p, void* workspace,
-                                  const LocalLayout& L, int sm_count, cudaStream_t s) {
+                                  const LocalLayout& L, int sm_count, cudaStream_t s,
+                                  bool modified) {
   cudaError_t e = launch_grid_sort(data, n, queries, m, radius, 0, workspace, L, sm_count, s);
   if (e != cudaSuccess) return e;
   if (grad_z && (e = cudaMemsetAsync(grad_z, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
@@ -1568,22 +1662,24 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
   const unsigned dgrid = static_cast<unsigned>((n + kLocalThreads - 1) / kLocalThreads);
   const bool data_side = grad_z || grad_xy;
-  if (p == 2.0) {
-    local_grad_query_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(
+  auto run = [&](auto mode, auto wmode) {
+    constexpr int M = decltype(mode)::value, W = decltype(wmode)::value;
+    local_grad_query_kernel<M, W><<<qgrid, kLocalThreads, 0, s>>>(
         grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec,
-        rec64);
+        rec64, radius);
     if (data_side)
-      local_grad_data_kernel<kPow2><<<dgrid, kLocalThreads, 0, s>>>(
+      local_grad_data_kernel<M, W><<<dgrid, kLocalThreads, 0, s>>>(
           grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, rec64, p, r2f, grad_z,
-          grad_xy);
+          grad_xy, radius);
+  };
+  using P2 = std::integral_constant<int, kPow2>;
+  using PG = std::integral_constant<int, kPowGeneral>;
+  using WS = std::integral_constant<int, kWeightShepard>;
+  using WM = std::integral_constant<int, kWeightModified>;
+  if (modified) {
+    if (p == 2.0) run(P2{}, WM{}); else run(PG{}, WM{});
   } else {
-    local_grad_query_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(
-        grid, sorted, n, starts_d, sums, qrec, m, p, r2f, r2t, grad_out, grad_q, grad_p, rec,
-        rec64);
-    if (data_side)
-      local_grad_data_kernel<kPowGeneral><<<dgrid, kLocalThreads, 0, s>>>(
-          grid, sorted, n, starts_d, sums, starts_q, sums_q, qrec, m, rec, rec64, p, r2f, grad_z,
-          grad_xy);
+    if (p == 2.0) run(P2{}, WS{}); else run(PG{}, WS{});
   }
   return cudaGetLastError();
 }

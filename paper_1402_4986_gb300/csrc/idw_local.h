@@ -31,15 +31,16 @@ cudaError_t launch_local(const float* data, int64_t n, const float* queries, int
                          const LocalLayout& L, int sm_count, cudaStream_t s,
                          bool sort_queries = true, bool modified = false);
 
-// Gradients of L = sum_j grad_out[j] Z(q_j) for the radius form (membership
-// sets held fixed): the grid build, then one kernel per query and one per
-// data point.  The workspace holds L.bytes plus local_grad_record_bytes(m).
+// Gradients of L = sum_j grad_out[j] Z(q_j) for the radius form, or with
+// modified = true for modified Shepard (membership sets held fixed): the
+// grid build, then one kernel per query and one per data point.  The workspace holds L.bytes plus local_grad_record_bytes(m).
 // grad_z (n), grad_xy (n x 2), grad_q (m x 2) and grad_p (1) may be null.
 size_t local_grad_record_bytes(int64_t m);
 cudaError_t launch_local_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                   double p, double radius, const float* grad_out, float* grad_z,
                                   float* grad_xy, float* grad_q, double* grad_p, void* workspace,
-                                  const LocalLayout& L, int sm_count, cudaStream_t s);
+                                  const LocalLayout& L, int sm_count, cudaStream_t s,
+                                  bool modified = false);
 
 // Index-check failures of a debug build (bit s = check site s failed since
 // the last call; cleared by the call), on the current device.  *enabled is

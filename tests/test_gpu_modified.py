@@ -119,3 +119,74 @@ def test_prepared_index(idw):
         assert np.array_equal(np.isnan(Zc), ~ok)
         assert np.max(np.abs(Zc[ok] - Z64[ok])) / np.max(np.abs(data[:, 2])) <= TOL
 
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / scale) if scale > 0 else float(np.max(np.abs(a)))
+
+
+def _grad_compare(idw, data, q, p, radius, g, tol=1e-4):
+    gz, gxy, gq, gp = idw.local_backward(_dev(data), _dev(q), p, radius, _dev(g), modified=True)
+    torch.cuda.synchronize()
+    G = oracle.idw_modified_grad(data, q, p, radius, g)
+    errs = {"z": _rel(gz.cpu().numpy(), G["grad_z"]), "xy": _rel(gxy.cpu().numpy(), G["grad_xy"]),
+            "q": _rel(gq.cpu().numpy(), G["grad_q"]),
+            "p": abs(float(gp.cpu()[0]) - G["grad_p"]) / max(abs(G["grad_p"]), 1e-300)}
+    for key, e in errs.items():
+        assert e <= tol, (key, errs)
+
+
+@pytest.mark.parametrize("p", [2.0, 3.5, 1.5])
+def test_gradients_match_the_oracle(idw, p):
+    """All four gradients of modified Shepard, within 1e-4 of each one's
+    largest magnitude, with exact hits among the queries."""
+    prob = synthetic.config_local(n=5003, m=3001, members=40.0, seed=168)
+    data, q = prob["data"], prob["queries"].copy()
+    q[::500] = data[:7 * 500:500, :2][: q[::500].shape[0]]
+    g = np.random.default_rng(169).standard_normal(q.shape[0]).astype(np.float32)
+    _grad_compare(idw, data, q, p, prob["radius"], g)
+
+
+def test_gradients_clustered_and_fp64_path(idw):
+    prob = synthetic.config_local(n=20000, m=3000, members=16.0, clustered=True, seed=170)
+    g = np.random.default_rng(171).standard_normal(3000).astype(np.float32)
+    _grad_compare(idw, prob["data"], prob["queries"], 2.0, prob["radius"], g)
+    rng = np.random.default_rng(172)
+    xy = (rng.random((400, 2)) * 3e-19).astype(np.float32)
+    data = np.concatenate([xy, rng.standard_normal((400, 1)).astype(np.float32)], 1)
+    q = (rng.random((150, 2)) * 3e-19).astype(np.float32)
+    _grad_compare(idw, data, q, 2.5, 1e-19, rng.standard_normal(150).astype(np.float32))
+
+
+def test_gradients_at_infinite_radius_are_the_global_adjoint(idw):
+    prob = synthetic.uniform_problem(2000, 700, seed=173)
+    g = np.random.default_rng(174).standard_normal(700).astype(np.float32)
+    gz, gxy, gq, gp = idw.local_backward(_dev(prob["data"]), _dev(prob["queries"]), 2.5,
+                                         float("inf"), _dev(g), modified=True)
+    G = oracle.idw_grad(prob["data"], prob["queries"], 2.5, g)
+    assert _rel(gz.cpu().numpy(), G["grad_z"]) <= 1e-4
+    assert _rel(gxy.cpu().numpy(), G["grad_xy"]) <= 1e-4
+    assert _rel(gq.cpu().numpy(), G["grad_q"]) <= 1e-4
+    assert abs(float(gp.cpu()[0]) - G["grad_p"]) <= 1e-4 * abs(G["grad_p"])
+
+
+def test_autograd_function(idw):
+    prob = synthetic.config_local(n=4000, m=1500, members=25.0, seed=175)
+    data, q, R = prob["data"], prob["queries"], prob["radius"]
+    d = _dev(data).requires_grad_(True)
+    qq = _dev(q).requires_grad_(True)
+    p = torch.tensor(2.5, device="cuda", requires_grad=True)
+    Z = idw.idw_modified(d, qq, p, R)
+    w = torch.from_numpy(np.random.default_rng(176).standard_normal(1500).astype(np.float32)).cuda()
+    ok = torch.isfinite(Z)
+    (Z[ok] * w[ok]).sum().backward()
+    g = np.where(ok.cpu().numpy(), w.cpu().numpy(), 0).astype(np.float32)
+    G = oracle.idw_modified_grad(data, q, 2.5, R, g)
+    gd = d.grad.cpu().numpy().astype(np.float64)
+    assert _rel(gd[:, 2], G["grad_z"]) <= 1e-4
+    assert _rel(gd[:, :2], G["grad_xy"]) <= 1e-4
+    assert _rel(qq.grad.cpu().numpy(), G["grad_q"]) <= 1e-4
+    assert abs(float(p.grad) - G["grad_p"]) <= 1e-4 * abs(G["grad_p"])
