@@ -16,7 +16,7 @@
  * repeated queries (idw_local_index_*), and modified Shepard weights on the
  * radius form (idw_interpolate_modified).  Every form has gradients with
  * respect to z, the data and query coordinates, and p (idw_backward,
- * idw_local_backward, idw_knn_backward).
+ * idw_local_backward, idw_modified_backward, idw_knn_backward).
  *
  * Conventions shared by every entry point:
  *   - A data point is a row (x, y, z): d is the 2-D Euclidean distance in
