@@ -822,7 +822,10 @@ __global__ void __launch_bounds__(kLocalThreads)
       const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
       const float inv_r = kMod ? static_cast<float>(1.0 / radius) : 0.f;
       int best = INT_MAX, members = 0;
-      float d2min = INFINITY, scale = kMod ? 0.f : INFINITY, lsc = 0.f, s0 = 0.f, s1 = 0.f;
+      float d2min = INFINITY, scale = kMod ? 0.f : INFINITY, lsc = 0.f;
+      // (sum w, sum w z) as a compensated pair, as in the forward pass: Z
+      // and g / S0 then stay accurate however many members a query has.
+      u64 hi = 0, lo = 0;
 #pragma unroll
       for (int rr = 0; rr < 5; ++rr)
         for (int k = runs.a[rr]; k < runs.b[rr]; ++k) {
@@ -845,8 +848,8 @@ __global__ void __launch_bounds__(kLocalThreads)
               const float l = MODE == kPow2 ? 0.f : lg2_approx(tb);
               if (scale > 0.f) {
                 const float f = modified_ratio<MODE>(scale, tb, l, pf);  // (t_old / t)^p
-                s0 *= f;
-                s1 *= f;
+                hi = mul2(hi, pk(f, f));
+                lo = mul2(lo, pk(f, f));
               }
               scale = tb;
               lsc = l;
@@ -857,17 +860,20 @@ __global__ void __launch_bounds__(kLocalThreads)
               const float l = MODE == kPow2 ? 0.f : lg2_approx(d2);
               if (members > 1) {
                 const float f = grad_weight<MODE>(scale, d2, l, hp);  // (d2 / d2min_old)^(p/2)
-                s0 *= f;
-                s1 *= f;
+                hi = mul2(hi, pk(f, f));
+                lo = mul2(lo, pk(f, f));
               }
               scale = d2;
               lsc = l;
             }
             w = grad_weight<MODE>(d2, scale, lsc, hp);
           }
-          s0 += w;
-          s1 = fmaf(w, v.z, s1);
+          two_sum_acc(hi, lo, pk(w, __fmul_rn(w, v.z)));
         }
+      float h0, h1, l0, l1;
+      upk(hi, h0, h1);
+      upk(lo, l0, l1);
+      const float s0 = h0 + l0;
       LocalGradRec out{0.f, 0.f, 0.f, kGradHitNone};
       float gqx = 0.f, gqy = 0.f;
       if (best != INT_MAX) {
@@ -876,7 +882,10 @@ __global__ void __launch_bounds__(kLocalThreads)
       } else if (members > 0 && (!kMod || scale > 0.f)) {
         bool f32 = d2min >= 0x1p-100f;
         if (f32) {
-          const float Z = s1 / s0;
+          // Z = (h1 + l1) / (h0 + l0): quotient, then one residual correction.
+          const float z0 = __fdiv_rn(h1, h0);
+          const float Z = __fmaf_rn(__fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1)),
+                                    rcp_approx(h0), z0);
           const float lsc2 = lg2_approx(scale);
           float ax = 0.f, ay = 0.f, al = 0.f;
 #pragma unroll
