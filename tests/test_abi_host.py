@@ -64,6 +64,12 @@ def test_null_handle_is_rejected(lib):
     assert lib.idw_local_index_interpolate(None, None, None, 10, 2.0, 0.1, None, None, None) == 1
     assert lib.idw_local_index_knn(None, None, None, 10, 2.0, 4, None, None, None, None) == 1
     assert lib.idw_local_index_destroy(None) == 1
+    assert lib.idw_local_index_modified(None, None, None, 10, 2.0, 0.1, None, None, None) == 1
+    assert lib.idw_interpolate_modified(None, None, 10, None, 10, 2.0, 0.1, None, None, None) == 1
+    for fn in (lib.idw_local_backward, lib.idw_modified_backward):
+        assert fn(None, None, 10, None, 10, 2.0, 0.1, None, None, None, None, None, None) == 1
+    assert lib.idw_knn_backward(None, None, 10, None, 10, 2.0, 4, None, None, None, None, None,
+                                None) == 1
     out = ctypes.c_void_p()
     assert lib.idw_create(None, 0) == 1
 
@@ -159,3 +165,9 @@ def test_binding_rejects_host_tensors_for_device_entry():
         idw.LocalIndex(d, radius=0.1)
     with pytest.raises(ValueError):
         idw.LocalIndex(d, radius=0.1, k=4)
+    with pytest.raises(ValueError):
+        idw.interpolate_modified(d, q, 2.0, 0.1)
+    with pytest.raises(ValueError):
+        idw.local_backward(d, q, 2.0, 0.1, torch.ones(2))
+    with pytest.raises(ValueError):
+        idw.knn_backward(d, q, 2.0, 4, torch.ones(2))
