@@ -125,6 +125,7 @@ PINS = [
     pins.test_modified_with_infinite_radius_is_the_global_form,
     pins.test_modified_is_continuous_at_the_radius,
     pins.test_modified_members_and_hits_are_the_radius_form_s,
+    lambda: pins.test_modified_mpmath_general_p(2.5),
     lambda: pins.test_modified_gradient_matches_central_differences(3.0),
     pins.test_modified_gradient_at_infinite_radius_is_the_global_gradient,
     pins.test_modified_gradient_sums_translation_and_hits,

@@ -855,3 +855,34 @@ def test_modified_gradient_sums_translation_and_hits():
     assert hit[5] >= 0 and np.all(M["grad_q"][5] == 0)
     assert abs(M["grad_z"].sum() - np.isfinite(Zm).sum()) <= 1e-10
     assert np.abs(M["grad_xy"].sum(0) + M["grad_q"].sum(0)).max() <= 1e-9 * np.abs(M["grad_q"]).max()
+
+
+@pytest.mark.parametrize("p", [1.5, 2.5, 3.7])
+def test_modified_mpmath_general_p(p):
+    """Modified Shepard at general p against 50-digit evaluation of its
+    definition over the oracle's own FP32 membership sets."""
+    data, q = _tiny(11, 21, 13)
+    R = 0.45
+    Z, hit, cnt = oracle.idw_modified(data, q, p, R)
+    _, _, cl = oracle.idw_local(data, q, p, R)
+    assert np.array_equal(cnt, cl)
+    mpmath.mp.dps = 50
+    r2f = np.float32(R * R)
+    for j, (qx, qy) in enumerate(q):
+        s0 = mpmath.mpf(0)
+        s1 = mpmath.mpf(0)
+        for x, y, z in data:
+            if not _fp32_key(qx, qy, x, y) < r2f:
+                continue  # the radius form's FP32 membership test, emulated exactly
+            d = mpmath.sqrt((mpmath.mpf(float(qx)) - float(x)) ** 2 +
+                            (mpmath.mpf(float(qy)) - float(y)) ** 2)
+            t = 1 / d - 1 / mpmath.mpf(R)
+            w = t ** mpmath.mpf(p) if t > 0 else mpmath.mpf(0)
+            s0 += w
+            s1 += w * float(z)
+        assert hit[j] == -1
+        if s0 == 0:
+            assert np.isnan(Z[j])
+            continue
+        ref = float(s1 / s0)
+        assert abs(Z[j] - ref) <= 1e-14 * np.abs(data[:, 2]).max(), (p, j, Z[j], ref)
