@@ -107,6 +107,41 @@ def _check_inputs(data, queries, prec):
         raise ValueError("data and queries must be on the same device")
 
 
+def _check_buf(t, numel, dtype, device, name):
+    """A caller-supplied output or saved-state tensor: the library writes or
+    reads exactly ``numel`` contiguous ``dtype`` values at its address on
+    ``device``, so each of those must hold before the call."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a tensor, got {type(t).__name__}")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} values, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _handle_for(handle, device):
+    """``handle`` (or the device's process-wide one), checked to own ``device``."""
+    if handle is None:
+        return get_handle(device)
+    if device.type != "cuda" or handle.device != (device.index or 0):
+        raise ValueError(f"the handle belongs to cuda:{handle.device}, the tensors to {device}")
+    return handle
+
+
+def _grad_vec(grad_out, m, device):
+    """The upstream gradient as contiguous float32[m] on ``device``."""
+    if not isinstance(grad_out, torch.Tensor) or grad_out.device != device:
+        raise ValueError(f"grad_out must be a tensor on {device}")
+    if grad_out.numel() != m:
+        raise ValueError(f"grad_out must hold {m} values, got {grad_out.numel()}")
+    return grad_out.reshape(m).contiguous().to(torch.float32)
+
+
 def interpolate_saved(data: torch.Tensor, queries: torch.Tensor, p: float = 2.0,
                       precision="f32c", out=None, handle: Handle | None = None):
     """Eq. 1 plus the state the adjoint needs.
@@ -118,9 +153,10 @@ def interpolate_saved(data: torch.Tensor, queries: torch.Tensor, p: float = 2.0,
     prec = _prec(precision)
     _check_inputs(data, queries, prec)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    _check_buf(out, m, _DTYPE[prec], data.device, "out")
     s0 = torch.empty(m, dtype=torch.float64, device=data.device)
     hit = torch.empty(m, dtype=torch.int32, device=data.device)
     st = h.lib.idw_interpolate_saved(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m,
@@ -140,9 +176,10 @@ def interpolate(data: torch.Tensor, queries: torch.Tensor, p: float = 2.0, preci
     prec = _prec(precision)
     _check_inputs(data, queries, prec)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    _check_buf(out, m, _DTYPE[prec], data.device, "out")
     st = h.lib.idw_interpolate(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p), prec,
                                _ptr(out), _stream(data))
     _lib.check(st, "idw_interpolate", h.ptr)
@@ -159,7 +196,13 @@ def interpolate_host(data, queries, p: float = 2.0, precision="f32c", out=None,
     if data.dtype != dt or queries.dtype != dt or not data.is_contiguous() or \
             not queries.is_contiguous():
         raise ValueError(f"host inputs must be contiguous {dt}")
+    if data.dim() != 2 or data.shape[1] != 3:
+        raise ValueError(f"data must be (n, 3) rows (x, y, z), got {tuple(data.shape)}")
+    if queries.dim() != 2 or queries.shape[1] != 2:
+        raise ValueError(f"queries must be (m, 2) rows (x, y), got {tuple(queries.shape)}")
     m = queries.shape[0]
+    if out is not None:
+        _check_buf(out, m, dt, torch.device("cpu"), "out")
     h = handle or get_handle()
     if out is None:
         out = torch.empty(m, dtype=dt, pin_memory=True)
@@ -180,11 +223,18 @@ def interpolate_batched(datas, queries_list, p: float = 2.0, outs=None,
         raise ValueError("datas and queries_list differ in length")
     if k == 0:
         return []
+    dev = datas[0].device
     for d, q in zip(datas, queries_list):
         _check_inputs(d, q, prec)
+        if d.device != dev:
+            raise ValueError(f"every problem must be on {dev}, got {d.device}")
     if outs is None:
-        outs = [torch.empty(q.shape[0], dtype=_DTYPE[prec], device=q.device) for q in queries_list]
-    h = handle or get_handle(datas[0].device)
+        outs = [torch.empty(q.shape[0], dtype=_DTYPE[prec], device=dev) for q in queries_list]
+    if len(outs) != k:
+        raise ValueError(f"outs must hold {k} tensors, got {len(outs)}")
+    for i, (o, q) in enumerate(zip(outs, queries_list)):
+        _check_buf(o, q.shape[0], _DTYPE[prec], dev, f"outs[{i}]")
+    h = _handle_for(handle, dev)
     P = ctypes.c_void_p * k
     I = ctypes.c_int64 * k
     st = h.lib.idw_interpolate_batched(
@@ -205,9 +255,10 @@ def paper_interpolate(data, queries, p: float = 2.0, kernel: str = "tiled", layo
     prec = _prec(precision)
     _check_inputs(data, queries, prec)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=_DTYPE[prec], device=data.device)
+    _check_buf(out, m, _DTYPE[prec], data.device, "out")
     st = h.lib.idw_paper_interpolate(h.ptr, _lib.PAPER_KERNELS[kernel], _lib.PAPER_LAYOUTS[layout],
                                      _ptr(data), data.shape[0], _ptr(queries), m, float(p), prec,
                                      _ptr(out), _stream(data))
@@ -226,9 +277,10 @@ def interpolate_local(data, queries, p: float = 2.0, radius: float = float("inf"
     """
     _check_inputs(data, queries, PREC_F32_COMP)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=torch.float32, device=data.device)
+    _check_buf(out, m, torch.float32, data.device, "out")
     cnt = torch.empty(m, dtype=torch.int32, device=data.device) if counts else None
     st = h.lib.idw_interpolate_local(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p),
                                      float(radius), _ptr(out), _ptr(cnt),
@@ -244,9 +296,10 @@ def interpolate_modified(data, queries, p: float = 2.0, radius: float = float("i
     as ``interpolate_local``."""
     _check_inputs(data, queries, PREC_F32_COMP)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=torch.float32, device=data.device)
+    _check_buf(out, m, torch.float32, data.device, "out")
     cnt = torch.empty(m, dtype=torch.int32, device=data.device) if counts else None
     st = h.lib.idw_interpolate_modified(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m,
                                         float(p), float(radius), _ptr(out), _ptr(cnt),
@@ -266,9 +319,10 @@ def interpolate_knn(data, queries, p: float = 2.0, k: int = 16, out=None,
     """
     _check_inputs(data, queries, PREC_F32_COMP)
     m = queries.shape[0]
-    h = handle or get_handle(data.device)
+    h = _handle_for(handle, data.device)
     if out is None:
         out = torch.empty(m, dtype=torch.float32, device=data.device)
+    _check_buf(out, m, torch.float32, data.device, "out")
     nbr = torch.empty(m, int(k), dtype=torch.int32, device=data.device) if neighbours else None
     kd2 = torch.empty(m, dtype=torch.float32, device=data.device) if kth_d2 else None
     st = h.lib.idw_interpolate_knn(h.ptr, _ptr(data), data.shape[0], _ptr(queries), m, float(p),
@@ -325,10 +379,11 @@ class LocalIndex:
         Shepard weights (``interpolate_modified``).  ``handle`` (default: the
         build's) supplies the workspace: one handle per concurrent stream."""
         m = self._queries(queries)
-        h = handle or self.handle
+        h = self.handle if handle is None else _handle_for(handle, self.device)
         r = self.radius if radius is None else float(radius)
         if out is None:
             out = torch.empty(m, dtype=torch.float32, device=self.device)
+        _check_buf(out, m, torch.float32, self.device, "out")
         cnt = torch.empty(m, dtype=torch.int32, device=self.device) if counts else None
         fn = h.lib.idw_local_index_modified if modified else h.lib.idw_local_index_interpolate
         st = fn(h.ptr, self.ptr, _ptr(queries), m, float(p), 0.0 if r is None else r,
@@ -342,10 +397,11 @@ class LocalIndex:
         """``interpolate_knn`` on the indexed data (k defaults to the build k;
         ``handle`` as in ``interpolate``)."""
         m = self._queries(queries)
-        h = handle or self.handle
+        h = self.handle if handle is None else _handle_for(handle, self.device)
         kk = int(k) if k is not None else (self.k or 0)  # 0: refused by the library
         if out is None:
             out = torch.empty(m, dtype=torch.float32, device=self.device)
+        _check_buf(out, m, torch.float32, self.device, "out")
         nbr = torch.empty(m, max(kk, 1), dtype=torch.int32, device=self.device) if neighbours else None
         kd2 = torch.empty(m, dtype=torch.float32, device=self.device) if kth_d2 else None
         st = h.lib.idw_local_index_knn(
@@ -377,8 +433,11 @@ def backward(data, queries, p, Z, s0, hit, grad_out, need_z=True, need_data_xy=T
     gxy = torch.empty(n, 2, dtype=torch.float32, device=dev) if need_data_xy else None
     gq = torch.empty(m, 2, dtype=torch.float32, device=dev) if need_query_xy else None
     gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
-    h = handle or get_handle(dev)
-    g = grad_out.contiguous().to(torch.float32)
+    h = _handle_for(handle, dev)
+    _check_buf(Z, m, torch.float32, dev, "Z")
+    _check_buf(s0, m, torch.float64, dev, "s0")
+    _check_buf(hit, m, torch.int32, dev, "hit")
+    g = _grad_vec(grad_out, m, dev)
     st = h.lib.idw_backward(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), _ptr(Z), _ptr(s0),
                             _ptr(hit), _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp),
                             _stream(data))
@@ -429,8 +488,8 @@ def local_backward(data, queries, p, radius, grad_out, need_z=True, need_data_xy
     gxy = torch.empty(n, 2, dtype=torch.float32, device=dev) if need_data_xy else None
     gq = torch.empty(m, 2, dtype=torch.float32, device=dev) if need_query_xy else None
     gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
-    h = handle or get_handle(dev)
-    g = grad_out.contiguous().to(torch.float32)
+    h = _handle_for(handle, dev)
+    g = _grad_vec(grad_out, m, dev)
     name = "idw_modified_backward" if modified else "idw_local_backward"
     st = getattr(h.lib, name)(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), float(radius),
                               _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), _stream(data))
@@ -489,8 +548,8 @@ def knn_backward(data, queries, p, k, grad_out, need_z=True, need_data_xy=True,
     gxy = torch.empty(n, 2, dtype=torch.float32, device=dev) if need_data_xy else None
     gq = torch.empty(m, 2, dtype=torch.float32, device=dev) if need_query_xy else None
     gp = torch.empty(1, dtype=torch.float64, device=dev) if need_p else None
-    h = handle or get_handle(dev)
-    g = grad_out.contiguous().to(torch.float32)
+    h = _handle_for(handle, dev)
+    g = _grad_vec(grad_out, m, dev)
     st = h.lib.idw_knn_backward(h.ptr, _ptr(data), n, _ptr(queries), m, float(p), int(k),
                                 _ptr(g), _ptr(gz), _ptr(gxy), _ptr(gq), _ptr(gp), _stream(data))
     _lib.check(st, "idw_knn_backward", h.ptr)

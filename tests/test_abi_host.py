@@ -171,3 +171,77 @@ def test_binding_rejects_host_tensors_for_device_entry():
         idw.local_backward(d, q, 2.0, 0.1, torch.ones(2))
     with pytest.raises(ValueError):
         idw.knn_backward(d, q, 2.0, 4, torch.ones(2))
+
+
+# ------------------------------------------------- binding refusals (no GPU)
+# The binding checks every caller-supplied buffer before it calls into the
+# library, so a wrong size, dtype, device or layout raises ValueError instead
+# of becoming an out-of-bounds device write or host read.
+
+def _torch():
+    return pytest.importorskip("torch")
+
+
+def test_out_buffer_refusals():
+    torch = _torch()
+    import paper_1402_4986_gb300 as idw
+    cpu = torch.device("cpu")
+    ok = torch.empty(5)
+    assert idw._check_buf(ok, 5, torch.float32, cpu, "out") is ok
+    with pytest.raises(ValueError, match="hold 5 values"):
+        idw._check_buf(torch.empty(4), 5, torch.float32, cpu, "out")        # too short
+    with pytest.raises(ValueError, match="hold 5 values"):
+        idw._check_buf(torch.empty(6), 5, torch.float32, cpu, "out")        # too long
+    with pytest.raises(ValueError, match="float32"):
+        idw._check_buf(torch.empty(5, dtype=torch.float64), 5, torch.float32, cpu, "out")
+    with pytest.raises(ValueError, match="contiguous"):
+        idw._check_buf(torch.empty(5, 2)[:, 0], 5, torch.float32, cpu, "out")
+    with pytest.raises(ValueError, match="must be on cuda:0"):
+        idw._check_buf(ok, 5, torch.float32, torch.device("cuda", 0), "out")  # wrong device
+    with pytest.raises(ValueError, match="must be a tensor"):
+        idw._check_buf([0.0] * 5, 5, torch.float32, cpu, "out")
+
+
+def test_handle_device_refusal():
+    torch = _torch()
+    import paper_1402_4986_gb300 as idw
+
+    class FakeHandle:
+        device = 1
+    h = FakeHandle()
+    assert idw._handle_for(h, torch.device("cuda", 1)) is h
+    with pytest.raises(ValueError, match="belongs to cuda:1"):
+        idw._handle_for(h, torch.device("cuda", 0))
+    with pytest.raises(ValueError, match="belongs to cuda:1"):
+        idw._handle_for(h, torch.device("cpu"))
+
+
+def test_upstream_gradient_refusals():
+    torch = _torch()
+    import paper_1402_4986_gb300 as idw
+    cpu = torch.device("cpu")
+    g = idw._grad_vec(torch.ones(3, 1, dtype=torch.float64), 3, cpu)
+    assert g.dtype == torch.float32 and g.shape == (3,) and g.is_contiguous()
+    with pytest.raises(ValueError, match="hold 3 values"):
+        idw._grad_vec(torch.ones(2), 3, cpu)
+    with pytest.raises(ValueError, match="tensor on cuda:0"):
+        idw._grad_vec(torch.ones(3), 3, torch.device("cuda", 0))
+
+
+def test_host_entry_point_shape_refusals():
+    """interpolate_host reads n x 3 and m x 2 host values and writes m: a
+    (n, 2) data array or a short out would be read or written out of bounds."""
+    torch = _torch()
+    import paper_1402_4986_gb300 as idw
+    d = torch.zeros(8, 3)
+    q = torch.zeros(5, 2)
+    with pytest.raises(ValueError, match=r"data must be \(n, 3\)"):
+        idw.interpolate_host(torch.zeros(8, 2), q)
+    with pytest.raises(ValueError, match=r"queries must be \(m, 2\)"):
+        idw.interpolate_host(d, torch.zeros(5, 3))
+    with pytest.raises(ValueError, match="hold 5 values"):
+        idw.interpolate_host(d, q, out=torch.empty(4))
+    with pytest.raises(ValueError, match="float32"):
+        idw.interpolate_host(d, q, out=torch.empty(5, dtype=torch.float64))
+    with pytest.raises(ValueError, match="contiguous"):
+        idw.interpolate_host(torch.zeros(3, 8).t(), q)

@@ -155,3 +155,62 @@ def test_misaligned_pointers_are_refused(idw):
                                    P(ok32), P(s)) == 2
     torch.cuda.synchronize()
     assert torch.count_nonzero(buf) == 0  # nothing was launched
+
+
+def test_binding_refuses_bad_output_buffers(idw):
+    """Every caller-supplied output or saved-state buffer is checked (size,
+    dtype, device, layout) before the library is called."""
+    d, q = _prob(seed=72, n=500, m=300)
+    m = q.shape[0]
+    short = torch.empty(m - 1, device="cuda")
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate(d, q, 2.0, out=short)
+    with pytest.raises(ValueError, match="float64"):
+        idw.interpolate(d.double(), q.double(), 2.0, "f64", out=torch.empty(m, device="cuda"))
+    with pytest.raises(ValueError, match="must be on"):
+        idw.interpolate(d, q, 2.0, out=torch.empty(m))
+    with pytest.raises(ValueError, match="contiguous"):
+        idw.interpolate(d, q, 2.0, out=torch.empty(m, 2, device="cuda")[:, 0])
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate_saved(d, q, 2.0, out=short)
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate_batched([d, d], [q, q[:10].contiguous()], 2.0,
+                                outs=[torch.empty(m, device="cuda"), torch.empty(9, device="cuda")])
+    with pytest.raises(ValueError, match="outs must hold 2"):
+        idw.interpolate_batched([d, d], [q, q], 2.0, outs=[torch.empty(m, device="cuda")])
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate_local(d, q, 2.0, 0.1, out=short)
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate_modified(d, q, 2.0, 0.1, out=short)
+    with pytest.raises(ValueError, match="hold"):
+        idw.interpolate_knn(d, q, 2.0, 8, out=short)
+    with pytest.raises(ValueError, match="hold"):
+        idw.paper_interpolate(d, q, 2.0, out=short)
+    ix = idw.LocalIndex(d, k=8)
+    with pytest.raises(ValueError, match="hold"):
+        ix.knn(q, 2.0, out=short)
+    ix.close()
+    Z, s0, hit = idw.interpolate_saved(d, q, 2.0)
+    g = torch.ones(m, device="cuda")
+    with pytest.raises(ValueError, match="s0 must be torch.float64"):
+        idw.backward(d, q, 2.0, Z, s0.float(), hit, g)
+    with pytest.raises(ValueError, match="grad_out must hold"):
+        idw.backward(d, q, 2.0, Z, s0, hit, g[:-1])
+    with pytest.raises(ValueError, match="grad_out must be a tensor on"):
+        idw.knn_backward(d, q, 2.0, 8, g.cpu())
+    # Nothing above reached the library: the handle still computes.
+    idw.sync_status()
+    assert torch.isfinite(idw.interpolate(d, q, 2.0)).all()
+
+
+def test_batched_problems_must_share_one_device(idw):
+    if torch.cuda.device_count() < 2:
+        d, q = _prob(seed=73, n=100, m=50)
+        with pytest.raises(ValueError, match="must be on"):
+            idw.interpolate_batched([d, d], [q, q], 2.0,
+                                    outs=[torch.empty(50, device="cuda"), torch.empty(50)])
+        return
+    d0, q0 = _prob(seed=73, n=100, m=50)
+    d1, q1 = d0.to("cuda:1"), q0.to("cuda:1")
+    with pytest.raises(ValueError, match="every problem must be on"):
+        idw.interpolate_batched([d0, d1], [q0, q1], 2.0)
