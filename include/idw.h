@@ -373,18 +373,42 @@ idw_status idw_paper_interpolate(idw_handle_t handle, idw_paper_kernel kernel,
  * rejected with IDW_ERR_WORKSPACE before anything is launched; on a 152-SM
  * GB300, n = m = 262144 fits.
  *
+ * It plans the launch as idw_interpolate does on a handle without tuning
+ * options: the same default sweep variant for the size and weight form.
+ *
  * The first call on a device sets that device up (it looks up the array's
- * device address and clears its control words), so make that first call
- * before any stream capture.  Every call shares the one array and it keeps
- * the last call's contents; each call clears what must start at zero.  Calls
- * whose work overlaps on the GPU (different streams, or concurrent host
- * threads) race on the array: order them on one stream.  Returns
- * IDW_ERR_INVALID_ARG, IDW_ERR_ALIGNMENT, IDW_ERR_UNSUPPORTED (not
- * compute capability 10.3), IDW_ERR_WORKSPACE (too large) or
- * IDW_ERR_CUDA; the kernels run asynchronously after it returns.
+ * device address, clears its control words and waits for the clear), so make
+ * that first call before any stream capture.  Every call shares the one array
+ * and it keeps the last call's contents; each call clears, on its stream,
+ * what its kernels need to start at zero.  Calls whose work overlaps on the
+ * GPU (different streams, or concurrent host threads) race on the array:
+ * order them on one stream.  A sweep whose bounded wait gives up (see
+ * idw_selftest_bounded_wait) leaves that call's output invalid and sets a
+ * sticky error bit in the shared control words; idw_noalloc_sync_status
+ * reports and clears it.  Returns IDW_ERR_INVALID_ARG, IDW_ERR_ALIGNMENT,
+ * IDW_ERR_UNSUPPORTED (not compute capability 10.3), IDW_ERR_WORKSPACE (too
+ * large) or IDW_ERR_CUDA; the kernels run asynchronously after it returns.
  */
 idw_status idw_interpolate_noalloc(const float *data_xyz, int64_t n, const float *queries_xy,
                                    int64_t m, double p, float *out, void *stream);
+
+/*
+ * Device-side status of the allocation-free calls on the current device (the
+ * paper has no counterpart; see idw_interpolate_noalloc): waits for `stream`
+ * (cudaStream_t as void*), reads the sticky error bits of the shared control
+ * words, clears them, and returns IDW_ERR_DEVICE_TIMEOUT if a bounded wait
+ * gave up since the last check, else IDW_OK (IDW_ERR_CUDA on a CUDA error).
+ * It allocates nothing; it synchronises, so call it outside stream capture.
+ */
+idw_status idw_noalloc_sync_status(void *stream);
+
+/*
+ * The failure-detection self-test of idw_selftest_bounded_wait, reporting
+ * into the allocation-free path's shared control words instead of a
+ * handle's: after about two seconds the next idw_noalloc_sync_status
+ * returns IDW_ERR_DEVICE_TIMEOUT.  Allocates nothing.
+ */
+idw_status idw_noalloc_selftest_bounded_wait(void *stream);
 
 /*
  * Local (radius-limited) Shepard interpolation.  The paper computes the

@@ -87,6 +87,8 @@ SIGNATURES = {
                                       c_double, c_int, c_void_p, c_void_p]),
     "idw_interpolate_noalloc": (c_int, [c_void_p, c_int64, c_void_p, c_int64, c_double, c_void_p,
                                         c_void_p]),
+    "idw_noalloc_sync_status": (c_int, [c_void_p]),
+    "idw_noalloc_selftest_bounded_wait": (c_int, [c_void_p]),
     "idw_interpolate_local": (c_int, [c_void_p, c_void_p, c_int64, c_void_p, c_int64, c_double,
                                       c_double, c_void_p, c_void_p, c_void_p]),
     "idw_create_ex": (c_int, [ctypes.POINTER(c_void_p), c_int, ctypes.c_char_p]),

@@ -218,23 +218,10 @@ void save_tuning(idw_handle_t h) {
 }
 
 // Sweep variant for a batch: forced, tuned (timed once per size class with
-// CUDA events, never while the stream is being captured), or the default.
-// Default without tuning.  Small p = 2 problems (fewer than four
-// 256-point work units per resident CTA) use the fine-grained variant 5, so
-// the grid stays full and balanced; otherwise one 512-thread CTA per SM
-// (variant 4) keeps all 16 warps of an SM in step, when its 4096-query
-// tiles pad the queries no more than variant 0's 2048-query tiles (+1%).
+// CUDA events, never while the stream is being captured), or the default
+// rule of idw::default_sweep_variant.
 int default_variant(idw_handle_t h, const idw::F32Problem* probs, int count, double p) {
-  const int64_t q4 = idw::sweep_variant_queries_per_cta(4), q0 = idw::sweep_variant_queries_per_cta(0);
-  const int64_t tb = idw::sweep_variant_points_per_unit(0);
-  double pad4 = 0, pad0 = 0, units0 = 0;
-  for (int k = 0; k < count; ++k) {
-    pad4 += double((probs[k].m + q4 - 1) / q4 * q4);
-    pad0 += double((probs[k].m + q0 - 1) / q0 * q0);
-    units0 += double((probs[k].m + q0 - 1) / q0) * double((probs[k].n + tb - 1) / tb);
-  }
-  if (!uses_general_power(h, p) && units0 < 4.0 * h->sm_count * 2) return 5;
-  return pad4 <= 1.01 * pad0 ? 4 : 0;
+  return idw::default_sweep_variant(probs, count, uses_general_power(h, p), h->sm_count);
 }
 
 int choose_variant_unresolved(idw_handle_t h, const idw::F32Problem* probs, int count, double p,

@@ -439,6 +439,18 @@ int sweep_variant_points_per_unit(int variant) {
   }
 }
 
+int default_sweep_variant(const F32Problem* probs, int count, bool general_form, int sm_count) {
+  const int64_t q4 = qt_of<4>(), q0 = qt_of<0>();
+  double pad4 = 0, pad0 = 0, units0 = 0;
+  for (int k = 0; k < count; ++k) {
+    pad4 += double((probs[k].m + q4 - 1) / q4 * q4);
+    pad0 += double((probs[k].m + q0 - 1) / q0 * q0);
+    units0 += double((probs[k].m + q0 - 1) / q0) * double((probs[k].n + TB - 1) / TB);
+  }
+  if (!general_form && units0 < 4.0 * sm_count * 2) return 5;
+  return pad4 <= 1.01 * pad0 ? 4 : 0;
+}
+
 int resolve_sweep_variant(int variant, bool general_form) {
   if (variant < 0 || variant >= kNumSweepVariants) return 0;
   // Sub-tile work units need the aligned-AoS staging of the p = 2 form.

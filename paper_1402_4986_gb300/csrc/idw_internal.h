@@ -93,6 +93,12 @@ int sweep_variant_queries_per_cta(int variant);
 int sweep_variant_points_per_unit(int variant);
 // The variant actually run: sub-tile variants fall back to 0 for general p.
 int resolve_sweep_variant(int variant, bool general_form);
+// Default variant without tuning.  Small p = 2 problems (fewer than four
+// 256-point work units per resident CTA) use the fine-grained variant 5, so
+// the grid stays full and balanced; otherwise one 512-thread CTA per SM
+// (variant 4) keeps all 16 warps of an SM in step, when its 4096-query
+// tiles pad the queries no more than variant 0's 2048-query tiles (+1%).
+int default_sweep_variant(const F32Problem* probs, int count, bool general_form, int sm_count);
 
 // Enqueues range scan, staging, sweep, combine and slow path for the batch.
 cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, double p,
