@@ -6,10 +6,12 @@ sweep, FP64 combine, slow path.  Prints ONE JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun, one rank per GPU): every rank interpolates its own 2^20
-queries (seeded by rank) against the same replicated data; there is no
-collective on the data path (weak scaling).  Timing: barrier + synchronize on
-both sides of the K timed steps, max over ranks.
+Multi-GPU (one rank per GPU, under torchrun, or started by this script
+itself when ``--gpus N`` is given without a launcher): every rank
+interpolates its own 2^20 queries (seeded by rank) against the same
+replicated data; there is no collective on the data path (weak scaling).
+Timing: barrier + synchronize on both sides of the K timed steps, max over
+ranks.
 
 Besides ``value`` (device-resident pairs/s) the line carries:
   e2e           the same metric through the host-buffer C-ABI entry point,
@@ -21,7 +23,13 @@ Besides ``value`` (device-resident pairs/s) the line carries:
   error         max |Z - Z_64| / max |z| against the FP64 oracle on a query
                 sample (the same sample the CPU baseline times);
   cpu_baseline  the FP64 oracle on the host cores (bounded query sample);
-  clocks        nvidia-smi samples taken during the timed region.
+  clocks        nvidia-smi samples taken during the timed region;
+  general_p, batched, noalloc
+                after the timed region: the general-power sweep (p = 3.5) on
+                the same data, the 256-problem batched launch against this
+                run's single-instance pairs/s, and the allocation-free entry
+                point at N = M = 262144 against the handle path.
+``--full-check`` compares all M outputs with the oracle (minutes of host time).
 ``--impl reference`` times the oracle alone (the CPU reference arm).
 
 ``--config NAME`` prints one line per other workload instead (``all`` runs
@@ -63,6 +71,49 @@ SHARED_FMA_PER_PAIR = 1.5
 SHARED_MUFU_SAVED_PER_PAIR = 0.5
 SWEEP_SOURCES = ("idw_fwd_f32.cu", "idw_f32_common.cuh", "idw_device.cuh", "idw_internal.h")
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "sweep_p2_n1048576_dram.md")
+
+
+# Algorithmic cost per pair evaluation of each sweep (compensation, loads
+# and loop overhead not credited): FP32 FMA-pipe ops and MUFU ops by kind.
+#   p = 2      d^2 (2 FADD, FMUL, FFMA), S0 FADD, S1 FFMA; rcp
+#   general p  the same plus t = -(p/2) log2 d^2 (FMUL); lg2, ex2
+#   adjoint    one sweep's term (general p): d^2 (4), the two exponents (2
+#              FMUL), z - Z, (z - Z) v, two FFMA for the x / y sums, and for
+#              dL/dp (z - Z) w, log2 d^2 + shift, an FFMA; lg2 and two ex2
+#              (w and v = w / d^2).  The adjoint evaluates each pair twice
+#              (query sweep and data sweep).
+SWEEP_COSTS = {
+    "pow2": {"fma": 6.0, "mufu": {"mufu_rcp": 1.0}},
+    "general": {"fma": 7.0, "mufu": {"mufu_lg2": 1.0, "mufu_ex2": 1.0}},
+    "adjoint_general": {"fma": 13.0, "mufu": {"mufu_lg2": 1.0, "mufu_ex2": 2.0}},
+}
+
+
+def pipe_peak_pairs_s(kind, rates, sms, mhz, evaluations_per_pair=1.0):
+    """min(FMA pipe, MUFU pipe) pairs/s of a sweep from the measured per-SM
+    per-clock pipe rates (MUFU ops of different kinds share the pipe, so
+    their issue times add)."""
+    c = SWEEP_COSTS[kind]
+    ffma = max(rates["ffma"], rates["ffma2"])
+    mufu_clk = sum(n / rates[k] for k, n in c["mufu"].items())
+    per_sm_clk = min(ffma / c["fma"], 1.0 / mufu_clk)
+    return sms * mhz * 1e6 * per_sm_clk / evaluations_per_pair
+
+
+def roofline_block(kind, achieved, rates, sms, mhz, kernel, evaluations_per_pair=1.0,
+                   traffic=None, algorithmic_bytes=None):
+    """The roofline object of a non-headline line: the measured-rate pipe
+    bound of its sweep at the sampled clock."""
+    peak = pipe_peak_pairs_s(kind, rates, sms, mhz, evaluations_per_pair)
+    c = SWEEP_COSTS[kind]
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpairs/s",
+            "frac": achieved / peak if peak else None, "traffic": traffic,
+            "algorithmic_bytes_per_launch": algorithmic_bytes, "kernel": kernel,
+            "peak_basis": f"min(FMA pipe / {c['fma']:g} ops, MUFU pipe / "
+                          + " + ".join(f"{n:g} {k[5:]}" for k, n in c["mufu"].items())
+                          + f") per pair evaluation, measured per-SM-per-clock rates x {sms} "
+                          f"SMs x {mhz} MHz" + (f", {evaluations_per_pair:g} evaluations per pair"
+                                                if evaluations_per_pair != 1.0 else "")}
 
 
 def lp_pairs_per_sm_clk(ffma, mufu):
@@ -112,6 +163,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--full-check", action="store_true",
+                    help="headline only: after the timed region, compare every one of the M "
+                         "outputs with the FP64 oracle on all host cores (minutes) and report "
+                         "the maximum error")
     ap.add_argument("--members", type=float, nargs="*", default=None,
                     help="local / knn workloads only: these neighbour counts (K, or k) "
                          "instead of the default sweep")
@@ -348,6 +403,9 @@ def run_ours(args, ws, rank, local):
             "pipe_rates_per_sm_clk": rates,
             "sweep_ms_avg": sweep_avg_s * 1e3, "sweep_launches": sweep_launches}
 
+    extras = headline_extras(args, idw, h, data, q, data_np, q_np, value / ws, rates, sms,
+                             clk_mhz)
+
     # ---- FP64 oracle on the host: error check + CPU baseline on one sample
     cpu = None
     err = None
@@ -367,6 +425,16 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": S * n / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{S} random queries x all {n} data points ({cpu_s:.1f} s)"}
 
+    full = None
+    if args.full_check:
+        import oracle
+        cores = os.cpu_count() or 1
+        t = time.perf_counter()
+        Zall, _ = oracle.idw(data_np, q_np, 2.0, threads=cores)
+        full = {"queries": int(m), "max_error_vs_fp64_oracle": float(
+                    np.max(np.abs(Z_dev.astype(np.float64) - Zall)) / np.max(np.abs(data_np[:, 2]))),
+                "oracle_s": time.perf_counter() - t, "cores": cores}
+
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
@@ -380,10 +448,12 @@ def run_ours(args, ws, rank, local):
         "e2e": e2e, "gpu_launches": 5 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "error_vs_fp64_oracle": err,
+        **({"full_check": full} if full else {}),
         "f64_plain": {"value": f64_value, "unit": UNIT,
                       "sample": f"{m64} queries x all {n} data points"},
         "speedup_vs_f64_plain": value / ws / f64_value,
         "wall_s_timed_region": wall,
+        **extras,
         "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
                     "max": max(step_ms)},
     }
@@ -391,6 +461,84 @@ def run_ours(args, ws, rank, local):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def headline_extras(args, idw, h, data, q, data_np, q_np, single_pairs_s, rates, sms, mhz):
+    """Compact summaries of the other forward workloads, measured in the same
+    run after the headline's timed region: the general-power sweep on the
+    same N = M = 2^20 data (p = 3.5), the batched workload (256 uneven
+    problems in one persistent launch) against this run's single-instance
+    pairs/s, and the allocation-free entry point at N = M = 262144."""
+    import ctypes
+    import torch
+    import synthetic
+    out = {}
+    n, m = data.shape[0], q.shape[0]
+    pairs = float(n) * m
+    o = torch.empty(m, device="cuda")
+    # General power: the lg2/ex2 sweep.
+    p = 3.5
+    idw.interpolate(data, q, p, out=o, handle=h)
+    idw.profile_read(handle=h)
+    idw.profile_enable(True, handle=h)
+    ms = _events_ms(lambda: idw.interpolate(data, q, p, out=o, handle=h), 3, warm=0)
+    idw.profile_enable(False, handle=h)
+    sweep_ms, launches = idw.profile_read(handle=h)
+    achieved = pairs / (sweep_ms / max(1, launches) / 1e3)
+    gen = {"p": p, "pairs_s": pairs / (ms / 1e3), "call_ms": ms,
+           "roofline": roofline_block("general", achieved, rates, sms, mhz,
+                                      "sweep_kernel<general p> (all-pairs sweep)")}
+    if not args.no_cpu_baseline:
+        import oracle
+        idx = np.sort(np.random.default_rng(11).choice(m, 512, replace=False))
+        Z64, _ = oracle.idw(data_np, q_np[idx], p, threads=os.cpu_count() or 1)
+        gen["error_vs_fp64_oracle"] = float(
+            np.max(np.abs(o.cpu().numpy()[idx].astype(np.float64) - Z64)) /
+            np.max(np.abs(data_np[:, 2])))
+        gen["error_sample_queries"] = len(idx)
+    out["general_p"] = gen
+    # Batched: 256 uneven problems, one persistent launch.
+    batch = synthetic.config_batch()
+    bd = [torch.from_numpy(i["data"]).cuda() for i in batch["instances"]]
+    bq = [torch.from_numpy(i["queries"]).cuda() for i in batch["instances"]]
+    bo = [torch.empty(x.shape[0], device="cuda") for x in bq]
+    bpairs = float(sum(x.shape[0] * y.shape[0] for x, y in zip(bd, bq)))
+    idw.profile_read(handle=h)
+    idw.profile_enable(True, handle=h)
+    bms = _events_ms(lambda: idw.interpolate_batched(bd, bq, 2.0, outs=bo, handle=h), 5)
+    idw.profile_enable(False, handle=h)
+    bsweep, blaunch = idw.profile_read(handle=h)
+    out["batched"] = {
+        "instances": len(bd), "total_pairs": bpairs, "persistent_ms": bms,
+        "persistent_pairs_s": bpairs / (bms / 1e3),
+        "single_large_instance_pairs_s": single_pairs_s,
+        "persistent_vs_single": bpairs / (bms / 1e3) / single_pairs_s,
+        "roofline": roofline_block("pow2", bpairs / (bsweep / max(1, blaunch) / 1e3), rates, sms,
+                                   mhz, "sweep_kernel<p = 2, batch table> (one persistent launch)")}
+    del bd, bq, bo
+    # The allocation-free entry point against the handle path, N = M = 262144.
+    sp = synthetic.config_scale(262144)
+    sd = torch.from_numpy(sp["data"]).cuda()
+    sq = torch.from_numpy(sp["queries"]).cuda()
+    so = torch.empty(sq.shape[0], device="cuda")
+    lib = h.lib
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def noalloc():
+        rc = lib.idw_interpolate_noalloc(sd.data_ptr(), sd.shape[0], sq.data_ptr(), sq.shape[0],
+                                         2.0, so.data_ptr(), st)
+        if rc != 0:
+            raise RuntimeError(f"idw_interpolate_noalloc: status {rc}")
+
+    na_ms = _events_ms(noalloc, 10, warm=2)
+    if lib.idw_noalloc_sync_status(st) != 0:
+        raise RuntimeError("idw_interpolate_noalloc reported a device timeout")
+    hd_ms = _events_ms(lambda: idw.interpolate(sd, sq, 2.0, out=so, handle=h), 10, warm=2)
+    p2 = float(sd.shape[0]) * sq.shape[0]
+    out["noalloc"] = {"n": sd.shape[0], "m": sq.shape[0], "p": 2.0, "ms": na_ms,
+                      "pairs_s": p2 / (na_ms / 1e3), "handle_path_ms": hd_ms,
+                      "noalloc_vs_handle": hd_ms / na_ms}
+    return out
 
 
 # ------------------------------------------------------------ other workloads
@@ -407,6 +555,39 @@ def _events_ms(fn, reps, warm=1):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def _timed_with_sweep(idw, h, fn, reps, warm=1):
+    """(call ms, sweep-kernel ms) per call, both averaged over ``reps`` calls
+    on handle ``h`` (the library records CUDA events around each sweep)."""
+    for _ in range(warm):
+        fn()
+    idw.profile_read(handle=h)
+    idw.profile_enable(True, handle=h)
+    ms = _events_ms(fn, reps, warm=0)
+    idw.profile_enable(False, handle=h)
+    sweep_ms, launches = idw.profile_read(handle=h)
+    return ms, sweep_ms / max(1, launches)
+
+
+def _pipe_context():
+    """Measured pipe rates, SM count and the SM clock for the roofline of the
+    non-headline lines (the clock: the current nvidia-smi reading under load
+    is not sampled here, so the maximum SM clock is used, which makes the
+    fractions conservative)."""
+    import torch
+    import paper_1402_4986_gb300 as idw
+    dev = torch.cuda.current_device()
+    rates = idw.measure_pipe_rates(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                              "-i", str(dev)], capture_output=True, text=True, timeout=10).stdout
+        mhz = float(out.strip().splitlines()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pass
+    return rates, sms, mhz
 
 
 def _raster_order_rows(idw, d, form, arg, label):
@@ -472,6 +653,8 @@ def run_scale(args):
     import synthetic
     import paper_1402_4986_gb300 as idw
     rows = []
+    rates, sms, mhz = _pipe_context()
+    h = idw.get_handle()
     for n in synthetic.SCALE_SWEEP:
         prob = synthetic.config_scale(n)
         d = torch.from_numpy(prob["data"]).cuda()
@@ -479,7 +662,8 @@ def run_scale(args):
         out = torch.empty(n, device="cuda")
         pairs = float(n) * n
         reps = max(3, int(2e11 / pairs))
-        ms = _events_ms(lambda: idw.interpolate(d, q, 2.0, out=out), reps)
+        ms, sweep_ms = _timed_with_sweep(idw, h, lambda: idw.interpolate(d, q, 2.0, out=out,
+                                                                          handle=h), reps)
         m64 = min(n, 8192)
         d64, q64 = d.double(), q[:m64].double()
         ms64 = _events_ms(lambda: idw.interpolate(d64, q64, 2.0, "f64"), 2)
@@ -490,7 +674,9 @@ def run_scale(args):
         rows.append({"n": n, "m": n, "f32c_pairs_s": pairs / (ms / 1e3),
                      "f32c_ms": ms, "f64_pairs_s": float(n) * m64 / (ms64 / 1e3),
                      "speedup_vs_f64": (pairs / ms) / (float(n) * m64 / ms64),
-                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx),
+                     "roofline": roofline_block("pow2", pairs / (sweep_ms / 1e3), rates, sms, mhz,
+                                                "sweep_kernel<p = 2>")})
     _emit("paper-shaped scale sweep N=M, uniform [0,1)^2, wave field, p=2 (FP64 arm on "
           "min(N, 8192) queries)", rows)
 
@@ -508,23 +694,32 @@ def run_clustered(args):
     out = torch.empty(m, device="cuda")
     idx = np.random.default_rng(4).choice(m, 1024, replace=False)
     rows = []
+    rates, sms, mhz = _pipe_context()
+    h = idw.get_handle()
     for p in prob["p_values"]:
-        ms = _events_ms(lambda: idw.interpolate(d, q, p, out=out), 5)
+        ms, sweep_ms = _timed_with_sweep(idw, h, lambda: idw.interpolate(d, q, p, out=out,
+                                                                          handle=h), 5)
         Z64, _ = oracle.idw(prob["data"], prob["queries"][idx], p)
         err = float(np.max(np.abs(out.cpu().numpy()[idx] - Z64)) /
                     np.max(np.abs(prob["data"][:, 2])))
         rows.append({"p": p, "pairs_s": float(n) * m / (ms / 1e3), "ms": ms,
                      "path": "rcp" if p == 2.0 else "log2/exp2",
-                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+                     "error_vs_fp64_oracle": err, "error_sample_queries": len(idx),
+                     "roofline": roofline_block("pow2" if p == 2.0 else "general",
+                                                float(n) * m / (sweep_ms / 1e3), rates, sms, mhz,
+                                                "sweep_kernel")})
     # p = 2 through the log2/exp2 form as well.
     hg = idw.Handle(torch.cuda.current_device())
     idw.set_option("force_general_power", 1, handle=hg)
-    ms = _events_ms(lambda: idw.interpolate(d, q, 2.0, out=out, handle=hg), 5)
+    ms, sweep_ms = _timed_with_sweep(idw, hg, lambda: idw.interpolate(d, q, 2.0, out=out,
+                                                                       handle=hg), 5)
     Z64, _ = oracle.idw(prob["data"], prob["queries"][idx], 2.0)
     err = float(np.max(np.abs(out.cpu().numpy()[idx] - Z64)) / np.max(np.abs(prob["data"][:, 2])))
     hg.close()
     rows.append({"p": 2.0, "pairs_s": float(n) * m / (ms / 1e3), "ms": ms, "path": "log2/exp2",
-                 "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+                 "error_vs_fp64_oracle": err, "error_sample_queries": len(idx),
+                 "roofline": roofline_block("general", float(n) * m / (sweep_ms / 1e3), rates, sms,
+                                            mhz, "sweep_kernel<general p>")})
     _emit("clustered: N=262144 from 64 Gaussian blobs (sigma 0.01), z = exp(-4 r^2) + "
           "0.05 N(0,1), queries on a 1024^2 grid", rows)
 
@@ -551,12 +746,18 @@ def run_adjoint(args):
     fwd_ms = _events_ms(fwd, 3)
     bwd_ms = _events_ms(bwd, 3)
     pairs = float(n) * m
+    rates, sms, mhz = _pipe_context()
     _emit("adjoint: N=M=262144 uniform [0,1)^2, wave field, p=2.5, upstream grad N(0,1); "
           "backward = query sweep + data sweep (2 pair evaluations per pair)",
           [{"forward_ms": fwd_ms, "forward_pairs_s": pairs / (fwd_ms / 1e3),
             "backward_ms": bwd_ms, "backward_pairs_s": pairs / (bwd_ms / 1e3),
             "backward_pair_evaluations_s": 2 * pairs / (bwd_ms / 1e3),
-            "backward_over_forward": bwd_ms / fwd_ms}])
+            "backward_over_forward": bwd_ms / fwd_ms,
+            "roofline": roofline_block("adjoint_general", pairs / (bwd_ms / 1e3), rates, sms, mhz,
+                                       "query sweep + data sweep (whole backward call)",
+                                       evaluations_per_pair=2.0),
+            "forward_roofline": roofline_block("general", pairs / (fwd_ms / 1e3), rates, sms, mhz,
+                                               "sweep_kernel<general p> (whole forward call)")}])
 
 
 def run_batched(args, headline_pairs_s=None):
@@ -578,7 +779,9 @@ def run_batched(args, headline_pairs_s=None):
         for dk, qk, ok in zip(d, q, outs):
             idw.interpolate(dk, qk, 2.0, out=ok)
 
-    ms_b = _events_ms(batched, 5)
+    rates, sms, mhz = _pipe_context()
+    hb = idw.get_handle()
+    ms_b, sweep_b = _timed_with_sweep(idw, hb, batched, 5)
     ms_l = _events_ms(loop, 3)
     # Autotuned: the first call of the size class times every sweep variant.
     ht = idw.Handle(torch.cuda.current_device())
@@ -621,7 +824,9 @@ def run_batched(args, headline_pairs_s=None):
            "autotune_first_call_s": tune_s, "pairs_s_per_variant": per_variant,
            "single_large_instance_pairs_s": headline_pairs_s,
            "persistent_vs_single": (pairs / (ms_b / 1e3)) / headline_pairs_s,
-           "persistent_vs_loop": ms_l / ms_b}
+           "persistent_vs_loop": ms_l / ms_b,
+           "roofline": roofline_block("pow2", pairs / (sweep_b / 1e3), rates, sms, mhz,
+                                      "sweep_kernel<p = 2, batch table> (one persistent launch)")}
     _emit("batched: 256 problems, N_i, M_i log-uniform in [1024, 262144] (seeded), uniform "
           "[0,1)^2, p=2, FP32-compensated; one persistent launch (also graph-captured) vs a "
           "loop of per-instance calls; single large instance = N=M=2^20", [row])
@@ -862,9 +1067,37 @@ def run_knn(args):
           cpu_baseline=cpu)
 
 
+def spawn_ranks(args):
+    """``--gpus N`` without an external launcher: start N copies of this script
+    as ranks 0..N-1 (one GPU each, NCCL rendezvous on 127.0.0.1) and wait for
+    them; rank 0 prints the JSON line."""
+    import socket
+    import torch
+    visible = torch.cuda.device_count()
+    if visible < args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} needs {args.gpus} visible GPUs, found {visible}")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    procs = []
+    for r in range(args.gpus):
+        env = dict(os.environ, RANK=str(r), LOCAL_RANK=str(r), WORLD_SIZE=str(args.gpus),
+                   LOCAL_WORLD_SIZE=str(args.gpus), MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+        procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), *sys.argv[1:]],
+                                      env=env))
+    rc = 0
+    for pr in procs:
+        rc = max(rc, pr.wait())
+    sys.exit(rc)
+
+
 def main():
     args = parse()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1 and args.impl == "ours":
+        spawn_ranks(args)
     ws, rank, local = dist_env()
+    if "WORLD_SIZE" in os.environ and args.impl == "ours" and ws != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started {ws} ranks")
     if args.impl == "reference":
         run_reference(args, rank)
         return
