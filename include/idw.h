@@ -305,6 +305,25 @@ idw_status idw_selftest_bounded_wait(idw_handle_t handle, void *stream);
 idw_status idw_measure_pipe_rates(int device, double rates[6]);
 
 /*
+ * Diagnostic: the accuracy of the three MUFU approximations in the weight
+ * w = d^-p (Sec. 2.1, Eq. 1), measured exhaustively over every positive fp32
+ * input of the range each is used on.  errs[0..3] receive:
+ *   errs[0]  max |rcp.approx(x) x - 1| over normal x with normal 1/x;
+ *   errs[1]  max |lg2.approx(x) - log2 x| over x in [1/2, 2] (absolute, in
+ *            log2 units);
+ *   errs[2]  max |ex2.approx(t) / 2^t - 1| over |t| in [2^-30, 126] where
+ *            2^t is a normal float;
+ *   errs[3]  max |lg2.approx(x) - log2 x| / |log2 x| over every other normal
+ *            x (the result's own fp32 rounding included).
+ * These are the constants of the FP32 form's worst-case error bound.  The
+ * reference values come from the device's FP64 log2 and exp2 (the
+ * reciprocal's check r x - 1 is exact in FP64).  Synchronous; about four
+ * billion evaluations, well under a second on a GB300.  Errors:
+ * IDW_ERR_INVALID_ARG (null errs, bad device), IDW_ERR_CUDA.
+ */
+idw_status idw_measure_mufu_errors(int device, double errs[4]);
+
+/*
  * Diagnostic of a debug build (the library compiled with -DIDW_DEBUG_CHECKS,
  * e.g. paper_1402_4986_gb300.build.build(debug=True)): the kernels of the
  * local and k-nearest-neighbour forms check every gather, scatter, cell,

@@ -27,7 +27,7 @@ __all__ = [
     "KnnIDWFunction",
     "idw_knn",
     "paper_interpolate", "backward", "IDWFunction", "idw", "plan_forward",
-    "measure_pipe_rates", "sync_status", "profile_enable", "profile_read",
+    "measure_pipe_rates", "measure_mufu_errors", "sync_status", "profile_enable", "profile_read",
     "selftest_bounded_wait", "set_option", "get_option", "PREC_F32_COMP", "PREC_F64_PLAIN",
 ]
 
@@ -650,3 +650,12 @@ def measure_pipe_rates(device: int = 0) -> dict:
     _lib.check(lib.idw_measure_pipe_rates(int(device), arr), "idw_measure_pipe_rates")
     keys = ("ffma", "ffma2", "mufu_rcp", "mufu_lg2", "mufu_ex2", "dfma")
     return dict(zip(keys, list(arr)))
+
+
+def measure_mufu_errors(device: int = 0) -> dict:
+    """Worst-case accuracy of the MUFU rcp / lg2 / ex2 approximations, measured
+    over every fp32 input of their ranges (see include/idw.h)."""
+    lib = _lib.load()
+    arr = (ctypes.c_double * 4)()
+    _lib.check(lib.idw_measure_mufu_errors(int(device), arr), "idw_measure_mufu_errors")
+    return {"rcp_rel": arr[0], "lg2_abs": arr[1], "ex2_rel": arr[2], "lg2_rel_outer": arr[3]}

@@ -77,6 +77,7 @@ SIGNATURES = {
     "idw_plan_forward": (c_int, [c_int32, c_int32, c_int64, c_int64, c_double, c_int,
                                  ctypes.POINTER(PlanInfo)]),
     "idw_measure_pipe_rates": (c_int, [c_int, ctypes.POINTER(c_double)]),
+    "idw_measure_mufu_errors": (c_int, [c_int, ctypes.POINTER(c_double)]),
     "idw_debug_check_failures": (c_int, [c_int, ctypes.POINTER(ctypes.c_uint32)]),
     "idw_set_option": (c_int, [c_void_p, c_int, c_int64]),
     "idw_get_option": (c_int, [c_void_p, c_int, ctypes.POINTER(c_int64)]),

@@ -1043,4 +1043,18 @@ idw_status idw_measure_pipe_rates(int device, double rates[6]) {
   return e == cudaSuccess ? IDW_OK : IDW_ERR_CUDA;
 }
 
+idw_status idw_measure_mufu_errors(int device, double errs[4]) {
+  if (!errs) return IDW_ERR_INVALID_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return IDW_ERR_INVALID_ARG;
+  DeviceGuard guard(device);
+  if (!guard.ok) return IDW_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return IDW_ERR_CUDA;
+  cudaError_t e = idw::measure_mufu_errors(sms, errs);
+  return e == cudaSuccess ? IDW_OK : IDW_ERR_CUDA;
+}
+
 }  // extern "C"

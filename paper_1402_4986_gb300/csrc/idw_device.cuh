@@ -79,6 +79,36 @@ __device__ __forceinline__ void two_sum_acc(u64& hi, u64& lo, u64 c) {
   hi = s;
 }
 
+// Renormalises a (hi, lo) pair with TwoSum: afterwards hi = fl(hi + lo) and
+// lo is its exact remainder, so |lo| <= ulp(hi) / 2.  Keeping lo that small
+// keeps the rounding of later `lo += e` steps second order in u.
+__device__ __forceinline__ void two_sum_renorm(u64& hi, u64& lo) {
+  const u64 s = add2(hi, lo);
+  const u64 bv = sub2(s, hi);
+  const u64 av = sub2(s, bv);
+  lo = add2(sub2(hi, av), sub2(lo, bv));
+  hi = s;
+}
+
+// Balanced pairwise summation of 2^LEVELS packed terms fed one at a time.
+// Term i (a compile-time constant once the caller's loop is unrolled) enters
+// at level 0; P[l] holds the sum of the last finished block of 2^l terms
+// still waiting for its right-hand partner.  Every addition joins two blocks
+// of equal size, so each term passes through exactly LEVELS roundings.  The
+// sum of all 2^LEVELS terms lands in `total` with the last term.
+template <int LEVELS>
+__device__ __forceinline__ void tree_push(u64 (&P)[LEVELS], u64 v, int i, u64& total) {
+#pragma unroll
+  for (int l = 0; l < LEVELS; ++l) {
+    if (!((i >> l) & 1)) {
+      P[l] = v;
+      return;
+    }
+    v = add2(P[l], v);
+  }
+  total = v;
+}
+
 // ------------------------------------------------------------- MUFU ops
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;

@@ -20,8 +20,12 @@
 //     this moves work from the MUFU pipe (the binding one) to the FMA pipe.
 //     General p: 2^(-(p/2) log2 d^2) with the product's rounding error
 //     recovered by an FMA and applied to first order;
-//   * sums run in chunks of 64 (p = 2) or 32 points; each chunk sum is folded into
-//     (hi, lo) pairs by Knuth's TwoSum, so the error does not grow with n;
+//   * sums run in chunks of 64 (p = 2) or 32 points: S0 as a balanced
+//     binary tree, S1 as FMA chains of products joined by a tree; each chunk
+//     sum is folded into a (hi, lo) pair by Knuth's TwoSum (the pairs live in
+//     shared memory, one slot per thread and query pair) and the pair is
+//     renormalised once per work unit, so the worst-case error is a fixed
+//     number of roundings per term, independent of n;
 //   * the (problem, query tile, data tile) work units are split evenly over
 //     a grid of co-resident CTAs (stream-K).  Pieces of a query tile are
 //     summed in FP64 by the combine, which plays the role of the paper's
@@ -46,7 +50,11 @@ constexpr int TB = kRecordsF32;
 constexpr int ST = kStagesF32;
 constexpr uint32_t kTileBytes = static_cast<uint32_t>(kTileBytesF32);
 static_assert(kTileBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-static_assert(TB % kChunkF32Pow2 == 0 && TB % kChunkF32General == 0, "chunks tile a data tile");
+constexpr bool chunk_shape_ok(ChunkShape c) {
+  return TB % c.points == 0 && c.points == (1 << c.tree_levels) &&
+         c.points == c.chain << c.chain_levels;
+}
+static_assert(chunk_shape_ok(kChunkPow2) && chunk_shape_ok(kChunkGeneral), "chunk trees");
 
 // Compiled sweep variants (the autotuner picks one per size class):
 // threads per CTA, query pairs per thread, and how many of those pairs share
@@ -65,7 +73,7 @@ template <> struct Var<0> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT
 template <> struct Var<1> { static constexpr int NT = 256, KP = 4, KSH = 0, KALT = -1, TBV = 256; };
 template <> struct Var<2> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = 1, TBV = 256; };
 template <> struct Var<3> { static constexpr int NT = 128, KP = 4, KSH = 1, KALT = -1, TBV = 256; };
-template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1, KALT = -1, TBV = 256; };
+template <> struct Var<4> { static constexpr int NT = 512, KP = 4, KSH = 1, KALT = 1, TBV = 256; };
 template <> struct Var<5> { static constexpr int NT = 256, KP = 4, KSH = 1, KALT = -1, TBV = 64; };
 template <int V> __host__ __device__ constexpr int qt_of() { return Var<V>::NT * 2 * Var<V>::KP; }
 static_assert(kNumSweepVariants == 6, "variant table");
@@ -131,12 +139,51 @@ __device__ __forceinline__ void load_record(const unsigned char* tile, int i, u6
   }
 }
 
+// The running (hi, lo) pairs of a thread: slot 2k holds (S0 hi, S0 lo) of
+// query pair k and slot 2k + 1 (S1 hi, S1 lo), each a pair of packed lanes;
+// in registers, or in shared memory at [s NT + tid] after the tile ring.
+constexpr bool kSumsInShared = true;
+
+template <int KP, int NT, bool SMEM>
+struct SumSlots;
+template <int KP, int NT>
+struct SumSlots<KP, NT, false> {
+  ulonglong2 r[2 * KP];
+  __device__ __forceinline__ void bind(unsigned char*, int) {}
+  __device__ __forceinline__ ulonglong2 get(int s) const { return r[s]; }
+  __device__ __forceinline__ void set(int s, ulonglong2 v) { r[s] = v; }
+};
+template <int KP, int NT>
+struct SumSlots<KP, NT, true> {
+  ulonglong2* base;  // this thread's slot 0
+  __device__ __forceinline__ void bind(unsigned char* p, int tid) {
+    base = reinterpret_cast<ulonglong2*>(p) + tid;
+  }
+  __device__ __forceinline__ ulonglong2 get(int s) const { return base[s * NT]; }
+  __device__ __forceinline__ void set(int s, ulonglong2 v) { base[s * NT] = v; }
+};
+
+// Shared memory of one sweep CTA: the tile ring, then the sum slots.
+template <int V, int LAYOUT>
+__host__ __device__ constexpr size_t ring_bytes_of() {
+  return size_t(ST) * (Var<V>::TBV == TB ? tile_bytes_of<LAYOUT>() : Var<V>::TBV * 16u);
+}
+template <int V>
+__host__ __device__ constexpr size_t hl_bytes_of() {
+  return kSumsInShared ? size_t(2) * Var<V>::KP * Var<V>::NT * sizeof(ulonglong2) : 0;
+}
+template <int V, int LAYOUT>
+__host__ __device__ constexpr size_t sweep_smem_of() {
+  return ring_bytes_of<V, LAYOUT>() + hl_bytes_of<V>();
+}
+
 template <int MODE, int CAP, int V, int LAYOUT = 0>
 __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
   constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
   constexpr int KALT = Var<V>::KALT;
-  constexpr int CH = MODE == kPow2 ? kChunkF32Pow2 : kChunkF32General;
+  constexpr ChunkShape SH = MODE == kPow2 ? kChunkPow2 : kChunkGeneral;
+  constexpr int CH = SH.points;
   constexpr int TBU = Var<V>::TBV;
   static_assert(TBU == TB || LAYOUT == 1, "sub-tile units need record-contiguous staging");
   static_assert(TBU % CH == 0, "chunks tile a work unit");
@@ -145,6 +192,8 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
   constexpr uint32_t kTileBytes = TBU == TB ? tile_bytes_of<LAYOUT>() : TBU * 16u;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) unsigned long long full_bar[ST];
+  SumSlots<KP, NT, kSumsInShared> HL;
+  HL.bind(smem + ring_bytes_of<V, LAYOUT>(), threadIdx.x);
 
   const int tid = threadIdx.x;
   const int64_t g = blockIdx.x;
@@ -187,7 +236,7 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     const int64_t seg_end = min(total, I.unit_base + (qt + 1) * I.data_tiles - u0);
     const float sc = a.scales[ci];
 
-    u64 QX[KP], QY[KP], H0[KP], L0[KP], H1[KP], L1[KP];
+    u64 QX[KP], QY[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
       const int64_t ja = qt * QT + (2 * k) * NT + tid;
@@ -198,7 +247,8 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
       const float yb = jb < I.m ? I.queries[2 * jb + 1] * sc : 0.f;
       QX[k] = pk(xa, xb);
       QY[k] = pk(ya, yb);
-      H0[k] = L0[k] = H1[k] = L1[k] = 0ull;
+      HL.set(2 * k, make_ulonglong2(0ull, 0ull));
+      HL.set(2 * k + 1, make_ulonglong2(0ull, 0ull));
     }
 
     for (; i < seg_end; ++i) {
@@ -209,31 +259,48 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
         const unsigned char* tile = smem + s * kTileBytes;
 #pragma unroll 1
         for (int c = 0; c < TBU; c += CH) {
-          u64 C0[KP], C1[KP];
+          // S0: tree over the chunk's weights.  S1: chains of SH.chain
+          // products w z (one MUL, then FMAs), chains joined by a tree.
+          u64 P0[KP][SH.tree_levels], P1[KP][SH.chain_levels], T1[KP], C0[KP], C1[KP];
 #pragma unroll
           for (int r = 0; r < CH; ++r) {
             u64 xx, yy, zz;
             load_record<LAYOUT>(tile, c + r, xx, yy, zz);
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
-              const u64 dx = sub2f(QX[k], xx);
-              const u64 dy = sub2f(QY[k], yy);
-              const u64 d2 = fma2f(dy, dy, mul2f(dx, dx));
+              // d^2 rounded to nearest with subnormals kept: a d^2 that is
+              // itself subnormal is flushed by the weight's MUFU input and
+              // sends the query to the FP64 path through a non-finite sum.
+              const u64 dx = sub2(QX[k], xx);
+              const u64 dy = sub2(QY[k], yy);
+              const u64 d2 = fma2(dy, dy, mul2(dx, dx));
               const bool shared = k < KSHARED || (k == KALT && (r & 1));
               const u64 w = weight_pair<MODE>(d2, shared, hp2, nhp2);
-              if (r == 0) {
-                C0[k] = w;
-                C1[k] = mul2(w, zz);
+              tree_push<SH.tree_levels>(P0[k], w, r, C0[k]);
+              if (r % SH.chain == 0) {
+                T1[k] = mul2(w, zz);
               } else {
-                C0[k] = add2(C0[k], w);
-                C1[k] = fma2(w, zz, C1[k]);
+                T1[k] = fma2(w, zz, T1[k]);
               }
+              if (r % SH.chain == SH.chain - 1)
+                tree_push<SH.chain_levels>(P1[k], T1[k], r / SH.chain, C1[k]);
             }
           }
+          // Error-free folds of the chunk sums into the (hi, lo) slots; the
+          // last chunk of a work unit also renormalises each pair.
+          const bool last = c + CH == TBU;
 #pragma unroll
           for (int k = 0; k < KP; ++k) {
-            two_sum_acc(H0[k], L0[k], C0[k]);
-            two_sum_acc(H1[k], L1[k], C1[k]);
+            ulonglong2 s0 = HL.get(2 * k);
+            ulonglong2 s1 = HL.get(2 * k + 1);
+            two_sum_acc(s0.x, s0.y, C0[k]);
+            two_sum_acc(s1.x, s1.y, C1[k]);
+            if (last) {
+              two_sum_renorm(s0.x, s0.y);
+              two_sum_renorm(s1.x, s1.y);
+            }
+            HL.set(2 * k, s0);
+            HL.set(2 * k + 1, s1);
           }
         }
       }
@@ -252,11 +319,13 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     float4* P = a.partial + (I.qtile_base + qt + g) * QT;
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
+      const ulonglong2 s0 = HL.get(2 * k);
+      const ulonglong2 s1 = HL.get(2 * k + 1);
       float h0a, h0b, l0a, l0b, h1a, h1b, l1a, l1b;
-      upk(H0[k], h0a, h0b);
-      upk(L0[k], l0a, l0b);
-      upk(H1[k], h1a, h1b);
-      upk(L1[k], l1a, l1b);
+      upk(s0.x, h0a, h0b);
+      upk(s0.y, l0a, l0b);
+      upk(s1.x, h1a, h1b);
+      upk(s1.y, l1a, l1b);
       P[(2 * k) * NT + tid] = make_float4(h0a, l0a, h1a, l1a);
       P[(2 * k + 1) * NT + tid] = make_float4(h0b, l0b, h1b, l1b);
     }
@@ -270,21 +339,28 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
   }
 }
 
-// FP64 combine of the pieces of each query: Z = S1 / S0, or a flag that
-// routes the query to the slow path (exact hit or FP32 range exceeded).
-// One CTA covers 32 consecutive query slots (lanes x) and splits each
-// query's pieces over 8 warps (lanes y, strided); every warp's loads are
-// coalesced across its 32 queries, and the 8 partial sums are added in a
-// fixed order, so the result is deterministic.
+// FP64 combine of the pieces of each query: Z = S1 / S0, or, for a query
+// outside the fast form (exact hit or FP32 range exceeded), the FP64 slow
+// path run by the same CTA.  One CTA covers 32 consecutive query slots
+// (lanes x) and splits each query's pieces over 8 warps (lanes y, strided);
+// every warp's loads are coalesced across its 32 queries, and the 8 partial
+// sums are added in a fixed order, so the result is deterministic.  The
+// CTA's flagged queries are then redone one after another by all 256
+// threads (a query's slow path reads all n points).  Block 0 finally clears
+// the per-problem range words the range scan and staging of this call used,
+// so the next call (or graph replay) starts from zero without a memset.
 constexpr int kCombineQueries = 32;
 constexpr int kCombineLanes = 8;
+static_assert(kCombineQueries * kCombineLanes == kSlowThreads, "the combine CTA runs the slow path");
 
 template <int CAP, int QT>
 __global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
     combine_kernel(const __grid_constant__ Table<CAP> t, const float4* __restrict__ partial,
                    int64_t total_slots, int64_t units, int grid, const float* __restrict__ scales,
-                   double p, Control* __restrict__ ctrl, int2* __restrict__ list) {
+                   double p, Control* __restrict__ ctrl) {
   __shared__ double red0[kCombineLanes][kCombineQueries], red1[kCombineLanes][kCombineQueries];
+  __shared__ int2 flagged[kCombineQueries];
+  __shared__ int nflagged;
   const int lx = threadIdx.x % kCombineQueries, ly = threadIdx.x / kCombineQueries;
   const int64_t idx = int64_t(blockIdx.x) * kCombineQueries + lx;
   bool valid = idx < total_slots;
@@ -307,39 +383,38 @@ __global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
   }
   red0[ly][lx] = s0;
   red1[ly][lx] = s1;
+  if (threadIdx.x == 0) nflagged = 0;
   __syncthreads();
-  if (ly != 0 || !valid) return;
-  s0 = red0[0][lx];
-  s1 = red1[0][lx];
+  if (ly == 0 && valid) {
+    s0 = red0[0][lx];
+    s1 = red1[0][lx];
 #pragma unroll
-  for (int y = 1; y < kCombineLanes; ++y) {
-    s0 += red0[y][lx];
-    s1 += red1[y][lx];
+    for (int y = 1; y < kCombineLanes; ++y) {
+      s0 += red0[y][lx];
+      s1 += red1[y][lx];
+    }
+    if (!(s0 > kTinySumPerPoint * double(I.n)) || !isfinite(s0) || !isfinite(s1) ||
+        (p >= 2.0 && s0 > kHugeSumPow2Up)) {
+      flagged[atomicAdd(&nflagged, 1)] = make_int2(k, static_cast<int>(j));
+    } else {
+      I.out[j] = static_cast<float>(s1 / s0);
+      // Weights were computed on coordinates scaled by s: w = s^-p w_true.
+      if (I.s0_out) I.s0_out[j] = s0 * pow(double(scales[k]), p);
+      if (I.hit_out) I.hit_out[j] = kNoHit;
+    }
   }
-  if (!(s0 > kTinySumPerPoint * double(I.n)) || !isfinite(s0) || !isfinite(s1)) {
-    const unsigned slot = atomicAdd(&ctrl->flagged, 1u);
-    list[slot] = make_int2(k, static_cast<int>(j));
-    return;
+  __syncthreads();
+  const int nf = nflagged;
+  for (int f = 0; f < nf; ++f) {  // uniform across the CTA
+    const int2 e = flagged[f];
+    const Instance& F = t.inst[e.x];
+    const int64_t jf = e.y;
+    slow_one_query<float, float>(F.data, F.n, F.queries[2 * jf], F.queries[2 * jf + 1], p,
+                                 &F.out[jf], F.s0_out ? &F.s0_out[jf] : nullptr,
+                                 F.hit_out ? &F.hit_out[jf] : nullptr);
   }
-  I.out[j] = static_cast<float>(s1 / s0);
-  // Weights were computed on coordinates scaled by s: w = s^-p w_true.
-  if (I.s0_out) I.s0_out[j] = s0 * pow(double(scales[k]), p);
-  if (I.hit_out) I.hit_out[j] = kNoHit;
-}
-
-template <int CAP>
-__global__ void __launch_bounds__(kSlowThreads)
-    slow_batch_kernel(const __grid_constant__ Table<CAP> t, double p,
-                      const Control* __restrict__ ctrl, const int2* __restrict__ list) {
-  const unsigned count = ctrl->flagged;
-  for (unsigned f = blockIdx.x; f < count; f += gridDim.x) {
-    const int2 e = list[f];
-    const Instance& I = t.inst[e.x];
-    const int64_t j = e.y;
-    slow_one_query<float, float>(I.data, I.n, I.queries[2 * j], I.queries[2 * j + 1], p,
-                                 &I.out[j], I.s0_out ? &I.s0_out[j] : nullptr,
-                                 I.hit_out ? &I.hit_out[j] : nullptr);
-  }
+  if (blockIdx.x == 0)
+    for (int c = threadIdx.x; c < t.count; c += blockDim.x) ctrl->maxbits[c] = 0u;
 }
 
 // One thread waits, with the sweep kernels' bounded wait, on a barrier whose
@@ -355,6 +430,23 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Raises a kernel's dynamic shared memory limit to `bytes` (needed above
+// 48 KB), once per kernel and device (one flag word per instantiation).
+template <auto KERNEL>
+cudaError_t allow_dynamic_smem(size_t bytes) {
+  static unsigned long long done = 0;  // one bit per device ordinal < 64
+  if (bytes <= 48u * 1024u) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (__atomic_load_n(&done, __ATOMIC_ACQUIRE) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(bytes));
+  if (e == cudaSuccess && bit) __atomic_fetch_or(&done, bit, __ATOMIC_ACQ_REL);
+  return e;
+}
+
 template <int CAP, int V, int MODE, int LAYOUT>
 cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p,
                         unsigned char* ws, Control* ctrl, int sm_count, const SweepEvents* ev,
@@ -364,10 +456,8 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   t.pad = 0;
   unsigned char* tiles = ws;
   float4* partial = reinterpret_cast<float4*>(ws + plan.staged_bytes);
-  int2* list = reinterpret_cast<int2*>(ws + plan.staged_bytes + plan.partial_bytes);
-  unsigned* maxbits =
-      reinterpret_cast<unsigned*>(ws + plan.staged_bytes + plan.partial_bytes + plan.list_bytes);
-  float* scales = reinterpret_cast<float*>(maxbits + plan.count);
+  float* scales = reinterpret_cast<float*>(ws + plan.staged_bytes + plan.partial_bytes);
+  unsigned* maxbits = ctrl->maxbits;  // zero on entry: cleared by the previous call's combine
   int64_t longest = 1;
   for (int k = 0; k < plan.count; ++k) {
     Instance& I = t.inst[k];
@@ -385,9 +475,7 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
     I.qtile_base = static_cast<int32_t>(plan.qtile_base[k]);
     longest = std::max<int64_t>(longest, std::max(probs[k].n, probs[k].m));
   }
-  cudaError_t e = cudaMemsetAsync(maxbits, 0, sizeof(unsigned) * plan.count, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&ctrl->flagged, 0, sizeof(unsigned), stream);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
 
   const unsigned gx = static_cast<unsigned>(std::min<int64_t>(1024, (longest + 255) / 256));
   range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
@@ -403,8 +491,8 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   a.partial = partial;
   a.scales = scales;
   a.err = &ctrl->error;
-  const size_t smem =
-      size_t(ST) * (Var<V>::TBV == TB ? tile_bytes_of<LAYOUT>() : Var<V>::TBV * 16u);
+  constexpr size_t smem = sweep_smem_of<V, LAYOUT>();
+  if ((e = allow_dynamic_smem<sweep_kernel<MODE, CAP, V, LAYOUT>>(smem)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
   constexpr int NT = Var<V>::NT, QT = qt_of<V>();
   sweep_kernel<MODE, CAP, V, LAYOUT><<<plan.grid, NT, smem, stream>>>(a, t);
@@ -414,8 +502,7 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   const int64_t slots = plan.total_query_tiles * QT;
   combine_kernel<CAP, QT><<<static_cast<unsigned>((slots + kCombineQueries - 1) / kCombineQueries),
                             kCombineQueries * kCombineLanes, 0, stream>>>(
-      t, partial, slots, plan.units, plan.grid, scales, p, ctrl, list);
-  slow_batch_kernel<CAP><<<2 * sm_count, kSlowThreads, 0, stream>>>(t, p, ctrl, list);
+      t, partial, slots, plan.units, plan.grid, scales, p, ctrl);
   return cudaGetLastError();
 }
 
@@ -492,8 +579,8 @@ void plan_batch_f32(const F32Problem* probs, int count, int sm_count, int ctas_p
   bp->partial_slots = qtiles + bp->grid - 1;
   bp->staged_bytes = round_up(size_t(tiles) * kTileBytes, 256);  // the widest layout
   bp->partial_bytes = round_up(size_t(bp->partial_slots) * QT * sizeof(float4), 256);
-  bp->list_bytes = round_up(size_t(std::max<int64_t>(queries, 1)) * sizeof(int2), 256);
-  bp->scale_bytes = round_up(size_t(count) * 8, 256);
+  bp->list_bytes = 0;  // flagged queries are listed in the combine CTA's shared memory
+  bp->scale_bytes = round_up(size_t(count) * sizeof(float), 256);
   bp->workspace_bytes = bp->staged_bytes + bp->partial_bytes + bp->list_bytes + bp->scale_bytes;
 }
 
@@ -544,14 +631,17 @@ namespace {
 template <int V>
 int occupancy_variant(bool general_p) {
   int blocks = 0;
-  const size_t smem = size_t(ST) * kTileBytes;
   if constexpr (Var<V>::TBV == TB) {
     if (general_p) {
+      constexpr size_t smem = sweep_smem_of<V, 0>();
+      allow_dynamic_smem<sweep_kernel<kPowGeneral, kBatchCap, V, 0>>(smem);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &blocks, sweep_kernel<kPowGeneral, kBatchCap, V, 0>, Var<V>::NT, smem);
       return blocks > 0 ? blocks : 1;
     }
   }
+  constexpr size_t smem = sweep_smem_of<V, 1>();
+  allow_dynamic_smem<sweep_kernel<kPow2, kBatchCap, V, 1>>(smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, sweep_kernel<kPow2, kBatchCap, V, 1>,
                                                 Var<V>::NT, smem);
   return blocks > 0 ? blocks : 1;

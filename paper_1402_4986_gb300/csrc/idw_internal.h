@@ -18,10 +18,22 @@ constexpr int kQueryPairsF32 = 4;
 constexpr int kQueriesPerCtaF32 = kThreadsF32 * 2 * kQueryPairsF32;  // 2048
 constexpr int kRecordsF32 = 256;
 constexpr int kStagesF32 = 3;
-// Points per chunk between TwoSum folds: longer chunks cost fewer FMA-pipe
-// operations; the general-power body is longer, so it keeps shorter chunks.
-constexpr int kChunkF32Pow2 = 64;
-constexpr int kChunkF32General = 32;
+// Points per chunk between error-free TwoSum folds, and the shape of the
+// chunk sums.  S0 is summed as a balanced binary tree, S1 as FMA chains of
+// products w z joined by a tree, so every term passes through a fixed number
+// of roundings before the fold: p = 2, chunks of 64: 6 (S0) and 4 + 4 (S1);
+// general p, chunks of 32: 5 (S0) and 8 + 2 (S1).  The general form keeps
+// shorter chunks: its longer weight arithmetic leaves fewer registers.
+struct ChunkShape {
+  int points, tree_levels, chain, chain_levels;
+};
+constexpr ChunkShape kChunkPow2{64, 6, 4, 4};
+constexpr ChunkShape kChunkGeneral{32, 5, 8, 2};
+// Weight sums above 2^100 (coordinates prescaled into [2^9, 2^10)) can only
+// come from a point closer than 2^-50 to the query when p >= 2; such queries
+// are recomputed in FP64, which keeps every d^2 of the fast path far above
+// the FP32 subnormal range.
+constexpr double kHugeSumPow2Up = 1.2676506002282294e30;  // 2^100
 constexpr size_t kTileBytesF32 = size_t(kRecordsF32) * 24;  // 16 B (x,x,y,y) + 8 B (z,z)
 // Instances per batched launch (the instance table is a kernel parameter).
 constexpr int kBatchCap = 256;
@@ -45,10 +57,13 @@ constexpr double kTinySumPerPoint = 7.888609052210118e-31;  // 2^-100
 constexpr int32_t kNoHit = -1;
 constexpr int32_t kRecomputedF64 = -2;
 
-// Device control words owned by a handle.
+// Device control words owned by a handle (zeroed once at creation).
 struct Control {
   unsigned flagged;  // number of queries routed to the slow path this call
   unsigned error;    // sticky error bits (kErrWaitTimeout, ...)
+  // Per-problem largest |coordinate| (float bits) of the FP32 forward's
+  // range scan; every call leaves them zero (its combine clears them).
+  unsigned maxbits[kBatchCap];
 };
 
 enum WeightMode : int { kPow2 = 0, kPowGeneral = 1 };
@@ -172,5 +187,9 @@ cudaError_t launch_paper_kernel(int kernel, int layout, bool fp64, const void* r
 
 // Pipe-rate probe: returns ops per SM per clock for the 6 probed pipes.
 cudaError_t measure_pipe_rates(int sm_count, double rates[6]);
+// Exhaustive accuracy of the MUFU approximations the weights use:
+// errs = {max relative error of rcp, max absolute error of lg2 on [1/2, 2],
+// max relative error of ex2, max error of lg2 relative to |log2 x| elsewhere}.
+cudaError_t measure_mufu_errors(int sm_count, double errs[4]);
 
 }  // namespace idw

@@ -24,7 +24,7 @@ namespace {
 
 // 32 MiB of scratch, held by every GPU that loads this module until exit.
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
-constexpr size_t kControlBytes = 256;  // Control words, padded to keep alignment
+constexpr size_t kControlBytes = (sizeof(Control) + 255) / 256 * 256;  // padded to keep alignment
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;

@@ -185,3 +185,43 @@ def config_local(seed: int = DEFAULT_SEED + 6, n: int = 1 << 20, m: int = 1 << 2
     data = pack_xyz(xy, z)
     return {"data": data, "queries": uniform_xy(rng, m), "radius": local_radius(n, members),
             "p": 2.0}
+
+
+# Positions of the dominant point inside its 64-point block, one per query of
+# ``dominant_first``: chunk starts and ends, odd offsets, and both halves.
+DOMINANT_POSITIONS = (0, 1, 2, 3, 5, 7, 8, 15, 16, 17, 24, 31, 32, 33, 40, 47, 48, 56, 62, 63)
+
+
+def dominant_first(ratio: float = 0.45, positions=DOMINANT_POSITIONS, d0: float = 2.0 ** -20):
+    """An input built to defeat long sequential sums (not drawn at random).
+
+    Query j sits at the centre of its own unit cell; data block j (indices
+    64 j ... 64 j + 63) holds one point at distance d0 from it (index
+    64 j + positions[j], z = +1) and 63 points on a circle of radius
+    R = d0 2^12 / sqrt(ratio) around it (z = -1).  At p = 2 each circle
+    point's weight is ``ratio`` 2^-24 times the near point's, below half an
+    ulp of it for ratio < 1/2, so a running FP32 sum that starts at the near
+    point's weight rounds every one of them away.  The true Z_j is about
+    1 - 4 * 63 * ratio * 2^-24; blocks of the other queries lie a unit or
+    more away and weigh about 2^-30 of the near point or less.
+
+    Returns dict(data=(64 m, 3) f32, queries=(m, 2) f32, positions).
+    """
+    m = len(positions)
+    g = int(np.ceil(np.sqrt(m)))
+    R = d0 * 4096.0 / np.sqrt(ratio)
+    data = np.zeros((64 * m, 3), np.float32)
+    queries = np.zeros((m, 2), np.float32)
+    ang = 2.0 * np.pi * (np.arange(63) + 0.5) / 63.0
+    for j, pos in enumerate(positions):
+        c = np.array([j % g + 0.5, j // g + 0.5])  # multiples of 2^-1: d0 offsets stay exact
+        queries[j] = c
+        ring = np.stack([c[0] + R * np.cos(ang), c[1] + R * np.sin(ang)], 1)
+        block = np.empty((64, 3))
+        others = [i for i in range(64) if i != pos]
+        block[others, :2] = ring
+        block[others, 2] = -1.0
+        block[pos] = (c[0] + d0, c[1], 1.0)
+        data[64 * j:64 * j + 64] = block
+    return {"data": np.ascontiguousarray(data), "queries": np.ascontiguousarray(queries),
+            "positions": tuple(positions)}
