@@ -104,14 +104,14 @@ __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
     const float la = fminf(lg2_approx(a), 1048576.f);
     const float lb = fminf(lg2_approx(b), 1048576.f);
     const u64 L = pk(la, lb);
-    const u64 th = mul2(L, neg_half_p2);       // t = -(p/2) L, rounded
-    const u64 nth = mul2(L, half_p2);          // -t exactly
-    const u64 tl = fma2(L, neg_half_p2, nth);  // exact rounding error of t
+    const u64 th = mul2(L, neg_half_p2);  // t_hi = fl(t), t = -(p/2) L
+    // (p/2) L + t_hi = -(t - t_hi): the product's rounding error, exact.
+    const u64 ntl = fma2(L, half_p2, th);
     float ta, tb;
     upk(th, ta, tb);
     const u64 e = pk(ex2_approx(ta), ex2_approx(tb));
-    const u64 c = mul2(tl, pk(0.6931471805599453f, 0.6931471805599453f));
-    return fma2(e, c, e);  // 2^(th + tl) to first order in tl
+    const u64 c = mul2(ntl, pk(-0.6931471805599453f, -0.6931471805599453f));  // t_lo ln 2
+    return fma2(e, c, e);  // 2^(t_hi + t_lo) to first order in t_lo
   }
 }
 
