@@ -79,6 +79,15 @@ __device__ __forceinline__ void two_sum_acc(u64& hi, u64& lo, u64 c) {
   hi = s;
 }
 
+// Scalar TwoSum fold: hi + lo gains exactly c up to the rounding of lo + e.
+__device__ __forceinline__ void two_sum_acc_f32(float& hi, float& lo, float c) {
+  const float s = __fadd_rn(hi, c);
+  const float bv = __fsub_rn(s, hi);
+  const float av = __fsub_rn(s, bv);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, av), __fsub_rn(c, bv)));
+  hi = s;
+}
+
 // Renormalises a (hi, lo) pair with TwoSum: afterwards hi = fl(hi + lo) and
 // lo is its exact remainder, so |lo| <= ulp(hi) / 2.  Keeping lo that small
 // keeps the rounding of later `lo += e` steps second order in u.

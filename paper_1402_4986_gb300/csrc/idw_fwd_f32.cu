@@ -2,7 +2,8 @@
 // for one problem or a batch of independent problems in one launch.
 //
 // Pipeline (one call): coordinate range scan -> staging -> persistent
-// all-pairs sweep -> FP64 combine -> FP64 slow path for flagged queries.
+// all-pairs sweep -> combine (FP64 division) with the FP64 slow path of
+// flagged queries.
 //
 // The sweep is the paper's tiled kernel (Sec. 4.2: the data are read once
 // per block of prediction points, tile by tile) rebuilt for sm_103a:
@@ -28,8 +29,9 @@
 //     number of roundings per term, independent of n;
 //   * the (problem, query tile, data tile) work units are split evenly over
 //     a grid of co-resident CTAs (stream-K).  Pieces of a query tile are
-//     summed in FP64 by the combine, which plays the role of the paper's
-//     in-block reduction of the improved CDP kernel (Sec. 3.1).
+//     summed as compensated FP32 pairs by the combine, which converts each
+//     query's sums to FP64 once for the division; it plays the role of the
+//     paper's in-block reduction of the improved CDP kernel (Sec. 3.1).
 //   * coordinates are multiplied by a power of two per problem (exact in
 //     FP32) so the largest magnitude lies in [2^9, 2^10): Eq. 1 depends only
 //     on distance ratios, so Z is unchanged, and products of squared
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
     combine_kernel(const __grid_constant__ Table<CAP> t, const float4* __restrict__ partial,
                    int64_t total_slots, int64_t units, int grid, const float* __restrict__ scales,
                    double p, Control* __restrict__ ctrl) {
-  __shared__ double red0[kCombineLanes][kCombineQueries], red1[kCombineLanes][kCombineQueries];
+  __shared__ float4 red[kCombineLanes][kCombineQueries];
   __shared__ int2 flagged[kCombineQueries];
   __shared__ int nflagged;
   const int lx = threadIdx.x % kCombineQueries, ly = threadIdx.x / kCombineQueries;
@@ -370,29 +372,37 @@ __global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
   const int64_t qt = qtg - I.qtile_base;
   const int64_t j = qt * QT + lq;
   valid = valid && j < I.m;
-  double s0 = 0.0, s1 = 0.0;
+  // Each piece is an (S0 hi, S0 lo, S1 hi, S1 lo) record with |lo| at most
+  // half an ulp of hi.  Pieces are added as FP32 (hi, lo) pairs, the hi parts
+  // by TwoSum and the lo parts and the TwoSum errors plainly (the loss is of
+  // order P^2 u^2 for P pieces): the FP32 pipe runs this at 64 times the FP64
+  // pipe's rate.  The sums go to FP64 once, for the division.
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
   if (valid) {
     const int64_t g0 = cta_of_unit(I.unit_base + qt * I.data_tiles, units, grid);
     const int64_t g1 = cta_of_unit(I.unit_base + (qt + 1) * I.data_tiles - 1, units, grid);
 #pragma unroll 4
     for (int64_t g = g0 + ly; g <= g1; g += kCombineLanes) {
       const float4 v = partial[(qtg + g) * QT + lq];
-      s0 += double(v.x) + double(v.y);
-      s1 += double(v.z) + double(v.w);
+      two_sum_acc_f32(h0, l0, v.x);
+      l0 += v.y;
+      two_sum_acc_f32(h1, l1, v.z);
+      l1 += v.w;
     }
   }
-  red0[ly][lx] = s0;
-  red1[ly][lx] = s1;
+  red[ly][lx] = make_float4(h0, l0, h1, l1);
   if (threadIdx.x == 0) nflagged = 0;
   __syncthreads();
   if (ly == 0 && valid) {
-    s0 = red0[0][lx];
-    s1 = red1[0][lx];
 #pragma unroll
     for (int y = 1; y < kCombineLanes; ++y) {
-      s0 += red0[y][lx];
-      s1 += red1[y][lx];
+      const float4 r = red[y][lx];
+      two_sum_acc_f32(h0, l0, r.x);
+      l0 += r.y;
+      two_sum_acc_f32(h1, l1, r.z);
+      l1 += r.w;
     }
+    const double s0 = double(h0) + double(l0), s1 = double(h1) + double(l1);
     if (!(s0 > kTinySumPerPoint * double(I.n)) || !isfinite(s0) || !isfinite(s1) ||
         (p >= 2.0 && s0 > kHugeSumPow2Up)) {
       flagged[atomicAdd(&nflagged, 1)] = make_int2(k, static_cast<int>(j));
