@@ -1045,6 +1045,18 @@ def run_knn(args):
         rows.append({"data": "clustered" if clustered else "uniform", "call": "backward",
                      "n": n, "m": m, "k": k, "p": 2.0, "ms": bms, "queries_s": m / (bms / 1e3),
                      "grad_q_error_vs_fp64_oracle": gerr, "error_sample_queries": len(idx)})
+        # The deterministic mode: selections sorted by point, fixed-order sums.
+        hd = idw.Handle(torch.cuda.current_device())
+        idw.set_option("deterministic", 1, handle=hd)
+        dms = _events_ms(lambda: idw.knn_backward(d, q, 2.0, k, gout, handle=hd), 10, warm=3)
+        r1 = idw.knn_backward(d, q, 2.0, k, gout, handle=hd)
+        r1 = [t.clone() for t in r1]
+        r2 = idw.knn_backward(d, q, 2.0, k, gout, handle=hd)
+        hd.close()
+        rows.append({"data": "clustered" if clustered else "uniform",
+                     "call": "backward (deterministic)", "n": n, "m": m, "k": k, "p": 2.0,
+                     "ms": dms, "queries_s": m / (dms / 1e3), "vs_atomic_backward": dms / bms,
+                     "bitwise_repeatable": all(bool(torch.equal(a, b)) for a, b in zip(r1, r2))})
         build_ms = _events_ms(lambda: idw.LocalIndex(d, k=k).close(), 3, warm=1)
         ix = idw.LocalIndex(d, k=k)
         ms = _events_ms(lambda: ix.knn(q, 2.0, k, out=out), 10, warm=3)

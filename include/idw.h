@@ -258,6 +258,18 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *                               same either way.  idw_local_backward always
  *                               sorts (its data-side pass finds queries by
  *                               cell).
+ *   IDW_OPT_DETERMINISTIC       0 (default) or 1.  idw_knn_backward adds the
+ *                               data-side terms (dL/dz, dL/dx) with float
+ *                               atomics, whose order, and so the last bits,
+ *                               can vary between calls.  1 makes repeated
+ *                               calls on the same inputs bit-identical:
+ *                               neighbour rows in key order; the
+ *                               (point, query) selections sorted by point
+ *                               with a stable radix sort, so each point's
+ *                               terms are summed in increasing query order;
+ *                               dL/dp summed over queries in index order.  It
+ *                               needs m k < 2^31 (else IDW_ERR_UNSUPPORTED)
+ *                               and about 40 m k more workspace bytes.
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -270,7 +282,8 @@ typedef enum {
     IDW_OPT_TUNED_CLASSES = 5,
     IDW_OPT_STAGING_LAYOUT = 6,
     IDW_OPT_VALIDATE_INPUTS = 7,
-    IDW_OPT_LOCAL_QUERY_ORDER = 8
+    IDW_OPT_LOCAL_QUERY_ORDER = 8,
+    IDW_OPT_DETERMINISTIC = 9
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

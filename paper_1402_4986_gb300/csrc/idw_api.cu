@@ -38,6 +38,7 @@ struct idw_handle_s {
   int opt_autotune = 0, opt_variant = -1, opt_force_general = 0, opt_layout = -1;
   int opt_validate = 0;         // scan inputs for NaN / inf before computing
   int opt_query_order = 0;      // local forms: 1 keeps the caller's query order
+  bool opt_deterministic = false;  // k-NN gradients summed in a fixed order
   unsigned* vflag = nullptr;    // device word the scan sets
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
@@ -790,12 +791,14 @@ idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const 
   }
   st = validate_inputs(h, {{data, 3 * n, false}, {queries, 2 * m, false}, {grad_out, m, false}}, s);
   if (st != IDW_OK) return st;
+  const bool det = h->opt_deterministic;
+  if (det && m * int64_t(k) >= (int64_t(1) << 31)) return IDW_ERR_UNSUPPORTED;
   const idw::LocalLayout L = idw::local_layout(n, m, idw::local_max_cells(n));
-  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::knn_grad_scratch_bytes(n, m, k));
+  st = ensure_buffer(h, &h->ws, &h->ws_bytes, L.bytes + idw::knn_grad_scratch_bytes(n, m, k, det));
   if (st != IDW_OK) return st;
   e = idw::launch_knn_backward(data, n, queries, m, p, k, grad_out, grad_z, grad_data_xy,
                                grad_query_xy, grad_p, h->ws, L, h->sm_count, s,
-                               h->opt_query_order == 0);
+                               h->opt_query_order == 0, det);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -926,6 +929,10 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
       if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
       h->opt_query_order = static_cast<int>(value);
       return IDW_OK;
+    case IDW_OPT_DETERMINISTIC:
+      if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
+      h->opt_deterministic = value != 0;
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -942,6 +949,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_STAGING_LAYOUT: *value = h->opt_layout; return IDW_OK;
     case IDW_OPT_VALIDATE_INPUTS: *value = h->opt_validate; return IDW_OK;
     case IDW_OPT_LOCAL_QUERY_ORDER: *value = h->opt_query_order; return IDW_OK;
+    case IDW_OPT_DETERMINISTIC: *value = h->opt_deterministic; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

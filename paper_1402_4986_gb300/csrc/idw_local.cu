@@ -50,6 +50,7 @@
 #include "idw_device.cuh"
 #include "idw_internal.h"
 #include "idw_local.h"
+#include "idw_sort.cuh"
 
 namespace idw {
 namespace {
@@ -1382,6 +1383,7 @@ __global__ void __maxnreg__(64)
 struct KnnGradF64 {
   float gqx, gqy;
   double gp;
+  double Z, c, dmin;  // what the pair terms are computed from
 };
 __device__ __noinline__ KnnGradF64 knn_grad_query_f64(const int32_t* __restrict__ row, int cnt,
                                                       const float* __restrict__ data, float qx,
@@ -1420,8 +1422,21 @@ __device__ __noinline__ KnnGradF64 knn_grad_query_f64(const int32_t* __restrict_
   r.gqx = static_cast<float>(-c * p * ax);
   r.gqy = static_cast<float>(-c * p * ay);
   r.gp = -0.5 * c * al;
+  r.Z = Z;
+  r.c = c;
+  r.dmin = dmin;
   return r;
 }
+
+// Per-query state of a deterministic k-NN gradient: the data-side pass
+// recomputes each (point, query) term from it, point by point.
+enum KnnQMode : int { kKnnQNone = 0, kKnnQF32 = 1, kKnnQF64 = 2, kKnnQHit = 3 };
+struct KnnQState {
+  double Z, c, d2min;  // FP32 path: exact widenings of its float values
+  float lmin;          // log2 d2min (general p, FP32 path)
+  int mode;            // KnnQMode
+};
+static_assert(sizeof(KnnQState) == 32, "query state layout");
 
 template <int MODE>
 __global__ void __launch_bounds__(kLocalThreads)
@@ -1429,7 +1444,10 @@ __global__ void __launch_bounds__(kLocalThreads)
                     int64_t n, const int32_t* __restrict__ nbr, const int32_t* __restrict__ hit,
                     int k, double p, const float* __restrict__ grad_out,
                     float4* __restrict__ acc, float* __restrict__ grad_q,
-                    double* __restrict__ grad_p) {
+                    double* __restrict__ grad_p, KnnQState* __restrict__ qstate,
+                    double* __restrict__ gp_query) {
+  // qstate (deterministic mode): each query's state is recorded for the
+  // point-major pass, acc is null, and dL/dp goes per query to gp_query.
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double gp = 0.0;  // every lane joins the warp sum
   if (t < m) {
@@ -1443,8 +1461,10 @@ __global__ void __launch_bounds__(kLocalThreads)
       int cnt = 0;
       while (cnt < k && row[cnt] >= 0) ++cnt;
       float gqx = 0.f, gqy = 0.f;
+      KnnQState qs{0.0, 0.0, 0.0, 0.f, kKnnQNone};
       if (h >= 0) {
         if (acc && dcheck(h < n, kSiteData)) atomicAdd(&acc[h], make_float4(gj, 0.f, 0.f, 0.f));
+        qs.mode = kKnnQHit;
       } else if (cnt > 0) {
         const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
         // One pass: d2_min and the sums with weights scaled by the smallest
@@ -1495,6 +1515,7 @@ __global__ void __launch_bounds__(kLocalThreads)
             gqy = -c * pf * ay;
             const float gpf = (-0.5f * 0.6931471805599453f) * c * al;
             gp = gpf;
+            qs = KnnQState{double(Z), double(c), double(d2min), lmin, kKnnQF32};
           }
         }
         if (!f32) {
@@ -1503,17 +1524,140 @@ __global__ void __launch_bounds__(kLocalThreads)
           gqx = r64.gqx;
           gqy = r64.gqy;
           gp = r64.gp;
+          qs = KnnQState{r64.Z, r64.c, r64.dmin, 0.f, kKnnQF64};
         }
       }
       if (grad_q) {
         grad_q[2 * int64_t(j)] = gqx;
         grad_q[2 * int64_t(j) + 1] = gqy;
       }
+      if (qstate) qstate[j] = qs;
+      if (gp_query) gp_query[j] = gp;
     }
   }
-  if (grad_p) {
+  if (grad_p && !gp_query) {
     gp = warp_sum(gp);
     if ((threadIdx.x & 31) == 0 && gp != 0.0) atomicAdd(grad_p, gp);
+  }
+}
+
+// ----------------------------------------- deterministic k-NN gradients
+//
+// Point-major data-side terms in a fixed order: every (point, query)
+// selection becomes a key/value pair (point index, query index), listed
+// query-major; a stable radix sort by point keeps each point's queries in
+// increasing order; one warp per point then recomputes its terms from the
+// queries' states and sums them lane-strided and by a fixed shuffle tree.
+// dL/dp is summed over queries in index order by a fixed two-level tree.
+// Nothing depends on the order in which threads or atomics ran, so two calls
+// on the same inputs give the same bits.
+
+// Pair (x = j k + s): key = the selected point (the hit index for slot 0 of
+// a hit query), or n for an empty slot; value = j.
+__global__ void __launch_bounds__(256)
+    knn_pairs_kernel(const int32_t* __restrict__ nbr, const int32_t* __restrict__ hit,
+                     const KnnQState* __restrict__ qstate, int64_t m, int k, int64_t n,
+                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (x >= m * k) return;
+  const int64_t j = x / k;
+  const int sl = static_cast<int>(x - j * k);
+  const int mode = qstate[j].mode;
+  int64_t key = n;
+  if (mode == kKnnQHit) {
+    if (sl == 0 && dcheck(hit[j] >= 0 && hit[j] < n, kSiteData)) key = hit[j];
+  } else if (mode == kKnnQF32 || mode == kKnnQF64) {
+    const int32_t i = nbr[x];
+    if (i >= 0 && dcheck(i < n, kSiteData)) key = i;
+  }
+  keys[x] = static_cast<uint32_t>(key);
+  vals[x] = static_cast<uint32_t>(j);
+}
+
+// First and one-past-last position of each point's run of sorted keys (the
+// caller zeroes both arrays: a point no query selected has an empty run).
+__global__ void __launch_bounds__(256)
+    knn_runs_kernel(const uint32_t* __restrict__ keys, int64_t count, int64_t n,
+                    int32_t* __restrict__ first, int32_t* __restrict__ last) {
+  const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (x >= count) return;
+  const uint32_t key = keys[x];
+  if (key >= n) return;
+  if (x == 0 || keys[x - 1] != key) first[key] = static_cast<int32_t>(x);
+  if (x == count - 1 || keys[x + 1] != key) last[key] = static_cast<int32_t>(x + 1);
+}
+
+// One warp per data point: its terms (dL/dz, dL/dx, dL/dy), query by query
+// in increasing query order, recomputed as the query-major kernel computes
+// them.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+    knn_point_grad_kernel(const int32_t* __restrict__ first, const int32_t* __restrict__ last,
+                          const uint32_t* __restrict__ qidx, const KnnQState* __restrict__ qstate,
+                          const float* __restrict__ queries, const float* __restrict__ data,
+                          int64_t n, double p, const float* __restrict__ grad_out,
+                          float* __restrict__ grad_z, float* __restrict__ grad_xy) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps
+  const float x0 = data[3 * i], y0 = data[3 * i + 1], zi = data[3 * i + 2];
+  const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+  float gz = 0.f, gx = 0.f, gy = 0.f;
+  const int a = first[i], b = last[i];
+  for (int q = a + lane; q < b; q += 32) {
+    const int64_t j = qidx[q];
+    const KnnQState st = qstate[j];
+    const float gj = grad_out[j];
+    const float qx = queries[2 * j], qy = queries[2 * j + 1];
+    if (st.mode == kKnnQHit) {
+      gz += gj;
+    } else if (st.mode == kKnnQF32) {
+      const float Z = static_cast<float>(st.Z), c = static_cast<float>(st.c);
+      const float d2min = static_cast<float>(st.d2min);
+      const float dx = __fsub_rn(qx, x0), dy = __fsub_rn(qy, y0);
+      const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+      const float w = grad_weight<MODE>(d2, d2min, st.lmin, hp);
+      const float ar = (zi - Z) * w * rcp_approx(d2);
+      const float bb = c * pf * ar;
+      gz += c * w;
+      gx += bb * dx;
+      gy += bb * dy;
+    } else if (st.mode == kKnnQF64) {
+      const double ex = double(qx) - x0, ey = double(qy) - y0, e2 = ex * ex + ey * ey;
+      const double w = pow(st.d2min / e2, 0.5 * p);
+      const double av = (double(zi) - st.Z) * w;
+      gz += static_cast<float>(st.c * w);
+      gx += static_cast<float>(st.c * p * av * ex / e2);
+      gy += static_cast<float>(st.c * p * av * ey / e2);
+    }
+  }
+  gz = warp_sum(gz);
+  gx = warp_sum(gx);
+  gy = warp_sum(gy);
+  if (lane == 0) {
+    if (grad_z) grad_z[i] = gz;
+    if (grad_xy) reinterpret_cast<float2*>(grad_xy)[i] = make_float2(gx, gy);
+  }
+}
+
+// Fixed-order sum of v[0 .. count): CTA b sums its contiguous slice (thread
+// t takes every 256th value from t, then a fixed shuffle and shared-memory
+// tree), then one CTA sums the CTA totals the same way.
+constexpr int kDetSumCtas = 256;
+__global__ void __launch_bounds__(256)
+    fixed_sum_kernel(const double* __restrict__ v, int64_t count, double* __restrict__ out) {
+  __shared__ double part[8];
+  const int64_t per = (count + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = int64_t(blockIdx.x) * per, hi = min(count, lo + per);
+  double acc = 0.0;
+  for (int64_t x = lo + threadIdx.x; x < hi; x += blockDim.x) acc += v[x];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < 8; ++w) tot += part[w];
+    out[blockIdx.x] = tot;
   }
 }
 
@@ -1693,23 +1837,101 @@ cudaError_t launch_local_backward(const float* data, int64_t n, const float* que
   return cudaGetLastError();
 }
 
-size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k) {
-  return round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(m) * size_t(k) * 4, 256) +
-         round_up(size_t(n) * 16, 256);
+size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k, bool deterministic) {
+  size_t b = round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(m) * size_t(k) * 4, 256) +
+             round_up(size_t(n) * 16, 256);
+  if (deterministic) {
+    const int64_t pairs = m * int64_t(k);
+    b += 2 * round_up(size_t(pairs) * 4, 256) + radix_sort_scratch_bytes(pairs) +
+         2 * round_up(size_t(n) * 4, 256) + round_up(size_t(m) * sizeof(KnnQState), 256) +
+         round_up(size_t(m) * 8, 256) + round_up(size_t(kDetSumCtas) * 8, 256);
+  }
+  return b;
 }
+
+namespace {
+// The deterministic k-NN gradient after the search (rows sorted by key):
+// query-major kernel without atomics (states, dL/dq, per-query dL/dp), the
+// pair list, its stable sort by point, the runs, the point-major kernel and
+// the fixed-order dL/dp sum.
+cudaError_t launch_knn_backward_fixed_order(const float* data, int64_t n, const float* queries,
+                                            int64_t m, double p, int k, const float* grad_out,
+                                            float* grad_z, float* grad_xy, float* grad_q,
+                                            double* grad_p, unsigned char* ws,
+                                            const LocalLayout& L, const int32_t* hit,
+                                            const int32_t* nbr, cudaStream_t s) {
+  const int64_t pairs = m * int64_t(k);
+  size_t off = L.bytes + round_up(size_t(m) * 4, 256) * 2 + round_up(size_t(pairs) * 4, 256) +
+               round_up(size_t(n) * 16, 256);
+  auto take = [&](size_t bytes) {
+    unsigned char* ptr = ws + off;
+    off += round_up(bytes, 256);
+    return ptr;
+  };
+  uint32_t* keys = reinterpret_cast<uint32_t*>(take(size_t(pairs) * 4));
+  uint32_t* vals = reinterpret_cast<uint32_t*>(take(size_t(pairs) * 4));
+  void* sort_scratch = take(radix_sort_scratch_bytes(pairs));
+  int32_t* first = reinterpret_cast<int32_t*>(take(size_t(n) * 4));
+  int32_t* last = reinterpret_cast<int32_t*>(take(size_t(n) * 4));
+  KnnQState* qstate = reinterpret_cast<KnnQState*>(take(size_t(m) * sizeof(KnnQState)));
+  double* gpq = reinterpret_cast<double*>(take(size_t(m) * 8));
+  double* gpart = reinterpret_cast<double*>(take(size_t(kDetSumCtas) * 8));
+
+  const float4* qrec = reinterpret_cast<const float4*>(ws + L.off_qrec);
+  const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
+  if (p == 2.0)
+    knn_grad_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k, p,
+                                                           grad_out, nullptr, grad_q, grad_p,
+                                                           qstate, gpq);
+  else
+    knn_grad_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k,
+                                                                 p, grad_out, nullptr, grad_q,
+                                                                 grad_p, qstate, gpq);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (grad_p) {
+    fixed_sum_kernel<<<kDetSumCtas, 256, 0, s>>>(gpq, m, gpart);
+    fixed_sum_kernel<<<1, 256, 0, s>>>(gpart, kDetSumCtas, grad_p);
+  }
+  if (!grad_z && !grad_xy) return cudaGetLastError();
+  knn_pairs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(
+      nbr, hit, qstate, m, k, n, keys, vals);
+  int bits = 1;
+  while (bits < 32 && (uint64_t(1) << bits) <= uint64_t(n)) ++bits;  // keys in [0, n]
+  if ((e = radix_sort_pairs(keys, vals, pairs, bits, sort_scratch, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(first, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(last, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
+  knn_runs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(keys, pairs, n, first,
+                                                                             last);
+  const unsigned pgrid = static_cast<unsigned>((n * 32 + 255) / 256);
+  if (p == 2.0)
+    knn_point_grad_kernel<kPow2><<<pgrid, 256, 0, s>>>(first, last, vals, qstate, queries, data,
+                                                       n, p, grad_out, grad_z, grad_xy);
+  else
+    knn_point_grad_kernel<kPowGeneral><<<pgrid, 256, 0, s>>>(first, last, vals, qstate, queries,
+                                                             data, n, p, grad_out, grad_z,
+                                                             grad_xy);
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
                                 const LocalLayout& L, int sm_count, cudaStream_t s,
-                                bool sort_queries) {
+                                bool sort_queries, bool deterministic) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   float* zbuf = reinterpret_cast<float*>(ws + L.bytes);
   int32_t* hit = reinterpret_cast<int32_t*>(ws + L.bytes + round_up(size_t(m) * 4, 256));
   int32_t* nbr = reinterpret_cast<int32_t*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256));
+  // Deterministic mode: rows in key order, so each query's own sums run in
+  // one fixed order too.
   cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
-                             s, hit, sort_queries, false);
+                             s, hit, sort_queries, deterministic);
   if (e != cudaSuccess) return e;
+  if (deterministic)
+    return launch_knn_backward_fixed_order(data, n, queries, m, p, k, grad_out, grad_z, grad_xy,
+                                           grad_q, grad_p, ws, L, hit, nbr, s);
   const bool data_side = grad_z || grad_xy;
   float4* acc = data_side ? reinterpret_cast<float4*>(ws + L.bytes + 2 * round_up(size_t(m) * 4, 256) +
                                                       round_up(size_t(m) * size_t(k) * 4, 256))
@@ -1720,10 +1942,12 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
   const unsigned qgrid = static_cast<unsigned>((m + kLocalThreads - 1) / kLocalThreads);
   if (p == 2.0)
     knn_grad_kernel<kPow2><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k, p,
-                                                           grad_out, acc, grad_q, grad_p);
+                                                           grad_out, acc, grad_q, grad_p,
+                                                           nullptr, nullptr);
   else
     knn_grad_kernel<kPowGeneral><<<qgrid, kLocalThreads, 0, s>>>(qrec, m, data, n, nbr, hit, k,
-                                                                 p, grad_out, acc, grad_q, grad_p);
+                                                                 p, grad_out, acc, grad_q, grad_p,
+                                                                 nullptr, nullptr);
   if (acc)
     knn_grad_copy_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(acc, n, grad_z,
                                                                                grad_xy);

@@ -62,12 +62,15 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
 // neighbour lists and hits kept in the workspace after L.bytes (plus
 // knn_grad_scratch_bytes(n, m, k)), then one kernel per query that adds the
 // data-side terms with atomics.  Outputs as launch_local_backward.
-size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k);
+// With `deterministic`, the data-side terms are summed point by point in
+// increasing query order (a stable sort of the selections by point) and
+// dL/dp over queries in index order, so repeated calls give the same bits.
+size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k, bool deterministic = false);
 cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queries, int64_t m,
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
                                 const LocalLayout& L, int sm_count, cudaStream_t s,
-                                bool sort_queries = true);
+                                bool sort_queries = true, bool deterministic = false);
 
 // A prepared index: the data side of a local form built once and queried
 // by many calls.  The index's own buffer holds the plan, the data cell

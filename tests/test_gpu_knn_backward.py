@@ -139,3 +139,64 @@ def test_full_size_sampled_and_sum_rules(idw):
     assert abs(float(gz.double().sum()) - want) <= 1e-4 * float(np.sum(np.abs(g)))
     tot = gxy.double().sum(0) + gq.double().sum(0)
     assert float(tot.abs().max()) <= 1e-4 * float(gq.double().abs().sum(0).max())
+
+
+# ------------------------------------------------ deterministic mode
+# IDW_OPT_DETERMINISTIC: the data-side terms are summed point by point in
+# increasing query order (stable radix sort of the selections) and dL/dp over
+# queries in index order, so repeated calls give identical bits; each
+# gradient still meets the oracle bar.
+
+def _det_handle(idw):
+    h = idw.Handle(torch.cuda.current_device())
+    idw.set_option("deterministic", 1, handle=h)
+    return h
+
+
+@pytest.mark.parametrize("k,p,clustered", [(1, 2.0, False), (8, 3.5, False), (32, 2.0, False),
+                                           (64, 2.0, False), (32, 2.0, True)])
+def test_deterministic_mode_matches_oracle(idw, k, p, clustered):
+    if clustered:
+        prob = synthetic.config_local(seed=133, n=20000, m=3000, clustered=True)
+    else:
+        prob = synthetic.uniform_problem(5003, 2001, seed=141, exact_hits=7)
+    m = prob["queries"].shape[0]
+    g = np.random.default_rng(142).standard_normal(m).astype(np.float32)
+    h = _det_handle(idw)
+    gz, gxy, gq, gp = idw.knn_backward(_dev(prob["data"]), _dev(prob["queries"]), p, k, _dev(g),
+                                       handle=h)
+    torch.cuda.synchronize()
+    G = oracle.idw_knn_grad(prob["data"], prob["queries"], p, k, g)
+    assert _rel(gz.cpu().numpy(), G["grad_z"]) <= TOL
+    assert _rel(gxy.cpu().numpy(), G["grad_xy"]) <= TOL
+    assert _rel(gq.cpu().numpy(), G["grad_q"]) <= TOL
+    assert abs(float(gp.cpu()[0]) - G["grad_p"]) <= TOL * max(abs(G["grad_p"]), 1e-300)
+    h.close()
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_deterministic_mode_is_bitwise_repeatable(idw, clustered):
+    """Two calls, with other work in between that reshuffles the atomics of
+    the grid build, give bitwise-identical dL/dz, dL/dx, dL/dq and dL/dp;
+    clustered data make some points selected by thousands of queries."""
+    prob = synthetic.config_local(seed=143, n=1 << 17, m=1 << 17, clustered=clustered)
+    d, q = _dev(prob["data"]), _dev(prob["queries"])
+    g = _dev(np.random.default_rng(144).standard_normal(q.shape[0]))
+    h = _det_handle(idw)
+    first = idw.knn_backward(d, q, 2.0, 32, g, handle=h)
+    first = [t.clone() for t in first]
+    idw.interpolate_knn(d, q, 2.0, 16)  # unrelated work on the default handle
+    second = idw.knn_backward(d, q, 2.0, 32, g, handle=h)
+    torch.cuda.synchronize()
+    for a, b in zip(first, second):
+        assert torch.equal(a, b)
+    # The atomic mode agrees with it to rounding.  The two sum each point's
+    # terms in different FP32 orders; on clustered data a point collects
+    # thousands of terms of both signs, and the orders differ by up to about
+    # 1e-4 of the largest gradient (the oracle comparison of each mode is in
+    # test_deterministic_mode_matches_oracle and test_clustered).
+    atomic = idw.knn_backward(d, q, 2.0, 32, g)
+    for a, b in zip(first, atomic):
+        scale = float(b.abs().max())
+        assert float((a.double() - b.double()).abs().max()) <= 5 * TOL * max(scale, 1e-30)
+    h.close()
