@@ -445,7 +445,7 @@ def run_ours(args, ws, rank, local):
                                "FP32-compensated (FP64 combine)",
                    "n": n, "m": m, "p": 2.0, "parallelism": f"query shards x{ws}, data replicated",
                    "l2": "flushed between steps (256 MiB write; inputs are 36 MiB)"},
-        "e2e": e2e, "gpu_launches": 5 * args.steps,
+        "e2e": e2e, "gpu_launches": 4 * args.steps,
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "error_vs_fp64_oracle": err,
         **({"full_check": full} if full else {}),
@@ -496,6 +496,13 @@ def headline_extras(args, idw, h, data, q, data_np, q_np, single_pairs_s, rates,
             np.max(np.abs(o.cpu().numpy()[idx].astype(np.float64) - Z64)) /
             np.max(np.abs(data_np[:, 2])))
         gen["error_sample_queries"] = len(idx)
+    # The same sweep with one log2 in 16 on the FMA pipe (IDW_OPT_FMA_LOG2).
+    hf = idw.Handle(torch.cuda.current_device())
+    idw.set_option("fma_log2", 1, handle=hf)
+    fms = _events_ms(lambda: idw.interpolate(data, q, p, out=o, handle=hf), 3)
+    hf.close()
+    gen["fma_log2_1_in_16"] = {"pairs_s": pairs / (fms / 1e3), "call_ms": fms,
+                               "vs_mufu_lg2": ms / fms}
     out["general_p"] = gen
     # Batched: 256 uneven problems, one persistent launch.
     batch = synthetic.config_batch()
@@ -558,13 +565,15 @@ def _events_ms(fn, reps, warm=1):
 
 
 def _timed_with_sweep(idw, h, fn, reps, warm=1):
-    """(call ms, sweep-kernel ms) per call, both averaged over ``reps`` calls
-    on handle ``h`` (the library records CUDA events around each sweep)."""
-    for _ in range(warm):
-        fn()
+    """(call ms, sweep-kernel ms) per call, each averaged over ``reps`` calls
+    on handle ``h``: the calls timed as a user runs them, then the sweep
+    alone from the CUDA events the library records around it when profiling
+    is on (which launches the sweep without programmatic dependent launch,
+    so the call time is taken with profiling off)."""
+    ms = _events_ms(fn, reps, warm=warm)
     idw.profile_read(handle=h)
     idw.profile_enable(True, handle=h)
-    ms = _events_ms(fn, reps, warm=0)
+    _events_ms(fn, reps, warm=0)
     idw.profile_enable(False, handle=h)
     sweep_ms, launches = idw.profile_read(handle=h)
     return ms, sweep_ms / max(1, launches)

@@ -270,6 +270,16 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *                               dL/dp summed over queries in index order.  It
  *                               needs m k < 2^31 (else IDW_ERR_UNSUPPORTED)
  *                               and about 40 m k more workspace bytes.
+ *   IDW_OPT_FMA_LOG2            0 (default) or 1.  The general-power form
+ *                               (p != 2, one problem) takes log2 d^2 of one
+ *                               pair in 16 from a degree-8 minimax polynomial
+ *                               on the FMA pipe instead of the MUFU pipe
+ *                               (error at most 1.5u absolute on [1/2, 2] and
+ *                               1.5u relative elsewhere, below lg2.approx's).
+ *                               It runs sweep variant 4.  Measured slower on
+ *                               GB300 than the MUFU path at every fraction
+ *                               from 1/16 to 1/4, so it stays off; it exists
+ *                               to balance the pipes where that trade wins.
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -283,7 +293,8 @@ typedef enum {
     IDW_OPT_STAGING_LAYOUT = 6,
     IDW_OPT_VALIDATE_INPUTS = 7,
     IDW_OPT_LOCAL_QUERY_ORDER = 8,
-    IDW_OPT_DETERMINISTIC = 9
+    IDW_OPT_DETERMINISTIC = 9,
+    IDW_OPT_FMA_LOG2 = 10
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

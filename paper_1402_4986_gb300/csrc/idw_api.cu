@@ -39,6 +39,7 @@ struct idw_handle_s {
   int opt_validate = 0;         // scan inputs for NaN / inf before computing
   int opt_query_order = 0;      // local forms: 1 keeps the caller's query order
   bool opt_deterministic = false;  // k-NN gradients summed in a fixed order
+  bool opt_fma_log2 = false;       // general p: part of log2 on the FMA pipe
   unsigned* vflag = nullptr;    // device word the scan sets
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
@@ -498,11 +499,13 @@ idw_status idw_interpolate_saved(idw_handle_t h, const void* data, int64_t n, co
   if (prec == IDW_PREC_F32_COMP) {
     idw::F32Problem pb{static_cast<const float*>(data), n, static_cast<const float*>(queries), m,
                        static_cast<float*>(out), s0_out, hit_out};
-    const int v = choose_variant(h, &pb, 1, p, s);
+    const bool fma_log2 = h->opt_fma_log2 && uses_general_power(h, p);
+    const int v = fma_log2 ? 4 : choose_variant(h, &pb, 1, p, s);
     idw::BatchPlan bp;
     idw::plan_batch_f32(&pb, 1, h->sm_count, ctas_per_sm(h, prec, p, v), v, &bp);
     bp.force_general = h->opt_force_general != 0;
     bp.layout = v == 0 ? h->opt_layout : -1;
+    bp.fma_log2 = fma_log2;
     st = ensure_buffer(h, &h->ws, &h->ws_bytes, bp.workspace_bytes);
     if (st != IDW_OK) return st;
     h->last_variant = v;
@@ -933,6 +936,10 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
       if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
       h->opt_deterministic = value != 0;
       return IDW_OK;
+    case IDW_OPT_FMA_LOG2:
+      if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
+      h->opt_fma_log2 = value != 0;
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -950,6 +957,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_VALIDATE_INPUTS: *value = h->opt_validate; return IDW_OK;
     case IDW_OPT_LOCAL_QUERY_ORDER: *value = h->opt_query_order; return IDW_OK;
     case IDW_OPT_DETERMINISTIC: *value = h->opt_deterministic; return IDW_OK;
+    case IDW_OPT_FMA_LOG2: *value = h->opt_fma_log2; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

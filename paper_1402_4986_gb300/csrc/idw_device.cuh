@@ -118,6 +118,19 @@ __device__ __forceinline__ void tree_push(u64 (&P)[LEVELS], u64 v, int i, u64& t
   total = v;
 }
 
+// ------------------------------------------- programmatic dependent launch
+// A kernel launched with programmatic stream serialization may start before
+// the kernel ahead of it in the stream has finished.  pdl_wait() blocks
+// until every grid it depends on has completed and its memory is visible,
+// so a kernel calls it before it reads or writes anything those grids may
+// touch; without that launch attribute it returns at once.  pdl_trigger()
+// lets the next such kernel launch as soon as every CTA of this grid has
+// started (it still waits for this grid's completion in its pdl_wait()).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------- MUFU ops
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;

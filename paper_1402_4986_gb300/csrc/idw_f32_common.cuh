@@ -105,6 +105,8 @@ template <int CAP>
 __global__ void __launch_bounds__(256) range_kernel(const __grid_constant__ Table<CAP> t,
                                                     unsigned* __restrict__ maxbits) {
   __shared__ float red[8];
+  pdl_trigger();
+  pdl_wait();
   const Instance& I = t.inst[blockIdx.y];
   float mx = 0.f;
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
@@ -135,6 +137,8 @@ template <int CAP, int MODE, int LAYOUT = 0>
 __global__ void __launch_bounds__(256)
     stage_kernel(const __grid_constant__ Table<CAP> t, int64_t total_records,
                  const unsigned* __restrict__ maxbits, float* __restrict__ scales) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= total_records) return;
   const int k = find_record(t, r);

@@ -39,6 +39,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <utility>
 
 #include "idw_device.cuh"
 #include "idw_internal.h"
@@ -90,9 +91,45 @@ struct SweepArgs {
   unsigned* err;
 };
 
+// log2 on the FMA pipe, for both lanes: x = 2^k m, m in [1/sqrt 2, sqrt 2),
+// log2 x = k + s P(s), s = m - 1 (exact), P the degree-8 minimax fit of
+// log2(1 + s)/s for the relative error (Remez exchange, fit_log2.py),
+// rounded to fp32 and evaluated by Horner's rule with packed FMAs.  Zero or
+// subnormal x gives -inf and an infinite or NaN x gives 2^20, as the MUFU
+// path with its clamp does.  Error: at most 1.5u absolute for x in
+// [1/2, 2] and 1.5u relative to |log2 x| elsewhere (checked exhaustively
+// on the CPU).
+__constant__ float kLog2Poly[] = {
+    1.4426950216293335f,  -0.7213473320007324f, 0.48091062903404236f,
+    -0.3607036769390106f, 0.28791624307632446f, -0.23894482851028442f,
+    0.21571560204029083f, -0.20726972818374634f, 0.12583701312541962f,
+};
+constexpr int kLog2PolyDegree = 8;
+
+__device__ __forceinline__ u64 log2_fma_pair(u64 x2) {
+  float xa, xb;
+  upk(x2, xa, xb);
+  const int ua = __float_as_int(xa), ub = __float_as_int(xb);
+  const int ka = (ua - 0x3F3504F3) >> 23, kb = (ub - 0x3F3504F3) >> 23;  // m >= 1/sqrt 2
+  const u64 m = pk(__int_as_float(ua - (ka << 23)), __int_as_float(ub - (kb << 23)));
+  // float(k) exactly: k sits in the low mantissa bits of 1.5 2^23.
+  const u64 kf = pk(__int_as_float(0x4B400000 + ka) - 12582912.f,
+                    __int_as_float(0x4B400000 + kb) - 12582912.f);
+  const u64 sv = sub2(m, pk(1.f, 1.f));
+  u64 poly = pk(kLog2Poly[kLog2PolyDegree], kLog2Poly[kLog2PolyDegree]);
+#pragma unroll
+  for (int i = kLog2PolyDegree - 1; i >= 0; --i) poly = fma2(poly, sv, pk(kLog2Poly[i], kLog2Poly[i]));
+  float la, lb;
+  upk(fma2(sv, poly, kf), la, lb);
+  const int ea = (ua >> 23) & 0xff, eb = (ub >> 23) & 0xff;
+  la = ea == 0 ? -INFINITY : (ea == 0xff ? 1048576.f : la);
+  lb = eb == 0 ? -INFINITY : (eb == 0xff ? 1048576.f : lb);
+  return pk(la, lb);
+}
+
 template <int MODE>
 __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
-                                           u64 neg_half_p2) {
+                                           u64 neg_half_p2, bool fma_log2 = false) {
   float a, b;
   upk(d2, a, b);
   if (MODE == kPow2) {
@@ -102,10 +139,10 @@ __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
     }
     return pk(rcp_approx(a), rcp_approx(b));
   } else {
-    // L = log2 d^2, clamped so that +inf (padding) stays finite below.
-    const float la = fminf(lg2_approx(a), 1048576.f);
-    const float lb = fminf(lg2_approx(b), 1048576.f);
-    const u64 L = pk(la, lb);
+    // L = log2 d^2, clamped so that +inf (padding) stays finite below; on
+    // the MUFU pipe, or for a fixed fraction of the pairs on the FMA pipe.
+    const u64 L = fma_log2 ? log2_fma_pair(d2)
+                           : pk(fminf(lg2_approx(a), 1048576.f), fminf(lg2_approx(b), 1048576.f));
     const u64 th = mul2(L, neg_half_p2);  // t_hi = fl(t), t = -(p/2) L
     // (p/2) L + t_hi = -(t - t_hi): the product's rounding error, exact.
     const u64 ntl = fma2(L, half_p2, th);
@@ -116,6 +153,15 @@ __device__ __forceinline__ u64 weight_pair(u64 d2, bool shared_rcp, u64 half_p2,
     return fma2(e, c, e);  // 2^(t_hi + t_lo) to first order in t_lo
   }
 }
+
+// General power with the FMA-pipe log2 (IDW_OPT_FMA_LOG2): query pair 0
+// takes log2 d^2 on the FMA pipe for the data points r with
+// r % kLog2FmaPeriod == 0, 1 pair in 16.  The MUFU pipe (lg2 at 16 and ex2
+// at 32 per SM per clock) binds the general sweep while the FMA pipe is 73 %
+// busy, yet every fraction measured (1/16 to 1/4) was slower: the polynomial
+// and its exponent handling cost more issue slots than the lg2 they replace.
+// It is kept as an option, off by default.
+constexpr int kLog2FmaPeriod = 4;
 
 // The record of data point c + r of a staged tile as three register pairs
 // (x,x), (y,y), (z,z), for each staging layout.
@@ -179,7 +225,7 @@ __host__ __device__ constexpr size_t sweep_smem_of() {
   return ring_bytes_of<V, LAYOUT>() + hl_bytes_of<V>();
 }
 
-template <int MODE, int CAP, int V, int LAYOUT = 0>
+template <int MODE, int CAP, int V, int LAYOUT = 0, bool FMA_LOG2 = false>
 __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     sweep_kernel(const SweepArgs a, const __grid_constant__ Table<CAP> t) {
   constexpr int NT = Var<V>::NT, KP = Var<V>::KP, KSHARED = Var<V>::KSH, QT = qt_of<V>();
@@ -207,6 +253,8 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
     for (int s = 0; s < ST; ++s) mbar_init(smem_u32(&full_bar[s]), 1);
     fence_barrier_init();
   }
+  pdl_trigger();
+  pdl_wait();  // the staged tiles and scales come from the kernels before
   __syncthreads();
 
   // Producer (thread 0): one bulk copy per unit, STAGES units ahead.
@@ -277,7 +325,8 @@ __global__ void __launch_bounds__(Var<V>::NT, 512 / Var<V>::NT)
               const u64 dy = sub2(QY[k], yy);
               const u64 d2 = fma2(dy, dy, mul2(dx, dx));
               const bool shared = k < KSHARED || (k == KALT && (r & 1));
-              const u64 w = weight_pair<MODE>(d2, shared, hp2, nhp2);
+              const bool fma_log2 = FMA_LOG2 && k == 0 && r % kLog2FmaPeriod == 0;
+              const u64 w = weight_pair<MODE>(d2, shared, hp2, nhp2, fma_log2);
               tree_push<SH.tree_levels>(P0[k], w, r, C0[k]);
               if (r % SH.chain == 0) {
                 T1[k] = mul2(w, zz);
@@ -363,6 +412,8 @@ __global__ void __launch_bounds__(kCombineQueries * kCombineLanes)
   __shared__ float4 red[kCombineLanes][kCombineQueries];
   __shared__ int2 flagged[kCombineQueries];
   __shared__ int nflagged;
+  pdl_trigger();
+  pdl_wait();
   const int lx = threadIdx.x % kCombineQueries, ly = threadIdx.x / kCombineQueries;
   const int64_t idx = int64_t(blockIdx.x) * kCombineQueries + lx;
   bool valid = idx < total_slots;
@@ -440,6 +491,26 @@ __global__ void bounded_wait_selftest_kernel(unsigned* err) {
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Launches `kernel` allowed to start before the kernel ahead of it in the
+// stream completes (programmatic dependent launch); the kernel itself waits
+// in pdl_wait() before touching memory, so results are as with a plain
+// launch and only launch latency overlaps.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t stream, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Raises a kernel's dynamic shared memory limit to `bytes` (needed above
 // 48 KB), once per kernel and device (one flag word per instantiation).
 template <auto KERNEL>
@@ -457,7 +528,7 @@ cudaError_t allow_dynamic_smem(size_t bytes) {
   return e;
 }
 
-template <int CAP, int V, int MODE, int LAYOUT>
+template <int CAP, int V, int MODE, int LAYOUT, bool FMA_LOG2 = false>
 cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p,
                         unsigned char* ws, Control* ctrl, int sm_count, const SweepEvents* ev,
                         cudaStream_t stream) {
@@ -488,10 +559,14 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   cudaError_t e;
 
   const unsigned gx = static_cast<unsigned>(std::min<int64_t>(1024, (longest + 255) / 256));
-  range_kernel<CAP><<<dim3(gx, plan.count), 256, 0, stream>>>(t, maxbits);
+  if ((e = launch_pdl(range_kernel<CAP>, dim3(gx, plan.count), dim3(256), 0, stream, t,
+                      maxbits)) != cudaSuccess)
+    return e;
   const int64_t records = plan.total_stage_tiles * TB;
   const unsigned sgrid = static_cast<unsigned>((records + 255) / 256);
-  stage_kernel<CAP, MODE, LAYOUT><<<sgrid, 256, 0, stream>>>(t, records, maxbits, scales);
+  if ((e = launch_pdl(stage_kernel<CAP, MODE, LAYOUT>, dim3(sgrid), dim3(256), 0, stream, t,
+                      records, static_cast<const unsigned*>(maxbits), scales)) != cudaSuccess)
+    return e;
 
   SweepArgs a;
   a.units = plan.units;
@@ -502,18 +577,26 @@ cudaError_t launch_impl(const F32Problem* probs, const BatchPlan& plan, double p
   a.scales = scales;
   a.err = &ctrl->error;
   constexpr size_t smem = sweep_smem_of<V, LAYOUT>();
-  if ((e = allow_dynamic_smem<sweep_kernel<MODE, CAP, V, LAYOUT>>(smem)) != cudaSuccess) return e;
+  if ((e = allow_dynamic_smem<sweep_kernel<MODE, CAP, V, LAYOUT, FMA_LOG2>>(smem)) != cudaSuccess)
+    return e;
   if (ev && (e = cudaEventRecord(ev->start, stream)) != cudaSuccess) return e;
   constexpr int NT = Var<V>::NT, QT = qt_of<V>();
-  sweep_kernel<MODE, CAP, V, LAYOUT><<<plan.grid, NT, smem, stream>>>(a, t);
+  // With profiling events the sweep is launched plainly, so that the events
+  // around it bracket it alone.
+  if (ev)
+    sweep_kernel<MODE, CAP, V, LAYOUT, FMA_LOG2><<<plan.grid, NT, smem, stream>>>(a, t);
+  else if ((e = launch_pdl(sweep_kernel<MODE, CAP, V, LAYOUT, FMA_LOG2>, dim3(plan.grid),
+                           dim3(NT), smem, stream, a, t)) != cudaSuccess)
+    return e;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev->stop, stream)) != cudaSuccess) return e;
 
   const int64_t slots = plan.total_query_tiles * QT;
-  combine_kernel<CAP, QT><<<static_cast<unsigned>((slots + kCombineQueries - 1) / kCombineQueries),
-                            kCombineQueries * kCombineLanes, 0, stream>>>(
-      t, partial, slots, plan.units, plan.grid, scales, p, ctrl);
-  return cudaGetLastError();
+  return launch_pdl(combine_kernel<CAP, QT>,
+                    dim3(static_cast<unsigned>((slots + kCombineQueries - 1) / kCombineQueries)),
+                    dim3(kCombineQueries * kCombineLanes), 0, stream, t,
+                    static_cast<const float4*>(partial), slots, plan.units, plan.grid,
+                    static_cast<const float*>(scales), p, ctrl);
 }
 
 }  // namespace
@@ -607,6 +690,8 @@ cudaError_t launch_batch_f32(const F32Problem* probs, const BatchPlan& plan, dou
   // general p, which need no register moves.  The other layouts are built
   // for the single-problem sweep of variant 0 (the layout ablation).
   const int layout = plan.layout >= 0 ? plan.layout : (pow2 ? 1 : 0);
+  if (one && plan.variant == 4 && !pow2 && plan.fma_log2)
+    return launch_impl<1, 4, kPowGeneral, 0, true>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
   if (one && plan.variant == 0) {
     if (pow2 && layout == 0) return launch_impl<1, 0, kPow2, 0>(probs, plan, p, ws, ctrl, sm_count, ev, stream);
     if (pow2 && layout == 2) return launch_impl<1, 0, kPow2, 2>(probs, plan, p, ws, ctrl, sm_count, ev, stream);

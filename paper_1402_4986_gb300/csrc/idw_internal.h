@@ -92,6 +92,7 @@ struct BatchPlan {
   int variant = 0;
   bool force_general = false;  // evaluate p = 2 through the log2/exp2 path
   int layout = -1;             // data-tile staging layout; -1 = default for the weight form
+  bool fma_log2 = false;       // general p, one problem, variant 4: 1 log2 in 16 on the FMA pipe
   int count = 0;
   std::vector<int64_t> data_tiles, query_tiles, unit_base, qtile_base, tile_offset;
   int64_t units = 0, total_query_tiles = 0, total_stage_tiles = 0;

@@ -98,3 +98,23 @@ def test_mufu_errors_exhaustive(idw):
     assert 0.0 < e["lg2_abs"] <= 2.0 ** -21
     assert 0.0 < e["ex2_rel"] <= 2.0 ** -21
     assert 0.0 < e["lg2_rel_outer"] <= 2.0 ** -21
+
+
+@pytest.mark.parametrize("p", [0.5, 1.5, 3.5, 6.0])
+def test_fma_log2_option_matches_oracle(idw, p):
+    """IDW_OPT_FMA_LOG2: one pair in 16 takes log2 d^2 from the FMA-pipe
+    polynomial; ragged sizes (padding records), exact hits and the bar."""
+    prob = synthetic.uniform_problem(9001, 4099, seed=int(10 * p) + 150, exact_hits=5)
+    d = torch.from_numpy(prob["data"]).cuda()
+    q = torch.from_numpy(prob["queries"]).cuda()
+    h = idw.Handle(0)
+    idw.set_option("fma_log2", 1, handle=h)
+    Z = idw.interpolate(d, q, p, handle=h)
+    idw.sync_status(handle=h)
+    assert idw.get_option("last_variant", handle=h) == 4
+    Z64, _ = oracle.idw(prob["data"], prob["queries"], p)
+    e = _err(Z, Z64, prob["data"])
+    h.close()
+    assert e.max() <= TOL_F32C, e.max()
+    hq = torch.from_numpy(prob["hit_q"]).cuda()
+    assert torch.equal(Z[hq].cpu(), torch.from_numpy(prob["data"][prob["hit_d"], 2]))
