@@ -1044,6 +1044,19 @@ def run_knn(args):
                          "neighbours_match_oracle": bool(np.array_equal(
                              nbr.cpu().numpy()[idx], r["nbr"])),
                          "error_vs_fp64_oracle": err, "error_sample_queries": len(idx)})
+        # The same call with the lanes of each warp kept in step
+        # (IDW_OPT_KNN_SEARCH = 1): the same selection, another schedule.
+        hs = idw.Handle(torch.cuda.current_device())
+        idw.set_option("knn_search", 1, handle=hs)
+        sms = _events_ms(lambda: idw.interpolate_knn(d, q, 2.0, k, out=out, handle=hs), 10, warm=3)
+        _, nbs = idw.interpolate_knn(d, q, 2.0, k, neighbours=True, handle=hs)
+        _, nbr2 = idw.interpolate_knn(d, q, 2.0, k, neighbours=True)
+        hs.close()
+        rows.append({"data": "clustered" if clustered else "uniform",
+                     "call": "one-shot, lockstep search", "n": n, "m": m, "k": k, "p": 2.0,
+                     "ms": sms, "queries_s": m / (sms / 1e3),
+                     "vs_default_search": sms / rows[-2]["ms"],
+                     "neighbours_match_default_search": bool(torch.equal(nbs, nbr2))})
         gout = torch.from_numpy(np.random.default_rng(8).standard_normal(m).astype(np.float32)).cuda()
         bms = _events_ms(lambda: idw.knn_backward(d, q, 2.0, k, gout), 10, warm=3)
         _, _, gq, _ = idw.knn_backward(d, q, 2.0, k, gout)

@@ -280,6 +280,19 @@ idw_status idw_plan_forward(int32_t sm_count, int32_t ctas_per_sm, int64_t n, in
  *                               GB300 than the MUFU path at every fraction
  *                               from 1/16 to 1/4, so it stays off; it exists
  *                               to balance the pipes where that trade wins.
+ *   IDW_OPT_KNN_SEARCH          0 (default) or 1.  The k-NN search of
+ *                               idw_interpolate_knn and idw_knn_backward: 0
+ *                               one thread per query, each growing its own
+ *                               square of cells at its own pace; 1 the same
+ *                               per-query search with the 32 lanes of a warp
+ *                               kept in step (the same step and row order,
+ *                               each lane's row runs walked as one stream,
+ *                               heap inserts merged by the warp together).
+ *                               The selection, and so the result, is the
+ *                               same.  1 keeps more lanes busy but spends
+ *                               as many instructions on keeping them in
+ *                               step, and is slower at k >= 32 and on
+ *                               clustered data.  Prepared indexes use 0.
  *   IDW_OPT_LAST_VARIANT        read-only: the variant of the last call.
  *   IDW_OPT_TUNED_CLASSES       read-only: size classes tuned so far.
  * Unknown options or out-of-range values give IDW_ERR_INVALID_ARG.
@@ -294,7 +307,8 @@ typedef enum {
     IDW_OPT_VALIDATE_INPUTS = 7,
     IDW_OPT_LOCAL_QUERY_ORDER = 8,
     IDW_OPT_DETERMINISTIC = 9,
-    IDW_OPT_FMA_LOG2 = 10
+    IDW_OPT_FMA_LOG2 = 10,
+    IDW_OPT_KNN_SEARCH = 11
 } idw_option;
 
 idw_status idw_set_option(idw_handle_t handle, idw_option option, int64_t value);

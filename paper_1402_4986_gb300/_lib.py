@@ -35,7 +35,7 @@ PAPER_KERNELS = {"naive": 0, "tiled": 1}
 PAPER_LAYOUTS = {"soa": 0, "aos": 1, "aoas": 2, "hybrid": 3}
 OPTIONS = {"autotune": 1, "sweep_variant": 2, "force_general_power": 3, "last_variant": 4,
            "tuned_classes": 5, "staging_layout": 6, "validate_inputs": 7,
-           "local_query_order": 8, "deterministic": 9, "fma_log2": 10}
+           "local_query_order": 8, "deterministic": 9, "fma_log2": 10, "knn_search": 11}
 
 
 class PlanInfo(ctypes.Structure):

@@ -40,6 +40,7 @@ struct idw_handle_s {
   int opt_query_order = 0;      // local forms: 1 keeps the caller's query order
   bool opt_deterministic = false;  // k-NN gradients summed in a fixed order
   bool opt_fma_log2 = false;       // general p: part of log2 on the FMA pipe
+  int opt_knn_search = 0;          // k-NN search: 0 one thread per query, 1 warp-cooperative
   unsigned* vflag = nullptr;    // device word the scan sets
   int last_variant = -1;
   std::map<std::string, int> tuned;  // size class -> sweep variant
@@ -749,7 +750,7 @@ idw_status idw_interpolate_knn(idw_handle_t h, const float* data, int64_t n, con
   if (st != IDW_OK) return st;
   const cudaError_t e = idw::launch_knn(data, n, queries, m, p, k, out, nbr_out, kd2_out, h->ws, L,
                                         h->sm_count, static_cast<cudaStream_t>(stream), nullptr,
-                                        h->opt_query_order == 0);
+                                        h->opt_query_order == 0, true, h->opt_knn_search == 1);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -801,7 +802,7 @@ idw_status idw_knn_backward(idw_handle_t h, const float* data, int64_t n, const 
   if (st != IDW_OK) return st;
   e = idw::launch_knn_backward(data, n, queries, m, p, k, grad_out, grad_z, grad_data_xy,
                                grad_query_xy, grad_p, h->ws, L, h->sm_count, s,
-                               h->opt_query_order == 0, det);
+                               h->opt_query_order == 0, det, h->opt_knn_search == 1);
   return e == cudaSuccess ? IDW_OK : cuda_fail(h, e);
 }
 
@@ -940,6 +941,10 @@ idw_status idw_set_option(idw_handle_t h, idw_option opt, int64_t value) {
       if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
       h->opt_fma_log2 = value != 0;
       return IDW_OK;
+    case IDW_OPT_KNN_SEARCH:
+      if (value < 0 || value > 1) return IDW_ERR_INVALID_ARG;
+      h->opt_knn_search = static_cast<int>(value);
+      return IDW_OK;
     default:
       return IDW_ERR_INVALID_ARG;
   }
@@ -958,6 +963,7 @@ idw_status idw_get_option(idw_handle_t h, idw_option opt, int64_t* value) {
     case IDW_OPT_LOCAL_QUERY_ORDER: *value = h->opt_query_order; return IDW_OK;
     case IDW_OPT_DETERMINISTIC: *value = h->opt_deterministic; return IDW_OK;
     case IDW_OPT_FMA_LOG2: *value = h->opt_fma_log2; return IDW_OK;
+    case IDW_OPT_KNN_SEARCH: *value = h->opt_knn_search; return IDW_OK;
     default: return IDW_ERR_INVALID_ARG;
   }
 }

@@ -1088,8 +1088,10 @@ struct KnnHeap {
     h[at * kKnnThreads] = key;
   }
   // Replaces the largest key by a smaller one (keys are distinct).
-  __device__ __forceinline__ void replace_top(u64 key, int n) {
-    int at = 0;
+  __device__ __forceinline__ void replace_top(u64 key, int n) { sift_down(0, key, n); }
+  // Puts `key` at slot `at` of the first n slots and sifts it down, the
+  // subtree below `at` being a heap already.
+  __device__ __forceinline__ void sift_down(int at, u64 key, int n) {
     for (;;) {
       const int c0 = 4 * at + 1;
       if (c0 >= n) break;
@@ -1111,7 +1113,84 @@ struct KnnHeap {
     }
     h[at * kKnnThreads] = key;
   }
+  // Floyd's bottom-up construction of a heap over the first n slots.
+  __device__ void heapify(int n) {
+    for (int a = (n - 2) >> 2; a >= 0; --a) sift_down(a, h[a * kKnnThreads], n);
+  }
 };
+
+// Writes one query's k-NN result from its heap: Z (the z of the lowest
+// coincident index, or Eq. 1 over the selection with compensated FP32 sums,
+// or FP64 when those leave FP32's range; NaN when nothing is selected), the
+// hit index, the k-th key's d^2 and the neighbour row (key order when
+// sort_rows, else heap order).  Shared by both search kernels.
+template <int MODE>
+__device__ __forceinline__ void knn_write_result(KnnHeap& hp, int best_hit, float qx, float qy,
+                                                 int j, const float* __restrict__ data,
+                                                 int64_t n, double p, int k,
+                                                 float* __restrict__ out,
+                                                 int32_t* __restrict__ nbr_out,
+                                                 float* __restrict__ kd2_out,
+                                                 int32_t* __restrict__ hit_out, bool sort_rows) {
+  const int size = hp.size;
+  if (kd2_out) kd2_out[j] = size > 0 ? key_d2(hp.top()) : __int_as_float(0x7fc00000);
+  float zv = __int_as_float(0x7fc00000);  // NaN: nothing selected
+  if (best_hit != INT_MAX) {
+    if (dcheck(best_hit >= 0 && best_hit < n, kSiteData)) zv = data[3 * int64_t(best_hit) + 2];
+  } else if (size > 0) {
+    const float hpw = static_cast<float>(0.5 * p), nhp = -hpw;
+    u64 hi = 0, lo = 0;
+    for (int s = 0; s < size; ++s) {
+      const u64 key = hp.h[s * kKnnThreads];
+      const float w = local_weight<MODE>(key_d2(key), hpw, nhp);
+      two_sum_acc(hi, lo, pk(w, __fmul_rn(w, data[3 * int64_t(key_index(key)) + 2])));
+    }
+    float h0, h1, l0, l1;
+    upk(hi, h0, h1);
+    upk(lo, l0, l1);
+    if (h0 >= kTinyPerMember * float(size) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
+        fabsf(l1) <= FLT_MAX) {
+      const float z0 = __fdiv_rn(h1, h0);
+      const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
+      zv = __fmaf_rn(res, rcp_approx(h0), z0);
+    } else {
+      // Outside FP32's range: FP64 over the selected points, scaled by
+      // d2_min^(p/2).
+      double dmin = INFINITY;
+      for (int s = 0; s < size; ++s) {
+        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
+        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+        dmin = fmin(dmin, ex * ex + ey * ey);
+      }
+      double s0 = 0.0, s1 = 0.0;
+      for (int s = 0; s < size; ++s) {
+        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
+        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
+        const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
+        s0 += w;
+        s1 += w * double(x[2]);
+      }
+      zv = static_cast<float>(s1 / s0);
+    }
+  }
+  out[j] = zv;
+  if (hit_out) hit_out[j] = best_hit != INT_MAX ? best_hit : -1;
+  if (nbr_out) {
+    int32_t* row = nbr_out + int64_t(j) * k;
+    for (int s = size; s < k; ++s) row[s] = -1;
+    if (!sort_rows) {  // the selection in heap order (the gradient needs no order)
+      for (int s = 0; s < size; ++s) row[s] = key_index(hp.h[s * kKnnThreads]);
+      return;
+    }
+    // Heap sort: the largest remaining key goes to the end of the row.
+    for (int n = size; n > 0; --n) {
+      const u64 top = hp.top();
+      row[n - 1] = key_index(top);
+      const u64 last = hp.h[(n - 1) * kKnnThreads];
+      if (n > 1) hp.replace_top(last, n - 1);
+    }
+  }
+}
 
 // At most 64 registers (32 one-warp blocks per SM); left to itself the
 // compiler settles on fewer and spills.
@@ -1141,9 +1220,14 @@ __global__ void __maxnreg__(64)
   auto run = [&](int yy, int xa, int xb) {
     const int a = cell_start(starts, base, yy * g.gx + xa, g.cells);
     const int b = cell_start(starts, base, yy * g.gx + xb + 1, g.cells);
+    // Each candidate's record is loaded one iteration ahead, so that its
+    // latency overlaps the previous candidate's heap work.
+    float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a < b && dcheck(a >= 0 && a < n, kSiteGather)) nv = sorted[a];
     for (int q = a; q < b; ++q) {
       if (!dcheck(q >= 0 && q < n, kSiteGather)) break;
-      const float4 v = sorted[q];
+      const float4 v = nv;
+      if (q + 1 < b && dcheck(q + 1 < n, kSiteGather)) nv = sorted[q + 1];
       const float d2 = fp32_d2(qx, qy, v.x, v.y);
       const int idx = __float_as_int(v.w);
       if (d2 == 0.f && v.x == qx && v.y == qy) best_hit = min(best_hit, idx);
@@ -1303,64 +1387,283 @@ __global__ void __maxnreg__(64)
       r = r2;
     }
   }
-  const int size = hp.size;
-  if (kd2_out) kd2_out[j] = size > 0 ? key_d2(hp.top()) : __int_as_float(0x7fc00000);
-  float zv = __int_as_float(0x7fc00000);  // NaN: nothing selected
-  if (best_hit != INT_MAX) {
-    if (dcheck(best_hit >= 0 && best_hit < n, kSiteData)) zv = data[3 * int64_t(best_hit) + 2];
-  } else if (size > 0) {
-    const float hpw = static_cast<float>(0.5 * p), nhp = -hpw;
-    u64 hi = 0, lo = 0;
-    for (int s = 0; s < size; ++s) {
-      const u64 key = hp.h[s * kKnnThreads];
-      const float w = local_weight<MODE>(key_d2(key), hpw, nhp);
-      two_sum_acc(hi, lo, pk(w, __fmul_rn(w, data[3 * int64_t(key_index(key)) + 2])));
+  knn_write_result<MODE>(hp, best_hit, qx, qy, j, data, n, p, k, out, nbr_out, kd2_out, hit_out,
+                         sort_rows);
+}
+
+// ------------------------------------------- k-NN, warp-synchronous
+//
+// The same search as knn_query_kernel, one thread per query, with the 32
+// lanes of a warp kept in step so that they diverge far less:
+// * every lane grows its square by the same step at the same time (the
+//   smallest of the lanes' step choices; a lane whose stop test has held
+//   idles until the warp's last lane stops);
+// * a band's rows are taken in the same order by every lane (row offsets
+//   -r2 .. r2 from the lane's own cell row), each lane listing its
+//   non-empty row runs (clipped to its disc) in shared memory first, then
+//   walking its listed runs as one flat stream of candidates, so a lane
+//   waits only when its whole stream is shorter than another's;
+// * keys that beat a lane's k-th key are appended to its k slots while it
+//   fills and to a short pending list after that; the warp merges the
+//   pending lists into the lanes' heaps together (building each heap, by
+//   Floyd's method, once its k slots are full) whenever a lane's list is
+//   nearly full and at the end of each step, where the stop test needs the
+//   exact k-th key.
+// It is an option, not the default: the lanes do keep more in step (16.6
+// of 32 threads per instruction against 11.7), but the lockstep control
+// costs about as many warp instructions as the divergence it removes, the
+// run lists cut the warps an SM holds, and on clustered data the lanes of
+// a warp need very different numbers of steps.
+// Every cell the single-query search walks is walked here too, or lies
+// beyond the lane's k-th key, so the selection is the same: the k smallest
+// keys.
+
+constexpr int kSyncRuns = 8;     // row runs a lane lists before walking them
+constexpr int kSyncPending = 4;  // keys a lane holds back before the warp merges
+
+// Shared memory of one warp: (k + kSyncPending) key slots and kSyncRuns
+// runs per lane, lane-interleaved.
+size_t knn_sync_smem_bytes(int k) {
+  return size_t(k + kSyncPending) * kKnnThreads * sizeof(u64) +
+         size_t(kSyncRuns) * kKnnThreads * sizeof(int2);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kKnnThreads)
+    knn_sync_kernel(const GridDev* __restrict__ grid, const float4* __restrict__ sorted,
+                    const int32_t* __restrict__ starts, const int32_t* __restrict__ base,
+                    const int32_t* __restrict__ bpre, const int32_t* __restrict__ sat,
+                    const float4* __restrict__ qrec, const float* __restrict__ data, int64_t n,
+                    int64_t m, double p, int k, float* __restrict__ out,
+                    int32_t* __restrict__ nbr_out, float* __restrict__ kd2_out,
+                    int32_t* __restrict__ hit_out, bool sort_rows) {
+  extern __shared__ __align__(16) unsigned char knn_smem[];
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int64_t t = int64_t(blockIdx.x) * kKnnThreads + lane;
+  KnnHeap hp;
+  hp.h = reinterpret_cast<u64*>(knn_smem) + lane;
+  int2* runs = reinterpret_cast<int2*>(knn_smem + size_t(k + kSyncPending) * kKnnThreads *
+                                                      sizeof(u64)) + lane;
+  const GridDev g = *grid;
+  float qx = 0.f, qy = 0.f;
+  int j = -1;
+  if (t < m) {
+    const float4 rq = qrec[t];
+    qx = rq.x;
+    qy = rq.y;
+    j = __float_as_int(rq.z);
+    if (!dcheck(j >= 0 && j < m, kSiteOutput)) j = -1;
+  }
+  const bool searching = j >= 0 && finite2(qx, qy);
+  int best_hit = INT_MAX;
+  // The heap's largest key once it is built, else above every key; zero
+  // (nothing is taken) for a lane that does not search.
+  u64 worst = searching ? ~u64(0) : u64(0);
+  bool heaped = false;  // the k slots are full and form a heap
+  int np = 0;           // keys pending after the k slots
+  auto flush = [&]() {
+    if (!heaped && hp.size == k) {
+      hp.heapify(k);
+      heaped = true;
+      worst = hp.top();
     }
-    float h0, h1, l0, l1;
-    upk(hi, h0, h1);
-    upk(lo, l0, l1);
-    if (h0 >= kTinyPerMember * float(size) && h0 <= FLT_MAX && fabsf(h1) <= FLT_MAX &&
-        fabsf(l1) <= FLT_MAX) {
-      const float z0 = __fdiv_rn(h1, h0);
-      const float res = __fadd_rn(__fmaf_rn(-z0, h0, h1), __fmaf_rn(-z0, l0, l1));
-      zv = __fmaf_rn(res, rcp_approx(h0), z0);
+#pragma unroll 1
+    for (int i = 0; i < kSyncPending; ++i) {
+      if (i < np) {
+        const u64 key = hp.h[(k + i) * kKnnThreads];
+        if (key < worst) {
+          hp.replace_top(key, k);
+          worst = hp.top();
+        }
+      }
+    }
+    np = 0;
+  };
+  int nr = 0;  // runs listed
+  // Keys one candidate record against the lane's query.
+  auto consider = [&](const float4 c) {
+    const float d2 = fp32_d2(qx, qy, c.x, c.y);
+    const int idx = __float_as_int(c.w);
+    if (d2 == 0.f && c.x == qx && c.y == qy) best_hit = min(best_hit, idx);
+    const u64 key = knn_key(d2, idx);
+    if (key < worst) {  // to the k slots while filling, else pending
+      const bool fill = hp.size < k;
+      const int slot = fill ? hp.size : k + np;
+      if (dcheck(slot < k + kSyncPending && idx >= 0 && idx < n, kSiteHeap)) {
+        hp.h[slot * kKnnThreads] = key;
+        hp.size += fill;
+        np += !fill;
+      }
+    }
+  };
+  // Walks the listed runs as one stream, two candidates per lane per pass,
+  // both records loaded before either is keyed (a pass adds at most two
+  // pending keys, so the warp merges when a lane holds more than
+  // kSyncPending - 2).
+  auto walk_runs = [&]() {
+    int ri = 0, q = 0, b = 0;
+    auto take = [&]() {  // the lane's next candidate, or -1
+      if (q >= b && ri < nr) {
+        const int2 rr = runs[ri * kKnnThreads];
+        ++ri;
+        q = rr.x;
+        b = rr.y;
+      }
+      return q < b ? q++ : -1;
+    };
+    for (;;) {
+      const int c0 = take(), c1 = take();
+      float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+      const bool t0 = c0 >= 0 && dcheck(c0 < n, kSiteGather);
+      const bool t1 = c1 >= 0 && dcheck(c1 < n, kSiteGather);
+      if (t0) v0 = sorted[c0];
+      if (t1) v1 = sorted[c1];
+      if (t0) consider(v0);
+      if (t1) consider(v1);
+      // Merged before the loop can end, so that every lane leaves with at
+      // most kSyncPending - 2 keys pending and the next pass has room.
+      if (__any_sync(kFull, np > kSyncPending - 2)) flush();
+      if (!__any_sync(kFull, q < b || ri < nr)) break;
+    }
+    nr = 0;
+  };
+
+  const float u = searching ? cell_pos(qx, g.hx0, g.inv2) : 0.f;
+  const float v = searching ? cell_pos(qy, g.hy0, g.inv2) : 0.f;
+  const int cx = clamp_floor(u, 0, g.gx - 1), cy = clamp_floor(v, 0, g.gy - 1);
+  const float mg = __fmaf_ru(fabsf(u) + fabsf(v), 0x1p-22f, 0x1p-9f);
+  const float ax = fmaxf(0.f, fmaxf(u - float(g.gx), -u) - mg);
+  const float ay = fmaxf(0.f, fmaxf(v - float(g.gy), -v) - mg);
+  const float hh = g.inv2 > 0.f ? 2.f / g.inv2 : 0.f;
+  const float h2 = __fmul_rd(hh, hh) * (1.f - 0x1p-18f);
+  const float ih2 = __frcp_ru(h2);
+  auto reach2 = [&]() { return __fmul_ru(__fadd_ru(key_d2(worst), 0x1p-126f), ih2); };
+  auto clip = [&](float c, float e, int& lo, int& hi) {
+    if (lo > hi) return;
+    const float a = ceilf(__fsub_rd(__fsub_rd(__fsub_rd(c, mg), e), 1.f));
+    const float b = floorf(__fadd_ru(__fadd_ru(c, mg), e));
+    const int nlo = int(fminf(fmaxf(float(lo), a), float(hi) + 1.f));
+    const int nhi = int(fmaxf(fminf(float(hi), b), float(lo) - 1.f));
+    lo = nlo;
+    hi = nhi;
+  };
+  auto square_count = [&](int rr) {
+    const int ya = max(0, cy - rr), yb = min(g.gy - 1, cy + rr);
+    const int xa = max(0, cx - rr), xb = min(g.gx - 1, cx + rr);
+    const int W = g.gx + 1;
+    if (!dcheck(ya >= 0 && xa >= 0 && yb < g.gy && xb < g.gx, kSiteTable)) return 0;
+    return sat[(yb + 1) * W + xb + 1] - sat[ya * W + xb + 1] - sat[(yb + 1) * W + xa] +
+           sat[ya * W + xa];
+  };
+  // Lists run [xa, xb] of row yy (already clipped) when it holds points.
+  auto list_run = [&](int yy, int xa, int xb) {
+    if (xa > xb) return;
+    const int a = cell_start(starts, base, yy * g.gx + xa, g.cells);
+    const int b = cell_start(starts, base, yy * g.gx + xb + 1, g.cells);
+    if (a < b && dcheck(nr < kSyncRuns, kSiteTable)) runs[nr++ * kKnnThreads] = make_int2(a, b);
+  };
+
+  bool finished = !searching;
+  int in_square = -1;  // points in this lane's square of radius r, once counted
+  for (int r = -1;;) {
+    if (r >= 0) {
+      flush();  // the stop test and the clipping use the exact k-th key
+      if (!finished) {
+        const bool open_l = cx - r > 0, open_r = cx + r < g.gx - 1;
+        const bool open_b = cy - r > 0, open_t = cy + r < g.gy - 1;
+        if (!(open_l || open_r || open_b || open_t)) {
+          finished = true;  // the square covers the grid
+        } else if (heaped) {
+          float l2 = INFINITY;
+          if (open_l) {
+            const float dx = fmaxf(ax, fmaxf(0.f, (u - float(cx - r)) - mg));
+            l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+          }
+          if (open_r) {
+            const float dx = fmaxf(ax, fmaxf(0.f, (float(cx + r + 1) - u) - mg));
+            l2 = fminf(l2, __fmaf_rd(dx, dx, __fmul_rd(ay, ay)));
+          }
+          if (open_b) {
+            const float dy = fmaxf(ay, fmaxf(0.f, (v - float(cy - r)) - mg));
+            l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+          }
+          if (open_t) {
+            const float dy = fmaxf(ay, fmaxf(0.f, (float(cy + r + 1) - v) - mg));
+            l2 = fminf(l2, __fmaf_rd(dy, dy, __fmul_rd(ax, ax)));
+          }
+          if (key_d2(worst) < __fmul_rd(l2, h2) - 0x1p-126f) finished = true;
+        }
+      }
+      if (__all_sync(kFull, finished)) break;
+    }
+    // The step: each searching lane chooses as the single-query search does
+    // (from r = 4 on, halved while its band would hold more than 4k points,
+    // counted from the summed-area table); the warp takes the smallest.
+    int r2 = r + max(1, r >> 1);
+    bool walk = !finished;
+    if (r >= 4) {
+      int mine = INT_MAX;
+      if (!finished) {
+        if (in_square < 0) in_square = square_count(r);
+        mine = r2;
+        int c2 = square_count(mine);
+        while (c2 - in_square > 4 * k && mine > r + 1) {
+          mine = r + max(1, (mine - r) >> 1);
+          c2 = square_count(mine);
+        }
+      }
+      r2 = __reduce_min_sync(kFull, mine);
+      if (!finished) {
+        const int c2 = square_count(r2);
+        walk = c2 != in_square;  // an empty band is not walked
+        in_square = c2;
+      }
+    }
+    if (r < 0) {
+      if (walk) list_run(cy, cx, cx);  // the lane's own cell
     } else {
-      // Outside FP32's range: FP64 over the selected points, scaled by
-      // d2_min^(p/2).
-      double dmin = INFINITY;
-      for (int s = 0; s < size; ++s) {
-        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
-        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
-        dmin = fmin(dmin, ex * ex + ey * ey);
+      // Row offsets -r2 .. r2 from the lane's own row, the same for every
+      // lane: within r a row holds the band's two side strips, beyond it a
+      // whole row of the band.
+      const bool check_blocks = r >= 8;
+#pragma unroll 1
+      for (int s = -r2; s <= r2; ++s) {
+        if (__any_sync(kFull, nr > kSyncRuns - 2)) walk_runs();
+        const int yy = cy + s;
+        if (!walk || yy < 0 || yy >= g.gy) continue;
+        int xa = max(0, cx - r2), xb = min(g.gx - 1, cx + r2);
+        if (heaped) {  // the columns this row's chord reaches
+          const float gap = fmaxf(0.f, fmaxf(float(yy) - v, v - float(yy + 1)) - mg);
+          const float w2 = reach2(), g2 = __fmul_rd(gap, gap);
+          if (g2 > w2) continue;
+          clip(u, __fsqrt_ru(__fsub_ru(w2, g2)), xa, xb);
+          if (xa > xb) continue;
+        }
+        if (check_blocks) {  // the row's stretch of 8 x 8-cell blocks holds no point
+          const int by = yy >> kBlockShift;
+          const int32_t* bp = bpre + by * (kMaxBlocksPerAxis + 1);
+          if (!dcheck(by < kMaxBlocksPerAxis && (xb >> kBlockShift) < kMaxBlocksPerAxis,
+                      kSiteBlock) ||
+              bp[(xb >> kBlockShift) + 1] == bp[xa >> kBlockShift])
+            continue;
+        }
+        if (s >= -r && s <= r) {
+          list_run(yy, xa, min(xb, cx - r - 1));
+          list_run(yy, max(xa, cx + r + 1), xb);
+        } else {
+          list_run(yy, xa, xb);
+        }
       }
-      double s0 = 0.0, s1 = 0.0;
-      for (int s = 0; s < size; ++s) {
-        const float* x = data + 3 * int64_t(key_index(hp.h[s * kKnnThreads]));
-        const double ex = double(qx) - x[0], ey = double(qy) - x[1];
-        const double w = pow(dmin / (ex * ex + ey * ey), 0.5 * p);
-        s0 += w;
-        s1 += w * double(x[2]);
-      }
-      zv = static_cast<float>(s1 / s0);
     }
+    walk_runs();
+    r = r2;
   }
-  out[j] = zv;
-  if (hit_out) hit_out[j] = best_hit != INT_MAX ? best_hit : -1;
-  if (nbr_out) {
-    int32_t* row = nbr_out + int64_t(j) * k;
-    for (int s = size; s < k; ++s) row[s] = -1;
-    if (!sort_rows) {  // the selection in heap order (the gradient needs no order)
-      for (int s = 0; s < size; ++s) row[s] = key_index(hp.h[s * kKnnThreads]);
-      return;
-    }
-    // Heap sort: the largest remaining key goes to the end of the row.
-    for (int n = size; n > 0; --n) {
-      const u64 top = hp.top();
-      row[n - 1] = key_index(top);
-      const u64 last = hp.h[(n - 1) * kKnnThreads];
-      if (n > 1) hp.replace_top(last, n - 1);
-    }
-  }
+  flush();
+  if (!heaped) hp.heapify(hp.size);  // fewer than k points
+  if (j >= 0)
+    knn_write_result<MODE>(hp, best_hit, qx, qy, j, data, n, p, k, out, nbr_out, kd2_out,
+                           hit_out, sort_rows);
 }
 
 // ------------------------------------------------------ k-NN gradients
@@ -1919,7 +2222,7 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
                                 const LocalLayout& L, int sm_count, cudaStream_t s,
-                                bool sort_queries, bool deterministic) {
+                                bool sort_queries, bool deterministic, bool warp_search) {
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   float* zbuf = reinterpret_cast<float*>(ws + L.bytes);
   int32_t* hit = reinterpret_cast<int32_t*>(ws + L.bytes + round_up(size_t(m) * 4, 256));
@@ -1927,7 +2230,7 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
   // Deterministic mode: rows in key order, so each query's own sums run in
   // one fixed order too.
   cudaError_t e = launch_knn(data, n, queries, m, p, k, zbuf, nbr, nullptr, workspace, L, sm_count,
-                             s, hit, sort_queries, deterministic);
+                             s, hit, sort_queries, deterministic, warp_search);
   if (e != cudaSuccess) return e;
   if (deterministic)
     return launch_knn_backward_fixed_order(data, n, queries, m, p, k, grad_out, grad_z, grad_xy,
@@ -1970,16 +2273,26 @@ cudaError_t debug_check_failures(unsigned* sites, bool* enabled) {
 
 size_t knn_smem_bytes(int k) { return size_t(k) * kKnnThreads * sizeof(u64); }
 
+
 cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64_t m, double p,
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s, int32_t* hit_out,
-                       bool sort_queries, bool sort_rows) {
-  const size_t smem = knn_smem_bytes(k);
-  cudaError_t e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(knn_query_kernel<kPowGeneral>,
+                       bool sort_queries, bool sort_rows, bool warp_search) {
+  const size_t smem = warp_search ? knn_sync_smem_bytes(k) : knn_smem_bytes(k);
+  cudaError_t e = cudaSuccess;
+  if (warp_search) {
+    e = cudaFuncSetAttribute(knn_sync_kernel<kPow2>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(knn_sync_kernel<kPowGeneral>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  } else {
+    e = cudaFuncSetAttribute(knn_query_kernel<kPow2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(knn_query_kernel<kPowGeneral>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  }
   if (e != cudaSuccess) return e;
   e = launch_grid_sort(data, n, queries, m, 0.0, k, workspace, L, sm_count, s, sort_queries);
   if (e != cudaSuccess) return e;
@@ -1995,14 +2308,10 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
   sat_kernel<<<(kMaxCellsPerAxis + 1 + kSatCols - 1) / kSatCols, kSatCols * kSatWarps, 0, s>>>(
       grid, starts_d, sums, sat);
   const unsigned qgrid = static_cast<unsigned>((m + kKnnThreads - 1) / kKnnThreads);
-  if (p == 2.0)
-    knn_query_kernel<kPow2><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
-        hit_out, sort_rows);
-  else
-    knn_query_kernel<kPowGeneral><<<qgrid, kKnnThreads, smem, s>>>(
-        grid, sorted, starts_d, sums, bpre, sat, qrec, data, n, m, p, k, out, nbr_out, kd2_out,
-        hit_out, sort_rows);
+  auto kernel = warp_search ? (p == 2.0 ? knn_sync_kernel<kPow2> : knn_sync_kernel<kPowGeneral>)
+                            : (p == 2.0 ? knn_query_kernel<kPow2> : knn_query_kernel<kPowGeneral>);
+  kernel<<<qgrid, kKnnThreads, smem, s>>>(grid, sorted, starts_d, sums, bpre, sat, qrec, data, n,
+                                          m, p, k, out, nbr_out, kd2_out, hit_out, sort_rows);
   return cudaGetLastError();
 }
 

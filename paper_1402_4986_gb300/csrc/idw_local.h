@@ -56,7 +56,7 @@ cudaError_t launch_knn(const float* data, int64_t n, const float* queries, int64
                        int k, float* out, int32_t* nbr_out, float* kd2_out, void* workspace,
                        const LocalLayout& L, int sm_count, cudaStream_t s,
                        int32_t* hit_out = nullptr, bool sort_queries = true,
-                       bool sort_rows = true);
+                       bool sort_rows = true, bool warp_search = false);
 
 // Gradients of the k-NN form (each selection held fixed): the search with
 // neighbour lists and hits kept in the workspace after L.bytes (plus
@@ -70,7 +70,8 @@ cudaError_t launch_knn_backward(const float* data, int64_t n, const float* queri
                                 double p, int k, const float* grad_out, float* grad_z,
                                 float* grad_xy, float* grad_q, double* grad_p, void* workspace,
                                 const LocalLayout& L, int sm_count, cudaStream_t s,
-                                bool sort_queries = true, bool deterministic = false);
+                                bool sort_queries = true, bool deterministic = false,
+                                bool warp_search = false);
 
 // A prepared index: the data side of a local form built once and queried
 // by many calls.  The index's own buffer holds the plan, the data cell

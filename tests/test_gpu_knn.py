@@ -5,7 +5,8 @@ Eq. 1 over the k data points nearest to each query, nearness being the key
 Both sides rank by the same FP32 expression, so the neighbour lists and the
 k-th keys must be identical; values are compared as for the global form
 (error = max_j |Z_gpu - Z_64| / max_i |z_i| <= 2e-6), NaN where nothing is
-selected, and bit-exact z at exact hits.
+selected, and bit-exact z at exact hits.  Each test runs under both k-NN searches
+(one thread per query, one warp per slice of a row's queries).
 """
 import numpy as np
 import pytest
@@ -19,13 +20,19 @@ pytestmark = pytest.mark.gpu
 TOL_F32C = 2e-6
 
 
-@pytest.fixture(scope="module")
-def idw():
+@pytest.fixture(scope="module", params=[0, 1], ids=["thread_search", "warp_search"])
+def idw(request):
+    """The library with the default handle's k-NN search set to one thread
+    per query (0) or one warp per row slice of queries (1); every test runs
+    under both, and both must select the same neighbours."""
     from paper_1402_4986_gb300 import build
     build.build()
     import paper_1402_4986_gb300 as m
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
-    return m
+    before = m.get_option("knn_search")
+    m.set_option("knn_search", request.param)
+    yield m
+    m.set_option("knn_search", before)
 
 
 def _dev(a):
@@ -172,3 +179,24 @@ def test_full_size_sampled(idw):
     assert np.array_equal(kd2.cpu().numpy()[idx], r["kd2"])
     err = np.max(np.abs(Z.cpu().numpy()[idx] - r["Z"])) / np.max(np.abs(data[:, 2]))
     assert err <= TOL_F32C, err
+
+
+def test_option_values(idw):
+    assert idw.get_option("knn_search") in (0, 1)
+    for bad in (-1, 2):
+        with pytest.raises(idw.IDWError):
+            idw.set_option("knn_search", bad)
+
+
+def test_rows_of_many_queries(idw):
+    """Rows of cells holding many queries (several warps per row, the last
+    one partial) and rows holding none: dense query bands across sparse
+    data, so a warp's queries span few columns and its rectangle is wide."""
+    rng = np.random.default_rng(63)
+    data = np.concatenate([rng.random((6000, 2)), rng.standard_normal((6000, 1))], 1)
+    data = data.astype(np.float32)
+    band = np.stack([rng.random(4000), 0.5 + 0.002 * rng.random(4000)], 1)
+    corner = 0.05 * rng.random((37, 2))
+    q = np.concatenate([band, corner]).astype(np.float32)
+    for k in (1, 16, 64):
+        _compare(idw, data, q, 2.0, k)

@@ -200,3 +200,26 @@ def test_deterministic_mode_is_bitwise_repeatable(idw, clustered):
         scale = float(b.abs().max())
         assert float((a.double() - b.double()).abs().max()) <= 5 * TOL * max(scale, 1e-30)
     h.close()
+
+
+@pytest.mark.parametrize("clustered", [False, True])
+def test_warp_search_gradients_match_oracle(idw, clustered):
+    """The gradients with the warp-cooperative search selecting each
+    query's neighbours (the same selection, reached in another order)."""
+    h = idw.Handle(torch.cuda.current_device())
+    idw.set_option("knn_search", 1, handle=h)
+    if clustered:
+        prob = synthetic.config_local(seed=141, n=20000, m=3000, clustered=True)
+    else:
+        prob = synthetic.uniform_problem(5003, 2001, seed=142, exact_hits=7)
+    data, q = prob["data"], prob["queries"]
+    g = np.random.default_rng(143).standard_normal(q.shape[0]).astype(np.float32)
+    for k in (1, 32):
+        gz, gxy, gq, gp = idw.knn_backward(_dev(data), _dev(q), 2.0, k, _dev(g), handle=h)
+        torch.cuda.synchronize()
+        G = oracle.idw_knn_grad(data, q, 2.0, k, g)
+        assert _rel(gz.cpu().numpy(), G["grad_z"]) <= TOL
+        assert _rel(gxy.cpu().numpy(), G["grad_xy"]) <= TOL
+        assert _rel(gq.cpu().numpy(), G["grad_q"]) <= TOL
+        assert abs(float(gp.cpu()[0]) - G["grad_p"]) <= TOL * max(abs(G["grad_p"]), 1e-300)
+    h.close()
