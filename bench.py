@@ -1062,8 +1062,11 @@ def run_knn(args):
         _, _, gq, _ = idw.knn_backward(d, q, 2.0, k, gout)
         Gs = oracle.idw_knn_grad(prob["data"], prob["queries"][np.sort(idx)], 2.0, k,
                                  gout.cpu().numpy()[np.sort(idx)])
-        gerr = float(np.max(np.abs(gq.cpu().numpy()[np.sort(idx)] - Gs["grad_q"])) /
-                     np.max(np.abs(Gs["grad_q"])))
+        # Relative to the largest |dL/dq| (absolute where every one is 0: at
+        # k = 1, Z is the nearest point's z and does not move with q).
+        gscale = float(np.max(np.abs(Gs["grad_q"])))
+        gerr = float(np.max(np.abs(gq.cpu().numpy()[np.sort(idx)] - Gs["grad_q"]))) / (
+            gscale if gscale > 0 else 1.0)
         rows.append({"data": "clustered" if clustered else "uniform", "call": "backward",
                      "n": n, "m": m, "k": k, "p": 2.0, "ms": bms, "queries_s": m / (bms / 1e3),
                      "grad_q_error_vs_fp64_oracle": gerr, "error_sample_queries": len(idx)})
