@@ -47,6 +47,16 @@ def test_library_exports_every_declared_symbol(lib):
         assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in the binding"
 
 
+def test_binding_options_match_the_header():
+    """Every idw_option of the header has the binding's name and value, and
+    the binding names no option the header lacks."""
+    text = open(os.path.join(ROOT, "include", "idw.h")).read()
+    declared = {m.group(1).lower(): int(m.group(2))
+                for m in re.finditer(r"\bIDW_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    from paper_1402_4986_gb300 import _lib
+    assert declared == _lib.OPTIONS
+
+
 def test_status_strings(lib):
     for code, name in {0: "IDW_OK", 1: "IDW_ERR_INVALID_ARG", 7: "IDW_ERR_DEVICE_TIMEOUT"}.items():
         assert lib.idw_status_string(code).decode() == name
