@@ -394,7 +394,7 @@ def run_ours(args, ws, rank, local):
             "lp_basis": "max pairs/s when a fraction f of pairs shares reciprocals: "
                         "r (6 + 1.5 f) <= 128 FMA lanes and r (1 - f/2) <= 16 MUFU lanes "
                         "per SM per clock",
-            "kernel": "fwd_f32_kernel (all-pairs sweep)",
+            "kernel": "sweep_kernel<p = 2> (all-pairs sweep)",
             "peak_basis": "min(128 FFMA / 6 ops, 16 MUFU / 1 op) per SM per clock x "
                           f"{sms} SMs x median SM clock {clk_mhz} MHz under load",
             "peak_measured_rates": peak_meas / 1e9,
@@ -464,11 +464,12 @@ def run_ours(args, ws, rank, local):
 
 
 def headline_extras(args, idw, h, data, q, data_np, q_np, single_pairs_s, rates, sms, mhz):
-    """Compact summaries of the other forward workloads, measured in the same
-    run after the headline's timed region: the general-power sweep on the
-    same N = M = 2^20 data (p = 3.5), the batched workload (256 uneven
-    problems in one persistent launch) against this run's single-instance
-    pairs/s, and the allocation-free entry point at N = M = 262144."""
+    """Compact summaries of the other workloads, measured in the same run
+    after the headline's timed region: the general-power sweep on the same
+    N = M = 2^20 data (p = 3.5), the batched workload (256 uneven problems
+    in one persistent launch) against this run's single-instance pairs/s,
+    the forward and adjoint at N = M = 262144, p = 2.5, and the
+    allocation-free entry point at N = M = 262144."""
     import ctypes
     import torch
     import synthetic
@@ -523,6 +524,42 @@ def headline_extras(args, idw, h, data, q, data_np, q_np, single_pairs_s, rates,
         "roofline": roofline_block("pow2", bpairs / (bsweep / max(1, blaunch) / 1e3), rates, sms,
                                    mhz, "sweep_kernel<p = 2, batch table> (one persistent launch)")}
     del bd, bq, bo
+    # Differentiation: forward with saved S0, then every gradient, N = M = 262144,
+    # p = 2.5; dL/dq of 256 sampled queries against the FP64 oracle (each
+    # query's dL/dq depends on its own row of Eq. 1 only).
+    ap = synthetic.config_adjoint()
+    ad = torch.from_numpy(ap["data"]).cuda()
+    aq = torch.from_numpy(ap["queries"]).cuda()
+    ag = torch.from_numpy(ap["grad_out"]).cuda()
+    saved = {}
+
+    def adj_fwd():
+        saved["Z"], saved["s0"], saved["hit"] = idw.interpolate_saved(ad, aq, ap["p"], handle=h)
+
+    def adj_bwd():
+        saved["g"] = idw.backward(ad, aq, ap["p"], saved["Z"], saved["s0"], saved["hit"], ag,
+                                  handle=h)
+
+    f_ms = _events_ms(adj_fwd, 3)
+    b_ms = _events_ms(adj_bwd, 3)
+    apairs = float(ad.shape[0]) * aq.shape[0]
+    adj = {"n": ad.shape[0], "m": aq.shape[0], "p": ap["p"], "forward_ms": f_ms,
+           "backward_ms": b_ms, "backward_over_forward": b_ms / f_ms,
+           "backward_pair_evaluations_s": 2 * apairs / (b_ms / 1e3),
+           "roofline": roofline_block("adjoint_general", apairs / (b_ms / 1e3), rates, sms, mhz,
+                                      "query sweep + data sweep (whole backward call)",
+                                      evaluations_per_pair=2.0)}
+    if not args.no_cpu_baseline:
+        import oracle
+        idx = np.sort(np.random.default_rng(12).choice(aq.shape[0], 256, replace=False))
+        G = oracle.idw_grad(ap["data"], ap["queries"][idx], ap["p"], ap["grad_out"][idx],
+                            threads=os.cpu_count() or 1)
+        gq = saved["g"][2].cpu().numpy()[idx]
+        adj["grad_q_error_vs_fp64_oracle"] = float(
+            np.max(np.abs(gq - G["grad_q"])) / np.max(np.abs(G["grad_q"])))
+        adj["error_sample_queries"] = len(idx)
+    out["adjoint"] = adj
+    del ad, aq, ag, saved
     # The allocation-free entry point against the handle path, N = M = 262144.
     sp = synthetic.config_scale(262144)
     sd = torch.from_numpy(sp["data"]).cuda()
