@@ -24,11 +24,13 @@ Besides ``value`` (device-resident pairs/s) the line carries:
                 sample (the same sample the CPU baseline times);
   cpu_baseline  the FP64 oracle on the host cores (bounded query sample);
   clocks        nvidia-smi samples taken during the timed region;
-  general_p, batched, noalloc
+  general_p, batched, adjoint, noalloc
                 after the timed region: the general-power sweep (p = 3.5) on
                 the same data, the 256-problem batched launch against this
-                run's single-instance pairs/s, and the allocation-free entry
-                point at N = M = 262144 against the handle path.
+                run's single-instance pairs/s, the forward and every
+                gradient at N = M = 262144, p = 2.5 (dL/dq sampled against
+                the oracle), and the allocation-free entry point at
+                N = M = 262144 against the handle path.
 ``--full-check`` compares all M outputs with the oracle (minutes of host time).
 ``--impl reference`` times the oracle alone (the CPU reference arm).
 
