@@ -875,9 +875,29 @@ def run_batched(args, headline_pairs_s=None):
            "persistent_vs_loop": ms_l / ms_b,
            "roofline": roofline_block("pow2", pairs / (sweep_b / 1e3), rates, sms, mhz,
                                       "sweep_kernel<p = 2, batch table> (one persistent launch)")}
+    # Small problems, where a per-instance loop pays a call's fixed latency
+    # for little arithmetic: 256 problems, N_i, M_i log-uniform in [256, 8192].
+    del d, q, outs, graph
+    small = synthetic.config_batch(count=256, lo=256, hi=8192)["instances"]
+    sd = [torch.from_numpy(i["data"]).cuda() for i in small]
+    sq = [torch.from_numpy(i["queries"]).cuda() for i in small]
+    so = [torch.empty(x.shape[0], device="cuda") for x in sq]
+    spairs = float(sum(x.shape[0] * y.shape[0] for x, y in zip(sd, sq)))
+    ms_sb = _events_ms(lambda: idw.interpolate_batched(sd, sq, 2.0, outs=so), 10, warm=2)
+
+    def small_loop():
+        for dk, qk, ok in zip(sd, sq, so):
+            idw.interpolate(dk, qk, 2.0, out=ok)
+
+    ms_sl = _events_ms(small_loop, 3)
+    small_row = {"instances": len(small), "sizes": "N_i, M_i log-uniform in [256, 8192]",
+                 "total_pairs": spairs, "persistent_ms": ms_sb,
+                 "persistent_pairs_s": spairs / (ms_sb / 1e3), "loop_ms": ms_sl,
+                 "loop_pairs_s": spairs / (ms_sl / 1e3), "persistent_vs_loop": ms_sl / ms_sb}
     _emit("batched: 256 problems, N_i, M_i log-uniform in [1024, 262144] (seeded), uniform "
           "[0,1)^2, p=2, FP32-compensated; one persistent launch (also graph-captured) vs a "
-          "loop of per-instance calls; single large instance = N=M=2^20", [row])
+          "loop of per-instance calls; single large instance = N=M=2^20; second row: 256 "
+          "small problems, N_i, M_i log-uniform in [256, 8192]", [row, small_row])
 
 
 def run_layout(args):
