@@ -884,16 +884,26 @@ def run_batched(args, headline_pairs_s=None):
     so = [torch.empty(x.shape[0], device="cuda") for x in sq]
     spairs = float(sum(x.shape[0] * y.shape[0] for x, y in zip(sd, sq)))
     ms_sb = _events_ms(lambda: idw.interpolate_batched(sd, sq, 2.0, outs=so), 10, warm=2)
+    small_default = idw.get_option("last_variant")
 
     def small_loop():
         for dk, qk, ok in zip(sd, sq, so):
             idw.interpolate(dk, qk, 2.0, out=ok)
 
     ms_sl = _events_ms(small_loop, 3)
+    hv = idw.Handle(torch.cuda.current_device())
+    small_variants = {}
+    for v in range(6):
+        idw.set_option("sweep_variant", v, handle=hv)
+        small_variants[v] = spairs / (_events_ms(
+            lambda: idw.interpolate_batched(sd, sq, 2.0, outs=so, handle=hv), 5, warm=2) / 1e3)
+    hv.close()
     small_row = {"instances": len(small), "sizes": "N_i, M_i log-uniform in [256, 8192]",
                  "total_pairs": spairs, "persistent_ms": ms_sb,
                  "persistent_pairs_s": spairs / (ms_sb / 1e3), "loop_ms": ms_sl,
-                 "loop_pairs_s": spairs / (ms_sl / 1e3), "persistent_vs_loop": ms_sl / ms_sb}
+                 "loop_pairs_s": spairs / (ms_sl / 1e3), "persistent_vs_loop": ms_sl / ms_sb,
+                 "default_variant": small_default,
+                 "pairs_s_per_variant": small_variants}
     _emit("batched: 256 problems, N_i, M_i log-uniform in [1024, 262144] (seeded), uniform "
           "[0,1)^2, p=2, FP32-compensated; one persistent launch (also graph-captured) vs a "
           "loop of per-instance calls; single large instance = N=M=2^20; second row: 256 "
