@@ -1409,14 +1409,14 @@ __global__ void __maxnreg__(64)
 //   Floyd's method, once its k slots are full) whenever a lane's list is
 //   nearly full and at the end of each step, where the stop test needs the
 //   exact k-th key.
+// Every cell the single-query search walks is walked here too, or lies
+// beyond the lane's k-th key, so the selection is the same: the k smallest
+// keys.
 // It is an option, not the default: the lanes do keep more in step (16.7
 // of 32 threads per instruction against 12.0 at k = 32), but the lockstep
 // control costs about as many warp instructions as the divergence it
 // removes, the run lists cut the warps an SM holds, and on clustered data
 // the lanes of a warp need very different numbers of steps.
-// Every cell the single-query search walks is walked here too, or lies
-// beyond the lane's k-th key, so the selection is the same: the k smallest
-// keys.
 
 constexpr int kSyncRuns = 8;     // row runs a lane lists before walking them
 constexpr int kSyncPending = 4;  // keys a lane holds back before the warp merges
