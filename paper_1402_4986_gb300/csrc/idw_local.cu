@@ -1847,20 +1847,21 @@ __global__ void __launch_bounds__(kLocalThreads)
 // ----------------------------------------- deterministic k-NN gradients
 //
 // Point-major data-side terms in a fixed order: every (point, query)
-// selection becomes a key/value pair (point index, query index), listed
-// query-major; a stable radix sort by point keeps each point's queries in
-// increasing order; one warp per point then recomputes its terms from the
-// queries' states and sums them lane-strided and by a fixed shuffle tree.
+// selection becomes one 64-bit item, the point index above the query index,
+// listed query-major; a stable radix sort by point keeps each point's
+// queries in increasing order; one warp per point then recomputes its
+// terms from the queries' states and sums them lane-strided and by a fixed
+// shuffle tree.
 // dL/dp is summed over queries in index order by a fixed two-level tree.
 // Nothing depends on the order in which threads or atomics ran, so two calls
 // on the same inputs give the same bits.
 
-// Pair (x = j k + s): key = the selected point (the hit index for slot 0 of
-// a hit query), or n for an empty slot; value = j.
+// Pair (x = j k + s), packed as key << 32 | j: key = the selected point
+// (the hit index for slot 0 of a hit query), or n for an empty slot.
 __global__ void __launch_bounds__(256)
     knn_pairs_kernel(const int32_t* __restrict__ nbr, const int32_t* __restrict__ hit,
                      const KnnQState* __restrict__ qstate, int64_t m, int k, int64_t n,
-                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                     uint64_t* __restrict__ items) {
   const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (x >= m * k) return;
   const int64_t j = x / k;
@@ -1873,21 +1874,21 @@ __global__ void __launch_bounds__(256)
     const int32_t i = nbr[x];
     if (i >= 0 && dcheck(i < n, kSiteData)) key = i;
   }
-  keys[x] = static_cast<uint32_t>(key);
-  vals[x] = static_cast<uint32_t>(j);
+  items[x] = (uint64_t(key) << 32) | uint64_t(uint32_t(j));
 }
 
 // First and one-past-last position of each point's run of sorted keys (the
 // caller zeroes both arrays: a point no query selected has an empty run).
 __global__ void __launch_bounds__(256)
-    knn_runs_kernel(const uint32_t* __restrict__ keys, int64_t count, int64_t n,
+    knn_runs_kernel(const uint64_t* __restrict__ items, int64_t count, int64_t n,
                     int32_t* __restrict__ first, int32_t* __restrict__ last) {
   const int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (x >= count) return;
-  const uint32_t key = keys[x];
+  const uint32_t key = uint32_t(items[x] >> 32);
   if (key >= n) return;
-  if (x == 0 || keys[x - 1] != key) first[key] = static_cast<int32_t>(x);
-  if (x == count - 1 || keys[x + 1] != key) last[key] = static_cast<int32_t>(x + 1);
+  if (x == 0 || uint32_t(items[x - 1] >> 32) != key) first[key] = static_cast<int32_t>(x);
+  if (x == count - 1 || uint32_t(items[x + 1] >> 32) != key)
+    last[key] = static_cast<int32_t>(x + 1);
 }
 
 // One warp per data point: its terms (dL/dz, dL/dx, dL/dy), query by query
@@ -1896,7 +1897,7 @@ __global__ void __launch_bounds__(256)
 template <int MODE>
 __global__ void __launch_bounds__(256)
     knn_point_grad_kernel(const int32_t* __restrict__ first, const int32_t* __restrict__ last,
-                          const uint32_t* __restrict__ qidx, const KnnQState* __restrict__ qstate,
+                          const uint64_t* __restrict__ items, const KnnQState* __restrict__ qstate,
                           const float* __restrict__ queries, const float* __restrict__ data,
                           int64_t n, double p, const float* __restrict__ grad_out,
                           float* __restrict__ grad_z, float* __restrict__ grad_xy) {
@@ -1908,7 +1909,7 @@ __global__ void __launch_bounds__(256)
   float gz = 0.f, gx = 0.f, gy = 0.f;
   const int a = first[i], b = last[i];
   for (int q = a + lane; q < b; q += 32) {
-    const int64_t j = qidx[q];
+    const int64_t j = uint32_t(items[q]);  // the pair's query
     const KnnQState st = qstate[j];
     const float gj = grad_out[j];
     const float qx = queries[2 * j], qy = queries[2 * j + 1];
@@ -2145,7 +2146,7 @@ size_t knn_grad_scratch_bytes(int64_t n, int64_t m, int k, bool deterministic) {
              round_up(size_t(n) * 16, 256);
   if (deterministic) {
     const int64_t pairs = m * int64_t(k);
-    b += 2 * round_up(size_t(pairs) * 4, 256) + radix_sort_scratch_bytes(pairs) +
+    b += round_up(size_t(pairs) * 8, 256) + radix_sort_scratch_bytes(pairs) +
          2 * round_up(size_t(n) * 4, 256) + round_up(size_t(m) * sizeof(KnnQState), 256) +
          round_up(size_t(m) * 8, 256) + round_up(size_t(kDetSumCtas) * 8, 256);
   }
@@ -2171,8 +2172,7 @@ cudaError_t launch_knn_backward_fixed_order(const float* data, int64_t n, const 
     off += round_up(bytes, 256);
     return ptr;
   };
-  uint32_t* keys = reinterpret_cast<uint32_t*>(take(size_t(pairs) * 4));
-  uint32_t* vals = reinterpret_cast<uint32_t*>(take(size_t(pairs) * 4));
+  uint64_t* items = reinterpret_cast<uint64_t*>(take(size_t(pairs) * 8));
   void* sort_scratch = take(radix_sort_scratch_bytes(pairs));
   int32_t* first = reinterpret_cast<int32_t*>(take(size_t(n) * 4));
   int32_t* last = reinterpret_cast<int32_t*>(take(size_t(n) * 4));
@@ -2198,22 +2198,24 @@ cudaError_t launch_knn_backward_fixed_order(const float* data, int64_t n, const 
   }
   if (!grad_z && !grad_xy) return cudaGetLastError();
   knn_pairs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(
-      nbr, hit, qstate, m, k, n, keys, vals);
+      nbr, hit, qstate, m, k, n, items);
   int bits = 1;
   while (bits < 32 && (uint64_t(1) << bits) <= uint64_t(n)) ++bits;  // keys in [0, n]
-  if ((e = radix_sort_pairs(keys, vals, pairs, bits, sort_scratch, s)) != cudaSuccess) return e;
+  uint64_t* sorted_items = nullptr;
+  if ((e = radix_sort_items(items, pairs, bits, sort_scratch, s, &sorted_items)) != cudaSuccess)
+    return e;
   if ((e = cudaMemsetAsync(first, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(last, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
-  knn_runs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(keys, pairs, n, first,
-                                                                             last);
+  knn_runs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(sorted_items, pairs, n,
+                                                                             first, last);
   const unsigned pgrid = static_cast<unsigned>((n * 32 + 255) / 256);
   if (p == 2.0)
-    knn_point_grad_kernel<kPow2><<<pgrid, 256, 0, s>>>(first, last, vals, qstate, queries, data,
-                                                       n, p, grad_out, grad_z, grad_xy);
+    knn_point_grad_kernel<kPow2><<<pgrid, 256, 0, s>>>(first, last, sorted_items, qstate, queries,
+                                                       data, n, p, grad_out, grad_z, grad_xy);
   else
-    knn_point_grad_kernel<kPowGeneral><<<pgrid, 256, 0, s>>>(first, last, vals, qstate, queries,
-                                                             data, n, p, grad_out, grad_z,
-                                                             grad_xy);
+    knn_point_grad_kernel<kPowGeneral><<<pgrid, 256, 0, s>>>(first, last, sorted_items, qstate,
+                                                             queries, data, n, p, grad_out,
+                                                             grad_z, grad_xy);
   return cudaGetLastError();
 }
 }  // namespace

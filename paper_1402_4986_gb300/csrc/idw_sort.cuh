@@ -1,20 +1,28 @@
-// Stable least-significant-digit radix sort of (uint32 key, uint32 value)
-// pairs on the device, and a device-wide exclusive scan of int32 counts.
-// The deterministic gradient of the k-NN form uses it to turn the query-major
-// list of (data point, query) selections into a point-major one whose
-// queries stay in increasing order within each point (stability), so every
-// point's terms are summed in one fixed order.
+// Stable least-significant-digit radix sort of 64-bit items by the key in
+// their high word (the low word is a payload that travels with it), and a
+// device-wide exclusive scan of int32 counts.  The deterministic gradient of
+// the k-NN form uses it to turn the query-major list of (data point, query)
+// selections into a point-major one whose queries stay in increasing order
+// within each point (stability), so every point's terms are summed in one
+// fixed order.
 //
-// One pass sorts on 8 bits:
+// One pass sorts on 8 bits of the key:
 //   1. count: each CTA counts the digits of its tile of kSortTile items
 //      (shared-memory atomics: counts do not depend on order);
 //   2. scan: the counts, laid out digit-major (digit d of tile b at
 //      d * tiles + b), are scanned into each (digit, tile)'s first output
 //      position;
-//   3. scatter: each CTA walks its tile in rounds of 256 consecutive items
-//      and ranks each item among the equal digits before it: lanes of a warp
-//      by a match mask, warps of a round by per-warp digit counts, rounds by
-//      a running count per digit.  Equal keys keep their input order.
+//   3. scatter: each CTA loads its tile into registers, counts and scans
+//      its digits again to get each digit's start within the tile, ranks
+//      every item among the equal digits before it (lanes of a warp by a
+//      match mask, warps of a round of 256 items by per-warp digit counts,
+//      rounds by a running count per digit), places the items in shared
+//      memory in digit order, and writes them out: a digit's items of one
+//      tile go to consecutive addresses, so the writes coalesce into runs
+//      instead of one scattered 8-byte store per item.  Equal keys keep
+//      their input order.
+// Passes alternate between the caller's buffer and a scratch buffer; the
+// sort returns whichever holds the result, so nothing is copied back.
 #pragma once
 
 #include <cstdint>
@@ -31,9 +39,14 @@ constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items per CTA
 constexpr int kRadix = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kScanThreads = 1024;
+static_assert(kRadix == kSortThreads, "one digit per thread in the tile scan");
+
+__device__ __forceinline__ int item_digit(uint64_t v, int shift) {
+  return static_cast<int>((v >> (32 + shift)) & (kRadix - 1));
+}
 
 __global__ void __launch_bounds__(kSortThreads)
-    radix_count_kernel(const uint32_t* __restrict__ keys, int64_t count, int shift,
+    radix_count_kernel(const uint64_t* __restrict__ items, int64_t count, int shift,
                        int32_t* __restrict__ counts, int64_t tiles) {
   __shared__ int32_t h[kRadix];
   h[threadIdx.x] = 0;
@@ -41,7 +54,7 @@ __global__ void __launch_bounds__(kSortThreads)
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
   for (int r = 0; r < kSortRounds; ++r) {
     const int64_t x = base + int64_t(r) * kSortThreads + threadIdx.x;
-    if (x < count) atomicAdd(&h[(keys[x] >> shift) & (kRadix - 1)], 1);
+    if (x < count) atomicAdd(&h[item_digit(items[x], shift)], 1);
   }
   __syncthreads();
   counts[int64_t(threadIdx.x) * tiles + blockIdx.x] = h[threadIdx.x];
@@ -86,34 +99,59 @@ __global__ void __launch_bounds__(kScanThreads)
 }
 
 __global__ void __launch_bounds__(kSortThreads)
-    radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                         int64_t count, int shift, const int32_t* __restrict__ offsets,
-                         int64_t tiles, uint32_t* __restrict__ keys_out,
-                         uint32_t* __restrict__ vals_out) {
-  __shared__ int32_t running[kRadix];          // equal digits in earlier rounds
-  __shared__ int32_t wcount[kSortWarps][kRadix];  // equal digits per warp, this round
-  __shared__ int32_t first[kRadix];            // this tile's first position per digit
+    radix_scatter_kernel(const uint64_t* __restrict__ in, int64_t count, int shift,
+                         const int32_t* __restrict__ offsets, int64_t tiles,
+                         uint64_t* __restrict__ out) {
+  __shared__ uint64_t stage[kSortTile];             // the tile in digit order
+  __shared__ int32_t wcount[kSortWarps][kRadix];    // equal digits per warp, this round
+  __shared__ int32_t local[kRadix];                 // each digit's start within the tile
+  __shared__ int32_t running[kRadix];               // equal digits in earlier rounds
+  __shared__ int32_t first[kRadix];                 // each digit's first output position
+  __shared__ int32_t wsum[kSortWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t base = int64_t(blockIdx.x) * kSortTile;
+  const int in_tile = static_cast<int>(count - base < kSortTile ? count - base : kSortTile);
+  local[t] = 0;
   running[t] = 0;
   first[t] = offsets[int64_t(t) * tiles + blockIdx.x];
   for (int ww = 0; ww < kSortWarps; ++ww) wcount[ww][t] = 0;
   __syncthreads();
-  const int64_t base = int64_t(blockIdx.x) * kSortTile;
-  const unsigned lt = (1u << lane) - 1u;
+  uint64_t item[kSortRounds];
+#pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const int64_t x = base + int64_t(r) * kSortThreads + t;
-    const bool valid = x < count;
-    const uint32_t key = valid ? keys_in[x] : 0u;
-    const int d = valid ? int((key >> shift) & (kRadix - 1)) : kRadix;  // kRadix: no digit
+    const int x = r * kSortThreads + t;
+    item[r] = x < in_tile ? in[base + x] : 0ull;
+    if (x < in_tile) atomicAdd(&local[item_digit(item[r], shift)], 1);
+  }
+  __syncthreads();
+  // Exclusive scan of the tile's digit counts (digit t on thread t).
+  const int32_t own = local[t];
+  int32_t incl = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int32_t before = incl - own;
+  for (int ww = 0; ww < w; ++ww) before += wsum[ww];
+  local[t] = before;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int x = r * kSortThreads + t;
+    const bool valid = x < in_tile;
+    const int d = valid ? item_digit(item[r], shift) : kRadix;  // kRadix: no digit
     const unsigned peers = __match_any_sync(0xffffffffu, d);
     const int rank = __popc(peers & lt);
     if (valid && rank == 0) wcount[w][d] = __popc(peers);
     __syncthreads();
     if (valid) {
-      int pos = first[d] + running[d] + rank;
+      int pos = local[d] + running[d] + rank;
       for (int ww = 0; ww < w; ++ww) pos += wcount[ww][d];
-      keys_out[pos] = key;
-      vals_out[pos] = vals_in[x];
+      stage[pos] = item[r];
     }
     __syncthreads();
     int add = 0;
@@ -123,6 +161,12 @@ __global__ void __launch_bounds__(kSortThreads)
     }
     running[t] += add;
     __syncthreads();
+  }
+  // Positions i .. of one digit are consecutive here and in the output.
+  for (int i = t; i < in_tile; i += kSortThreads) {
+    const uint64_t v = stage[i];
+    const int d = item_digit(v, shift);
+    out[first[d] + (i - local[d])] = v;
   }
 }
 
@@ -154,49 +198,43 @@ inline cudaError_t exclusive_scan_i32(int32_t* v, int64_t count, void* scratch, 
   return cudaGetLastError();
 }
 
-// Scratch (bytes) radix_sort_pairs needs for `count` pairs: one more key and
-// value buffer, the digit counts and the scan's scratch.
+// Scratch (bytes) radix_sort_items needs for `count` items: the second item
+// buffer, the digit counts and the scan's scratch.
 inline size_t radix_sort_scratch_bytes(int64_t count) {
   using namespace sort_detail;
   const int64_t tiles = (count + kSortTile - 1) / kSortTile;
-  const size_t pairs = (size_t(count) * sizeof(uint32_t) + 255) / 256 * 256;
+  const size_t items = (size_t(count) * sizeof(uint64_t) + 255) / 256 * 256;
   const size_t counts = (size_t(tiles) * kRadix * sizeof(int32_t) + 255) / 256 * 256;
-  return 2 * pairs + counts + scan_scratch_bytes(tiles * kRadix);
+  return items + counts + scan_scratch_bytes(tiles * kRadix);
 }
 
-// Stable sort of (keys, vals) by the low `bits` bits of the keys.  The result
-// ends in keys/vals (the scratch holds the other buffer of each pass).
-inline cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t count, int bits,
-                                    void* scratch, cudaStream_t s) {
+// Stable sort of `count` items by the low `bits` bits of their high words.
+// *result is set to the buffer that holds the sorted items: `items` after an
+// even number of 8-bit passes, the scratch buffer after an odd one.
+inline cudaError_t radix_sort_items(uint64_t* items, int64_t count, int bits, void* scratch,
+                                    cudaStream_t s, uint64_t** result) {
   using namespace sort_detail;
+  *result = items;
   if (count <= 1) return cudaSuccess;
   const int64_t tiles = (count + kSortTile - 1) / kSortTile;
-  const size_t pairs = (size_t(count) * sizeof(uint32_t) + 255) / 256 * 256;
+  const size_t ibytes = (size_t(count) * sizeof(uint64_t) + 255) / 256 * 256;
   unsigned char* p = static_cast<unsigned char*>(scratch);
-  uint32_t* k2 = reinterpret_cast<uint32_t*>(p);
-  uint32_t* v2 = reinterpret_cast<uint32_t*>(p + pairs);
-  int32_t* counts = reinterpret_cast<int32_t*>(p + 2 * pairs);
-  void* scan_scratch = p + 2 * pairs + (size_t(tiles) * kRadix * sizeof(int32_t) + 255) / 256 * 256;
-  uint32_t *ki = keys, *vi = vals, *ko = k2, *vo = v2;
+  uint64_t* other = reinterpret_cast<uint64_t*>(p);
+  int32_t* counts = reinterpret_cast<int32_t*>(p + ibytes);
+  void* scan_scratch = p + ibytes + (size_t(tiles) * kRadix * sizeof(int32_t) + 255) / 256 * 256;
+  uint64_t *src = items, *dst = other;
   const int passes = (bits + 7) / 8;
   for (int pass = 0; pass < passes; ++pass) {
     const int shift = 8 * pass;
-    radix_count_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(ki, count, shift,
+    radix_count_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(src, count, shift,
                                                                              counts, tiles);
     cudaError_t e = exclusive_scan_i32(counts, tiles * kRadix, scan_scratch, s);
     if (e != cudaSuccess) return e;
     radix_scatter_kernel<<<static_cast<unsigned>(tiles), kSortThreads, 0, s>>>(
-        ki, vi, count, shift, counts, tiles, ko, vo);
-    std::swap(ki, ko);
-    std::swap(vi, vo);
+        src, count, shift, counts, tiles, dst);
+    std::swap(src, dst);
   }
-  if (ki != keys) {  // an odd number of passes: copy back
-    cudaError_t e = cudaMemcpyAsync(keys, ki, size_t(count) * sizeof(uint32_t),
-                                    cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(vals, vi, size_t(count) * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-  }
+  *result = src;
   return cudaGetLastError();
 }
 
