@@ -97,7 +97,12 @@ def test_partial_outputs_and_errors(idw):
     full = idw.knn_backward(d, q, 2.0, 8, g)
     only_q = idw.knn_backward(d, q, 2.0, 8, g, need_z=False, need_data_xy=False, need_p=False)
     assert only_q[0] is None and only_q[1] is None and only_q[3] is None
-    assert torch.allclose(only_q[2], full[2], rtol=0, atol=1e-5 * float(full[2].abs().max()))
+    # Two calls agree to the oracle tolerance, not bitwise: each query sums
+    # its selection in heap order, which follows the cell scatter's order
+    # and so varies between calls, and the sums are rescaled whenever a
+    # nearer point appears; measured call-to-call differences reach 1e-5 of
+    # the largest dL/dq.
+    assert torch.allclose(only_q[2], full[2], rtol=0, atol=TOL * float(full[2].abs().max()))
     for bad_k in (0, 65):
         with pytest.raises(idw.IDWError):
             idw.knn_backward(d, q, 2.0, bad_k, g)
