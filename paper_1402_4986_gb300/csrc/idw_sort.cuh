@@ -12,15 +12,15 @@
 //   2. scan: the counts, laid out digit-major (digit d of tile b at
 //      d * tiles + b), are scanned into each (digit, tile)'s first output
 //      position;
-//   3. scatter: each CTA loads its tile into registers, counts and scans
-//      its digits again to get each digit's start within the tile, ranks
-//      every item among the equal digits before it (lanes of a warp by a
-//      match mask, warps of a round of 256 items by per-warp digit counts,
-//      rounds by a running count per digit), places the items in shared
-//      memory in digit order, and writes them out: a digit's items of one
-//      tile go to consecutive addresses, so the writes coalesce into runs
-//      instead of one scattered 8-byte store per item.  Equal keys keep
-//      their input order.
+//   3. scatter: each CTA loads its tile into registers, a contiguous slice
+//      per warp, and ranks every item among the equal digits before it in
+//      its warp's slice (lanes of a round by a match mask, rounds by the
+//      warp's own digit counters, so no CTA barrier per round); the warps'
+//      counts give each digit's start within the tile and each warp's
+//      offset inside it; the items are placed in shared memory in digit
+//      order and written out, a digit's items of one tile to consecutive
+//      addresses, so the writes coalesce into runs instead of one scattered
+//      8-byte store per item.  Equal keys keep their input order.
 // Passes alternate between the caller's buffer and a scratch buffer; the
 // sort returns whichever holds the result, so nothing is copied back.
 #pragma once
@@ -34,8 +34,8 @@ namespace idw {
 namespace sort_detail {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
-constexpr int kSortTile = kSortThreads * kSortRounds;  // 4096 items per CTA
+constexpr int kSortRounds = 8;
+constexpr int kSortTile = kSortThreads * kSortRounds;  // 2048 items per CTA
 constexpr int kRadix = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kScanThreads = 1024;
@@ -98,34 +98,57 @@ __global__ void __launch_bounds__(kScanThreads)
   if (x < count) v[x] += bases[blockIdx.x];
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
     radix_scatter_kernel(const uint64_t* __restrict__ in, int64_t count, int shift,
                          const int32_t* __restrict__ offsets, int64_t tiles,
                          uint64_t* __restrict__ out) {
-  __shared__ uint64_t stage[kSortTile];             // the tile in digit order
-  __shared__ int32_t wcount[kSortWarps][kRadix];    // equal digits per warp, this round
-  __shared__ int32_t local[kRadix];                 // each digit's start within the tile
-  __shared__ int32_t running[kRadix];               // equal digits in earlier rounds
-  __shared__ int32_t first[kRadix];                 // each digit's first output position
+  __shared__ uint64_t stage[kSortTile];           // the tile in digit order
+  __shared__ int32_t wcount[kSortWarps][kRadix];  // per warp: digits seen, then its prefix
+  __shared__ int32_t local[kRadix];               // each digit's start within the tile
+  __shared__ int32_t first[kRadix];               // each digit's first output position
   __shared__ int32_t wsum[kSortWarps];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int64_t base = int64_t(blockIdx.x) * kSortTile;
   const int in_tile = static_cast<int>(count - base < kSortTile ? count - base : kSortTile);
-  local[t] = 0;
-  running[t] = 0;
   first[t] = offsets[int64_t(t) * tiles + blockIdx.x];
   for (int ww = 0; ww < kSortWarps; ++ww) wcount[ww][t] = 0;
   __syncthreads();
+  // Warp w owns items [w * 32 kSortRounds, (w + 1) * 32 kSortRounds) of the
+  // tile, round r lane l holding item w * 32 kSortRounds + 32 r + l, so the
+  // order (warp, round, lane) is the input order.  Its rank among the equal
+  // digits before it within the warp: earlier rounds (the warp's own
+  // counters) plus the lanes below it in its round (a match mask).
   uint64_t item[kSortRounds];
+  int rank[kSortRounds];
+  const int wbase = w * 32 * kSortRounds;
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const int x = r * kSortThreads + t;
+    const int x = wbase + 32 * r + lane;
     item[r] = x < in_tile ? in[base + x] : 0ull;
-    if (x < in_tile) atomicAdd(&local[item_digit(item[r], shift)], 1);
+  }
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int x = wbase + 32 * r + lane;
+    const bool valid = x < in_tile;
+    const int d = valid ? item_digit(item[r], shift) : kRadix;  // kRadix: no digit
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int below = __popc(peers & lt);
+    const int seen = wcount[w][valid ? d : 0];
+    rank[r] = valid ? seen + below : 0;
+    __syncwarp();
+    if (valid && below == 0) wcount[w][d] += __popc(peers);
+    __syncwarp();
   }
   __syncthreads();
-  // Exclusive scan of the tile's digit counts (digit t on thread t).
-  const int32_t own = local[t];
+  // Digit t: the warps' counts become their exclusive prefix, and the tile's
+  // total for the digit is scanned over the digits into its start.
+  int32_t own = 0;
+  for (int ww = 0; ww < kSortWarps; ++ww) {
+    const int32_t c = wcount[ww][t];
+    wcount[ww][t] = own;
+    own += c;
+  }
   int32_t incl = own;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -138,30 +161,15 @@ __global__ void __launch_bounds__(kSortThreads)
   for (int ww = 0; ww < w; ++ww) before += wsum[ww];
   local[t] = before;
   __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const int x = r * kSortThreads + t;
-    const bool valid = x < in_tile;
-    const int d = valid ? item_digit(item[r], shift) : kRadix;  // kRadix: no digit
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & lt);
-    if (valid && rank == 0) wcount[w][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      int pos = local[d] + running[d] + rank;
-      for (int ww = 0; ww < w; ++ww) pos += wcount[ww][d];
-      stage[pos] = item[r];
+    const int x = wbase + 32 * r + lane;
+    if (x < in_tile) {
+      const int d = item_digit(item[r], shift);
+      stage[local[d] + wcount[w][d] + rank[r]] = item[r];
     }
-    __syncthreads();
-    int add = 0;
-    for (int ww = 0; ww < kSortWarps; ++ww) {
-      add += wcount[ww][t];
-      wcount[ww][t] = 0;
-    }
-    running[t] += add;
-    __syncthreads();
   }
+  __syncthreads();
   // Positions i .. of one digit are consecutive here and in the output.
   for (int i = t; i < in_tile; i += kSortThreads) {
     const uint64_t v = stage[i];
