@@ -1849,9 +1849,9 @@ __global__ void __launch_bounds__(kLocalThreads)
 // Point-major data-side terms in a fixed order: every (point, query)
 // selection becomes one 64-bit item, the point index above the query index,
 // listed query-major; a stable radix sort by point keeps each point's
-// queries in increasing order; one warp per point then recomputes its
-// terms from the queries' states and sums them lane-strided and by a fixed
-// shuffle tree.
+// queries in increasing order; 8 lanes per point (a whole warp for a point
+// with many terms) then recompute its terms from the queries' states and
+// sum them lane-strided and by a fixed shuffle tree.
 // dL/dp is summed over queries in index order by a fixed two-level tree.
 // Nothing depends on the order in which threads or atomics ran, so two calls
 // on the same inputs give the same bits.
@@ -1891,9 +1891,54 @@ __global__ void __launch_bounds__(256)
     last[key] = static_cast<int32_t>(x + 1);
 }
 
-// One warp per data point: its terms (dL/dz, dL/dx, dL/dy), query by query
-// in increasing query order, recomputed as the query-major kernel computes
-// them.
+// The data-side terms (dL/dz, dL/dx, dL/dy) of point (x0, y0, zi) for the
+// query of pair item q, recomputed as the query-major kernel computes them,
+// added to (gz, gx, gy).
+template <int MODE>
+__device__ __forceinline__ void knn_point_term(uint64_t item, const KnnQState* __restrict__ qstate,
+                                               const float* __restrict__ queries,
+                                               const float* __restrict__ grad_out, float x0,
+                                               float y0, float zi, double p, float hp, float pf,
+                                               float& gz, float& gx, float& gy) {
+  const int64_t j = uint32_t(item);  // the pair's query
+  const KnnQState st = qstate[j];
+  const float gj = grad_out[j];
+  const float qx = queries[2 * j], qy = queries[2 * j + 1];
+  if (st.mode == kKnnQHit) {
+    gz += gj;
+  } else if (st.mode == kKnnQF32) {
+    const float Z = static_cast<float>(st.Z), c = static_cast<float>(st.c);
+    const float d2min = static_cast<float>(st.d2min);
+    const float dx = __fsub_rn(qx, x0), dy = __fsub_rn(qy, y0);
+    const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+    const float w = grad_weight<MODE>(d2, d2min, st.lmin, hp);
+    const float ar = (zi - Z) * w * rcp_approx(d2);
+    const float bb = c * pf * ar;
+    gz += c * w;
+    gx += bb * dx;
+    gy += bb * dy;
+  } else if (st.mode == kKnnQF64) {
+    const double ex = double(qx) - x0, ey = double(qy) - y0, e2 = ex * ex + ey * ey;
+    const double w = pow(st.d2min / e2, 0.5 * p);
+    const double av = (double(zi) - st.Z) * w;
+    gz += static_cast<float>(st.c * w);
+    gx += static_cast<float>(st.c * p * av * ex / e2);
+    gy += static_cast<float>(st.c * p * av * ey / e2);
+  }
+}
+
+// A warp takes kPointsPerWarp consecutive data points and sums each one's
+// terms in increasing query order: normally kPointLanes lanes per point,
+// lane l summing the point's terms l, l + kPointLanes, ... and the lanes'
+// sums joined by a fixed shuffle tree (about k terms per point when m = n,
+// so a whole warp per point would leave most lanes one term and the warp
+// waiting on it); if one of its points has more than kHeavyTerms terms
+// (clustered data: a point inside a blob), all 32 lanes take the warp's
+// points one after the other the same way.  The choice depends only on the
+// counts, so a point's order of summation is the same in every call.
+constexpr int kPointLanes = 8;
+constexpr int kPointsPerWarp = 32 / kPointLanes;
+constexpr int kHeavyTerms = 16 * kPointLanes;
 template <int MODE>
 __global__ void __launch_bounds__(256)
     knn_point_grad_kernel(const int32_t* __restrict__ first, const int32_t* __restrict__ last,
@@ -1901,46 +1946,51 @@ __global__ void __launch_bounds__(256)
                           const float* __restrict__ queries, const float* __restrict__ data,
                           int64_t n, double p, const float* __restrict__ grad_out,
                           float* __restrict__ grad_z, float* __restrict__ grad_xy) {
-  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= n) return;  // whole warps
-  const float x0 = data[3 * i], y0 = data[3 * i + 1], zi = data[3 * i + 2];
-  const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
-  float gz = 0.f, gx = 0.f, gy = 0.f;
-  const int a = first[i], b = last[i];
-  for (int q = a + lane; q < b; q += 32) {
-    const int64_t j = uint32_t(items[q]);  // the pair's query
-    const KnnQState st = qstate[j];
-    const float gj = grad_out[j];
-    const float qx = queries[2 * j], qy = queries[2 * j + 1];
-    if (st.mode == kKnnQHit) {
-      gz += gj;
-    } else if (st.mode == kKnnQF32) {
-      const float Z = static_cast<float>(st.Z), c = static_cast<float>(st.c);
-      const float d2min = static_cast<float>(st.d2min);
-      const float dx = __fsub_rn(qx, x0), dy = __fsub_rn(qy, y0);
-      const float d2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
-      const float w = grad_weight<MODE>(d2, d2min, st.lmin, hp);
-      const float ar = (zi - Z) * w * rcp_approx(d2);
-      const float bb = c * pf * ar;
-      gz += c * w;
-      gx += bb * dx;
-      gy += bb * dy;
-    } else if (st.mode == kKnnQF64) {
-      const double ex = double(qx) - x0, ey = double(qy) - y0, e2 = ex * ex + ey * ey;
-      const double w = pow(st.d2min / e2, 0.5 * p);
-      const double av = (double(zi) - st.Z) * w;
-      gz += static_cast<float>(st.c * w);
-      gx += static_cast<float>(st.c * p * av * ex / e2);
-      gy += static_cast<float>(st.c * p * av * ey / e2);
-    }
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane32 = threadIdx.x & 31;
+  const int64_t i0 = ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * kPointsPerWarp;
+  const int g = lane32 / kPointLanes, lane = lane32 % kPointLanes;
+  const int64_t i = i0 + g;
+  const bool own = i < n;  // every lane stays for the shuffles
+  float x0 = 0.f, y0 = 0.f, zi = 0.f;
+  int a = 0, b = 0;
+  if (own) {
+    x0 = data[3 * i];
+    y0 = data[3 * i + 1];
+    zi = data[3 * i + 2];
+    a = first[i];
+    b = last[i];
   }
-  gz = warp_sum(gz);
-  gx = warp_sum(gx);
-  gy = warp_sum(gy);
-  if (lane == 0) {
-    if (grad_z) grad_z[i] = gz;
-    if (grad_xy) reinterpret_cast<float2*>(grad_xy)[i] = make_float2(gx, gy);
+  const float hp = static_cast<float>(0.5 * p), pf = static_cast<float>(p);
+  auto put = [&](int64_t pi, float gz, float gx, float gy) {
+    if (grad_z) grad_z[pi] = gz;
+    if (grad_xy) reinterpret_cast<float2*>(grad_xy)[pi] = make_float2(gx, gy);
+  };
+  if (!__any_sync(kFull, b - a > kHeavyTerms)) {
+    float gz = 0.f, gx = 0.f, gy = 0.f;
+    for (int q = a + lane; q < b; q += kPointLanes)
+      knn_point_term<MODE>(items[q], qstate, queries, grad_out, x0, y0, zi, p, hp, pf, gz, gx, gy);
+#pragma unroll
+    for (int o = kPointLanes / 2; o > 0; o >>= 1) {
+      gz += __shfl_xor_sync(kFull, gz, o);
+      gx += __shfl_xor_sync(kFull, gx, o);
+      gy += __shfl_xor_sync(kFull, gy, o);
+    }
+    if (own && lane == 0) put(i, gz, gx, gy);
+    return;
+  }
+  for (int h = 0; h < kPointsPerWarp; ++h) {  // the whole warp on each point
+    const int src = h * kPointLanes;
+    const float hx = __shfl_sync(kFull, x0, src), hy = __shfl_sync(kFull, y0, src);
+    const float hz = __shfl_sync(kFull, zi, src);
+    const int ha = __shfl_sync(kFull, a, src), hb = __shfl_sync(kFull, b, src);
+    float gz = 0.f, gx = 0.f, gy = 0.f;
+    for (int q = ha + lane32; q < hb; q += 32)
+      knn_point_term<MODE>(items[q], qstate, queries, grad_out, hx, hy, hz, p, hp, pf, gz, gx, gy);
+    gz = warp_sum(gz);
+    gx = warp_sum(gx);
+    gy = warp_sum(gy);
+    if (lane32 == 0 && i0 + h < n) put(i0 + h, gz, gx, gy);
   }
 }
 
@@ -2208,7 +2258,8 @@ cudaError_t launch_knn_backward_fixed_order(const float* data, int64_t n, const 
   if ((e = cudaMemsetAsync(last, 0, size_t(n) * 4, s)) != cudaSuccess) return e;
   knn_runs_kernel<<<static_cast<unsigned>((pairs + 255) / 256), 256, 0, s>>>(sorted_items, pairs, n,
                                                                              first, last);
-  const unsigned pgrid = static_cast<unsigned>((n * 32 + 255) / 256);
+  const unsigned pgrid =
+      static_cast<unsigned>(((n + kPointsPerWarp - 1) / kPointsPerWarp * 32 + 255) / 256);
   if (p == 2.0)
     knn_point_grad_kernel<kPow2><<<pgrid, 256, 0, s>>>(first, last, sorted_items, qstate, queries,
                                                        data, n, p, grad_out, grad_z, grad_xy);
